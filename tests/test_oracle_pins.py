@@ -1,0 +1,274 @@
+"""Pins for the FP64 oracle: each check compares it with something other than
+itself (a closed form, a different algorithm, brute force, a library routine
+used on a different formulation).  CPU only."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+
+def _rng(s):
+    return np.random.default_rng(s)
+
+
+def _orthonormal(d, k, rng):
+    Q, _ = np.linalg.qr(rng.standard_normal((d, k)))
+    return Q
+
+
+def _small_problem(seed=0, n=600, d=12, lam=(9.0, 5.0, 3.0, 1.0), sigma=0.3, sizes=(250, 200, 150)):
+    A = synth.spiked_rows(n, d, np.array(lam), sigma, seed, out_dtype=np.float64, threads=1)
+    parts = synth.split_rows(A, list(sizes))
+    return A, parts
+
+
+def _qr_power(M, Y0, steps):
+    """orth(M^steps Y0) by one matrix power and one QR (a route the oracle never takes)."""
+    Q, R = np.linalg.qr(np.linalg.matrix_power(M, steps) @ Y0)
+    return Q * np.sign(np.diag(R))
+
+
+# --------------------------------------------------------------------------- metric
+
+def test_subspace_dist_matches_definition_and_angles():
+    rng = _rng(1)
+    for _ in range(20):
+        d, k = 15, 4
+        U, V = _orthonormal(d, k, rng), _orthonormal(d, k, rng)
+        explicit = np.linalg.norm(U @ U.T - V @ V.T, 2)               # Def. 1 verbatim
+        cos_min = np.linalg.svd(U.T @ V, compute_uv=False).min()      # cos theta_k
+        assert O.subspace_dist(U, V) == pytest.approx(explicit, abs=1e-13)
+        assert O.subspace_dist(U, V) == pytest.approx(np.sqrt(max(0.0, 1 - cos_min ** 2)), abs=1e-10)
+    U = _orthonormal(10, 3, rng)
+    assert O.subspace_dist(U, U @ _orthonormal(3, 3, rng)) < 1e-14     # same span
+    E = np.eye(6)
+    assert O.subspace_dist(E[:, :2], E[:, 2:4]) == pytest.approx(1.0)  # orthogonal spans
+
+
+def test_subspace_dist_tiny_angle_accuracy():
+    # A rotation by a known tiny angle theta in the (e1, e4) plane: dist = sin(theta).
+    for theta in (1e-4, 1e-7, 1e-10):
+        U = np.eye(8)[:, :3]
+        V = U.copy()
+        V[:, 0] = np.cos(theta) * np.eye(8)[:, 0] + np.sin(theta) * np.eye(8)[:, 3]
+        assert O.subspace_dist(U, V) == pytest.approx(np.sin(theta), rel=1e-6)
+
+
+# --------------------------------------------------------------------------- orth
+
+def test_orth_is_q_factor_with_positive_r_diagonal():
+    rng = _rng(2)
+    Y = rng.standard_normal((40, 7)) @ np.diag([1e3, 1, 1, 1e-2, 5, 1, 1])
+    Q = O.orth(Y)
+    R = Q.T @ Y
+    assert np.abs(Q.T @ Q - np.eye(7)).max() < 1e-14
+    assert np.abs(np.tril(R, -1)).max() < 1e-10 * np.abs(R).max()
+    assert (np.diag(R) > 0).all()
+    assert np.abs(Q @ R - Y).max() < 1e-12 * np.abs(Y).max()
+
+
+# --------------------------------------------------------------------------- whole loop
+
+@pytest.mark.parametrize("agg", ["identity", "sign", "opt"])
+def test_p1_is_distributed_power_iteration(agg):
+    """p = 1 is DPI (Sec. 3, the special case below the definition of I_T): after T
+    rounds the output spans M^T Z_0 with M = sum_i p_i M_i formed explicitly."""
+    A, parts = _small_problem(seed=3)
+    Y0 = synth.gaussian_start(12, 3, 5)
+    T = 9
+    r = O.localpower(parts, 3, [1] * T, agg, Y0)
+    M = A.T @ A / A.shape[0]
+    assert O.subspace_dist(r["Z"], _qr_power(M, Y0, T)) < 1e-10  # matrix power: cond ~ (lam1/lam3)^T
+    assert r["rounds"] == T and r["local_steps"] == T
+
+
+@pytest.mark.parametrize("agg", ["identity", "sign", "opt"])
+def test_single_partition_is_subspace_iteration(agg):
+    A, _ = _small_problem(seed=4, sizes=(600,))
+    Y0 = synth.gaussian_start(12, 3, 6)
+    sched = [3, 2, 4, 1]
+    r = O.localpower([A], 3, sched, agg, Y0)
+    M = A.T @ A / A.shape[0]
+    assert O.subspace_dist(r["Z"], _qr_power(M, Y0, sum(sched))) < 1e-10
+
+
+@pytest.mark.parametrize("agg", ["identity", "sign", "opt"])
+def test_replicated_partitions_have_no_local_drift(agg):
+    """eta = 0 (every M_i = M, Def. 2): local iterates never drift apart, so the
+    output equals subspace iteration with sum(p_t) steps."""
+    A, _ = _small_problem(seed=5, n=300, sizes=(300,))
+    Y0 = synth.gaussian_start(12, 3, 7)
+    sched = [4, 4, 2]
+    r = O.localpower([A, A.copy(), A.copy()], 3, sched, agg, Y0)
+    M = A.T @ A / A.shape[0]
+    assert O.subspace_dist(r["Z"], _qr_power(M, Y0, sum(sched))) < 1e-10
+
+
+@pytest.mark.parametrize("agg", ["sign", "opt"])
+def test_decay_to_p1_converges_to_eigh(agg):
+    """With p decayed to 1 the error goes to zero (Sec. 3, decaying p; Sec. 5):
+    compare with a full eigendecomposition of M."""
+    A, parts = _small_problem(seed=6, d=8, lam=(8.0, 6.0, 4.0), sigma=0.5, n=900, sizes=(400, 300, 200))
+    Y0 = synth.gaussian_start(8, 3, 8)
+    sched = [8] * 3 + [4] * 3 + [2] * 3 + [1] * 80
+    r = O.localpower(parts, 3, sched, agg, Y0)
+    lam, V = np.linalg.eigh(A.T @ A / A.shape[0])
+    assert O.subspace_dist(r["Z"], V[:, -3:]) < 1e-10
+
+
+def test_constant_p_leaves_a_floor_that_p1_removes():
+    """Sec. 5 (final precision): with a constant p > 1 the error stops decreasing at
+    a non-zero floor; p = 1 does not have one.  Qualitative (the floor's value has
+    no closed form: parity unpinned)."""
+    A, parts = _small_problem(seed=7, d=10, lam=(5.0, 4.0, 3.0), sigma=0.6, n=200, sizes=(50, 50, 50, 50))
+    Y0 = synth.gaussian_start(10, 3, 9)
+    lam, V = np.linalg.eigh(A.T @ A / A.shape[0])
+    truth = V[:, -3:]
+    e1 = O.localpower(parts, 3, [1] * 120, "sign", Y0, truth=truth)["trace"][-1]["dist"]
+    e8 = O.localpower(parts, 3, [8] * 60, "sign", Y0, truth=truth)
+    assert e1 < 1e-8
+    d8 = [t["dist"] for t in e8["trace"]]
+    assert d8[-1] > 1e-4 and abs(d8[-1] - d8[-10]) < 1e-3 * d8[-1] + 1e-12
+
+
+# --------------------------------------------------------------------------- alignment
+
+def test_procrustes_lemma_identities():
+    """App. A, Lemma (orthogonal Procrustes): ||U - U~ O*||_2 = sqrt(2 - 2 sqrt(1 - dist^2))
+    and dist <= ||U - U~ O*||_2 <= sqrt(2) dist, with O* from the SVD of U~^T U."""
+    rng = _rng(10)
+    for scale in (1e-3, 1e-1, 0.5, 2.0):
+        for _ in range(10):
+            U = _orthonormal(20, 4, rng)
+            Ut = O.orth(U @ _orthonormal(4, 4, rng) + scale * rng.standard_normal((20, 4)))
+            Ostar = O.procrustes(Ut, U)
+            dd = np.linalg.norm(U - Ut @ Ostar, 2)
+            dist = O.subspace_dist(U, Ut)
+            assert dd == pytest.approx(np.sqrt(2 - 2 * np.sqrt(1 - dist ** 2)), rel=1e-9, abs=1e-14)
+            assert dist - 1e-12 <= dd <= np.sqrt(2) * dist + 1e-12
+            assert np.abs(Ostar.T @ Ostar - np.eye(4)).max() < 1e-13
+
+
+def test_procrustes_is_the_frobenius_minimiser():
+    rng = _rng(11)
+    Zi, Zb = _orthonormal(15, 3, rng), _orthonormal(15, 3, rng)
+    best = np.linalg.norm(Zi @ O.procrustes(Zi, Zb) - Zb)
+    for _ in range(500):
+        Q = _orthonormal(3, 3, rng)
+        assert best <= np.linalg.norm(Zi @ Q - Zb) + 1e-12
+
+
+def test_sign_fix_is_the_brute_force_minimiser():
+    rng = _rng(12)
+    for _ in range(20):
+        Zi, Zb = _orthonormal(9, 5, rng), _orthonormal(9, 5, rng)
+        D = O.sign_fix(Zi, Zb)
+        got = np.linalg.norm(Zi @ D - Zb)
+        brute = min(np.linalg.norm(Zi @ np.diag(s) - Zb) for s in itertools.product([-1.0, 1.0], repeat=5))
+        assert got == pytest.approx(brute, abs=1e-13)
+        assert set(np.diag(D)) <= {-1.0, 1.0}
+
+
+def test_k1_sign_fixing_equals_opt():
+    """For k = 1 the only orthogonal 1 x 1 matrices are +-1, so OPT and sign-fixing
+    coincide (the remark after eq. (4))."""
+    _, parts = _small_problem(seed=13)
+    Y0 = synth.gaussian_start(12, 1, 14)
+    rs = O.localpower(parts, 1, [4, 4, 3], "sign", Y0)
+    ro = O.localpower(parts, 1, [4, 4, 3], "opt", Y0)
+    assert np.abs(rs["Y"] - ro["Y"]).max() < 1e-13
+
+
+def test_aggregation_invariances():
+    """Sign-fixing and OPT make the aggregate independent of column signs (and, for
+    OPT, of any rotation) of the non-base local bases; transforming the base's
+    basis transforms the output the same way."""
+    rng = _rng(15)
+    sizes = [30, 50, 40]          # base = worker 1 (most rows)
+    Zl = [_orthonormal(11, 4, rng) for _ in sizes]
+    Yl = [rng.standard_normal((11, 4)) for _ in sizes]
+    S = np.diag([1.0, -1.0, -1.0, 1.0])
+    Q = _orthonormal(4, 4, rng)
+    for kind in ("sign", "opt"):
+        ref = O.aggregate(Yl, Zl, sizes, kind)
+        for i in (0, 2):
+            Y2, Z2 = list(Yl), list(Zl)
+            Y2[i], Z2[i] = Yl[i] @ S, Zl[i] @ S
+            assert np.abs(O.aggregate(Y2, Z2, sizes, kind) - ref).max() < 1e-13
+        Y2, Z2 = list(Yl), list(Zl)
+        Y2[1], Z2[1] = Yl[1] @ S, Zl[1] @ S
+        assert np.abs(O.aggregate(Y2, Z2, sizes, kind) - ref @ S).max() < 1e-13
+    ref = O.aggregate(Yl, Zl, sizes, "opt")
+    Y2, Z2 = list(Yl), list(Zl)
+    Y2[2], Z2[2] = Yl[2] @ Q, Zl[2] @ Q
+    assert np.abs(O.aggregate(Y2, Z2, sizes, "opt") - ref).max() < 1e-12
+    # vanilla averaging is NOT sign invariant
+    Y2, Z2 = list(Yl), list(Zl)
+    Y2[0], Z2[0] = Yl[0] @ S, Zl[0] @ S
+    assert np.abs(O.aggregate(Y2, Z2, sizes, "identity") - O.aggregate(Yl, Zl, sizes, "identity")).max() > 1e-3
+
+
+def test_base_is_the_largest_partition_lowest_index_on_ties():
+    assert O.base_index([3, 9, 9, 2]) == 1
+    assert O.base_index([5, 5, 5]) == 0
+    assert O.base_index([1, 2, 3]) == 2
+
+
+# --------------------------------------------------------------------------- Ritz
+
+def test_ritz_recovers_singular_values():
+    """sigma_j = sqrt(n lam_j(Z^T M Z)) equals the singular values of A when Z spans
+    the top right singular vectors (LAPACK SVD of A, a different factorisation)."""
+    A, parts = _small_problem(seed=16, n=300, sizes=(100, 120, 80))
+    _, s, Vt = np.linalg.svd(A, full_matrices=False)
+    Zr, sig = O.ritz(parts, O.orth(Vt[:4].T @ _orthonormal(4, 4, _rng(17))))
+    assert np.allclose(sig, s[:4], rtol=1e-12)
+    for j in range(4):
+        assert abs(abs(Zr[:, j] @ Vt[j]) - 1) < 1e-10
+
+
+def test_rayleigh_quotients_converge_to_top_squared_singular_values():
+    A, parts = _small_problem(seed=18, d=8, lam=(8.0, 6.0, 4.0), sigma=0.5, n=900, sizes=(400, 300, 200))
+    Y0 = synth.gaussian_start(8, 3, 19)
+    r = O.localpower(parts, 3, [4] * 3 + [1] * 80, "sign", Y0)
+    _, sig = O.ritz(parts, r["Z"])
+    s = np.linalg.svd(A, compute_uv=False)
+    assert np.allclose(sig ** 2 / A.shape[0], s[:3] ** 2 / A.shape[0], rtol=1e-10)
+
+
+# --------------------------------------------------------------------------- data model
+
+def test_spiked_model_top_subspace_is_the_spike_basis():
+    """For the spiked model the population top-k subspace is U[:, :k]; the sample one
+    is within O(sqrt(d/n)/gap) of it (loose check of generator + oracle)."""
+    d, lam, sigma, n = 20, np.array([9.0, 6.0, 4.0]), 0.5, 40_000
+    A = synth.spiked_rows(n, d, lam, sigma, 21, out_dtype=np.float64, threads=2)
+    U = synth.haar_columns(d, 3, 21)
+    V, _ = O.top_k_truth([A], 3)
+    assert O.subspace_dist(V, U) < 10 * np.sqrt(d / n) * (lam[0] + sigma ** 2) / lam[2]
+
+
+def test_stored_form_decoders_follow_the_formats():
+    # BF16: top half of the FP32 pattern.
+    assert O.decode_bf16(np.array([0x3F80, 0xC000, 0x3FC0], dtype=np.uint16)).tolist() == [1.0, -2.0, 1.5]
+    # E4M3 (OCP FN): 0x38 = 1, 0x7E = 448 (largest), 0x01 = 2^-9 (smallest subnormal),
+    # 0x08 = 2^-6 (smallest normal), 0xB8 = -1, 0x7F = NaN.
+    v = O.decode_e4m3(np.array([[0x38, 0x7E, 0x01, 0x08, 0xB8, 0x00]], dtype=np.uint8), np.array([1.0], np.float32))
+    assert v.tolist() == [[1.0, 448.0, 2.0 ** -9, 2.0 ** -6, -1.0, 0.0]]
+    assert np.isnan(O.decode_e4m3(np.array([[0x7F]], np.uint8), np.array([1.0], np.float32))).all()
+
+
+def test_encoders_round_to_nearest_within_half_an_ulp():
+    rng = _rng(22)
+    x = rng.standard_normal((64, 33)).astype(np.float32) * 3
+    xb = O.decode_bf16(synth.f32_to_bf16_bits(x))
+    assert (np.abs(xb - x) <= 2.0 ** -8 * np.abs(x) + 1e-45).all()
+    codes, sc = synth.f32_to_e4m3_rowscaled(x)
+    xq = O.decode_e4m3(codes, sc)
+    y = x / sc[:, None]
+    assert np.abs(y).max() <= 448.0 * (1 + 2 ** -20)
+    rel = np.abs(xq - x) / np.maximum(np.abs(x), 2.0 ** -6 * sc[:, None])
+    assert rel.max() <= 2.0 ** -4 + 1e-7   # half an ulp of a 3-bit mantissa
