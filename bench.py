@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Benchmark of the LocalPower hot path on GB300.
+
+One "step" is one complete LocalPower solve of the FP32 workload (n = 1,000,000
+rows, d = 1,024, k = 16, m = 64 row partitions, p decaying 8 -> 4 -> 2 -> 1 over
+10 rounds each, sign-fixing, then a Rayleigh-Ritz pass): 40 aggregations, 150
+local power steps and one Ritz pass, each pass streaming all of A (4.1 GB) from
+HBM.  The metric is algorithmic GB/s of A streamed; solves/s and per-solve
+latency percentiles ride along.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank solves its own replica of the workload (the
+solves are independent problems: weak scaling, no data-path collective); the
+elapsed time is the maximum over ranks.  ``--impl reference`` times the FP64
+CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LocalPower GB/s & solves/s at dist≤1e-4 vs plain FP32 path; p50/p99 latency"
+WORKLOAD = "fp32"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--agg", choices=["sign", "opt"], default="sign")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload(rank: int):
+    import synth
+    c = synth.CONFIGS[WORKLOAD]
+    A, sizes, Y0 = synth.make_config_data(WORKLOAD)
+    return c, A, sizes, Y0, synth.config_schedule(WORKLOAD)
+
+
+def _oracle_sample_gbps(parts, Y0, passes: int):
+    """The FP64 oracle's local power step (eq. (2)) over every partition, `passes` times."""
+    import oracle
+    Z = oracle.orth(Y0)
+    nbytes = sum(p.nbytes for p in parts)
+    t = time.perf_counter()
+    for _ in range(passes):
+        for P in parts:
+            oracle.local_step(P, Z)
+    dt = time.perf_counter() - t
+    return passes * nbytes / dt / 1e9, dt
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    import synth
+    c, A, sizes, Y0, sched = _workload(0)
+    parts = synth.split_rows(A, sizes)
+    sample = parts[:16]
+    for _ in range(args.warmup):
+        _oracle_sample_gbps(sample, Y0, 1)
+    t = time.perf_counter()
+    vals = [_oracle_sample_gbps(sample, Y0, 1)[0] for _ in range(args.steps)]
+    dt = time.perf_counter() - t
+    bytes_step = sum(p.nbytes for p in sample)
+    value = args.steps * bytes_step / dt / 1e9
+    cores = os.cpu_count()
+    sample_txt = (f"each step: one FP64 oracle local power step (eq. (2)) over 16 of the 64 partitions "
+                  f"({bytes_step / 1e9:.2f} GB of FP32 A)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(c, sched),
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample_txt},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def _config(c, sched):
+    return {"workload": (f"LocalPower FP32: n={c['n']:,} d={c['d']} k={c['k']} m={c['m']}, p=8,4,2,1 x10 rounds "
+                         f"(T={len(sched)}, {sum(sched)} local steps) + Rayleigh-Ritz pass"),
+            "n": c["n"], "d": c["d"], "k": c["k"], "m": c["m"], "rounds": len(sched), "local_steps": sum(sched),
+            "l2": "inputs larger than L2 (A is 4.1 GB; L2 is 129 MB)"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    import synth
+    from paper_2002_08014_gb300 import binding as B
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    c, A, sizes, Y0, sched = _workload(rank)
+    parts = synth.split_rows(A, sizes)
+    k = c["k"]
+    stream = torch.cuda.Stream(device=dev)
+    lp = B.LocalPower(parts, device=local, stream=stream)
+
+    def one_solve():
+        lp.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
+        return lp.result(k)
+
+    for _ in range(args.warmup):
+        one_solve()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---------------- device-resident timed region
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats, Z, sig = [], None, None
+    for _ in range(args.steps):
+        Z, sig, st = one_solve()
+        stats.append(st)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    bytes_solve = stats[-1]["a_bytes"]
+    value = world * args.steps * bytes_solve / (ms / 1e3) / 1e9
+    lat = sorted(s["ms_solve"] for s in stats)
+    p50 = float(np.percentile(lat, 50))
+    p99 = float(np.percentile(lat, 99))
+    step_ms = sum(s["ms_step_kernels"] for s in stats) / sum(s["step_launches"] for s in stats)
+    launch_bytes = float(c["n"]) * c["d"] * 4
+    launch_flops = 4.0 * c["n"] * c["d"] * k
+    hbm_peak, sm_max_mhz, peak_src = _peaks()
+    achieved_gbs = launch_bytes / (step_ms / 1e3) / 1e9
+    achieved_tf = launch_flops / (step_ms / 1e3) / 1e12
+    alu_peak = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12      # FP32 FMA lanes x 2 flop x max SM clock
+
+    # ---------------- end to end through the public API, host buffers
+    pinned = torch.from_numpy(A).pin_memory()
+    host_parts = [t.numpy() for t in torch.split(pinned, sizes)]
+    e2e_ms = []
+    for it in range(args.e2e_steps + 1):
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.lp_load_partitions(lp.ctx, host_parts, "f32")
+        lp.submit(k, sched, args.agg, Y0, ritz=True)
+        Ze, _, _ = lp.result(k)
+        e1.record(stream)
+        barrier()
+        if it > 0:   # the first is a warm-up
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_t = max(e2e_ms) if world == 1 else None
+    if world > 1:
+        t = torch.tensor([max(e2e_ms)], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_val = world * bytes_solve / (e2e_t / 1e3) / 1e9
+    h2d = A.nbytes + Y0.nbytes
+    d2h = Ze.nbytes + 8 * k
+
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(c, sched),
+            "solves_per_s": world * args.steps / (ms / 1e3),
+            "latency_ms": {"p50": p50, "p99": p99, "samples": len(lat)},
+            "clocks": clk,
+            "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+            "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": e2e_t},
+            "roofline": {"kernel": "step_simt_kernel (fused A_i^T (A_i Z_i))", "bound": "alu",
+                         "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
+                         "traffic": None, "launch_ms": step_ms,
+                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz"},
+            "roofline_hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": achieved_gbs / hbm_peak, "peak_source": f"{peak_src} HBM copy bandwidth",
+                             "frac_of_nominal_8000": achieved_gbs / 8000.0}}
+
+    if rank == 0 and not args.no_accuracy:
+        Zo = oracle.orth(Z)
+        M = np.zeros((c["d"], c["d"]))
+        for i in range(0, len(parts), 8):
+            blk = np.concatenate(parts[i:i + 8]).astype(np.float64)
+            M += blk.T @ blk
+        lam, V = np.linalg.eigh(M / c["n"])
+        line["accuracy"] = {"dist_to_eigh_topk": oracle.subspace_dist(Zo, V[:, ::-1][:, :k]),
+                            "orthonormality": float(np.abs(Z.T @ Z - np.eye(k)).max()),
+                            "sigma_rel_err": float(np.max(np.abs(sig - np.sqrt(c["n"] * lam[::-1][:k]))
+                                                          / np.sqrt(c["n"] * lam[::-1][:k])))}
+    if rank == 0 and not args.no_cpu_baseline:
+        gbs, dt = _oracle_sample_gbps(parts, Y0, 3)
+        line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"3 FP64 oracle local power steps (eq. (2)) over all 64 partitions "
+                                          f"({dt:.1f} s)"}
+    lp.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

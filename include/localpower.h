@@ -1,0 +1,181 @@
+/*
+ * localpower.h -- C ABI of the GB300 LocalPower library.
+ *
+ * LocalPower (Li, Wang, Chen & Zhang, "Communication-Efficient Distributed SVD
+ * via Local Power Iterations", ICML 2021) computes the top-k right singular
+ * subspace of a row-partitioned matrix A = [A_1; ...; A_m] (Sec. 1, problem
+ * statement; Alg. 1).  Here the m partitions are device-resident row blocks of
+ * one GPU; a "communication round" of the paper is one on-device aggregation.
+ *
+ * Conventions shared by every call:
+ *   - Matrices are row-major.  A partition A_i is s_i x d with row pitch d
+ *     elements as given by the caller (the library repacks it internally).
+ *   - Pointers are plain host or device pointers, as the lp_ptr_space argument
+ *     says.  The library never keeps a caller pointer after a call returns.
+ *   - Every call returns an lp_status.  No call aborts, throws or exits; after a
+ *     non-OK status lp_last_error() describes the failure.  A failed call leaves
+ *     the context usable unless the status is LP_ERR_CUDA (device context lost).
+ *   - One context is used by one host thread at a time.  Distinct contexts may
+ *     share a device.
+ */
+#ifndef LOCALPOWER_H
+#define LOCALPOWER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LP_ABI_VERSION 1
+#define LP_MAX_K 32
+
+typedef enum lp_status {
+    LP_OK = 0,
+    LP_ERR_INVALID = 1,     /* bad argument; nothing was launched or allocated   */
+    LP_ERR_STATE = 2,       /* call out of order (e.g. solve before load)        */
+    LP_ERR_OOM = 3,         /* HBM budget or device memory exhausted             */
+    LP_ERR_CUDA = 4,        /* a CUDA runtime call failed                        */
+    LP_ERR_NUMERIC = 5,     /* Cholesky breakdown, non-finite data or iterate    */
+    LP_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up                */
+    LP_ERR_UNSUPPORTED = 7  /* valid request this build has no kernel for        */
+} lp_status;
+
+typedef enum lp_dtype {
+    LP_F32 = 0,             /* IEEE binary32                                      */
+    LP_BF16 = 1,            /* bfloat16 bit patterns (uint16)                     */
+    LP_FP8_E4M3 = 2         /* OCP FP8 E4M3 "FN" codes (uint8) x one FP32 scale per row */
+} lp_dtype;
+
+/* The aligning family F of the unified update rule (App. B): F = {I} gives vanilla
+ * averaging, F = diagonal +-1 matrices gives sign-fixing (eq. (4)), F = O_k gives
+ * the orthogonal Procrustes transformation (eq. (3)). */
+typedef enum lp_aggregator {
+    LP_AGG_IDENTITY = 0,
+    LP_AGG_SIGN = 1,
+    LP_AGG_OPT = 2
+} lp_aggregator;
+
+typedef enum lp_ptr_space { LP_HOST = 0, LP_DEVICE = 1 } lp_ptr_space;
+
+/* lp_solve flags */
+#define LP_FLAG_RITZ   1u   /* finish with a Rayleigh-Ritz step: ordered basis + sigma */
+#define LP_FLAG_TIMING 2u   /* record CUDA events around every fused power-step launch */
+
+typedef struct lp_ctx lp_ctx;
+
+typedef struct lp_stats {
+    int32_t rounds;            /* aggregations performed = the paper's |I_T|          */
+    int32_t local_steps;       /* sum of p_t (+1 for the Ritz pass)                   */
+    int32_t step_launches;     /* launches of the fused power-step kernel             */
+    int32_t k;
+    int64_t n, d;
+    int32_t m;
+    int32_t path;              /* 0 = SIMT FP32 step kernel, 1 = tcgen05 tensor-core step */
+    double a_bytes;            /* algorithmic bytes of A read by the step kernels     */
+    double ms_solve;           /* solve wall time on the stream (events)              */
+    double ms_step_kernels;    /* summed step-kernel time (LP_FLAG_TIMING only)       */
+    int32_t kernel_launches;   /* every kernel this solve launched                    */
+    int32_t reserved;
+} lp_stats;
+
+/*
+ * lp_create: open a context on `device`.
+ *   hbm_budget_bytes: upper bound on device memory this context may allocate
+ *                     (0 = no bound beyond what the device has).  Requests over
+ *                     it fail with LP_ERR_OOM and allocate nothing.
+ *   cuda_stream:      a cudaStream_t the context launches on (borrowed, must
+ *                     outlive the context); NULL makes the context own a stream.
+ * Ownership: *out belongs to the caller and is released with lp_destroy.
+ */
+lp_status lp_create(lp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
+
+/*
+ * lp_load_partitions: copy the m row partitions A_i into library-owned device
+ * memory (Sec. 2, DPI: A^T = [A_1^T, ..., A_m^T], A_i in R^{s_i x d}; the
+ * weights are p_i = s_i / n with n = sum s_i).
+ *   rows[m]        s_i >= 1.
+ *   d              columns, d >= 1.
+ *   parts[m]       pointer to partition i, s_i x d row-major, elements of `dtype`.
+ *   row_scales[m]  LP_FP8_E4M3 only: s_i FP32 scales (value = code * scale); else NULL.
+ *   space          whether parts / row_scales are host or device pointers.
+ * Replaces any previously loaded partitions.  The caller keeps its buffers.
+ */
+lp_status lp_load_partitions(lp_ctx* ctx, int m, const int64_t* rows, int64_t d, lp_dtype dtype,
+                             const void* const* parts, const float* const* row_scales, lp_ptr_space space);
+
+/*
+ * lp_solve: run LocalPower (Alg. 1 with the aggregation of eqs. (3)-(4)) on the
+ * loaded partitions.  Round t runs p_schedule[t] local power steps per
+ * partition, Y_i <- (1/s_i) A_i^T (A_i Z_i) each followed (except the last) by
+ * Z_i <- orth(Y_i), then one aggregation Y <- sum_i p_i Y_i D_i and Z <- orth(Y).
+ * D_i = I whenever p_t = 1 (the remark after eq. (4)).  The base partition for
+ * alignment is the one with the most rows (lowest index on ties).
+ *   k              target rank, 1 <= k <= min(LP_MAX_K, d, min_i s_i).
+ *   p_schedule[T]  p_t >= 1 (a decaying p is just a schedule, Sec. 3).
+ *   y0             host pointer, d x k row-major FP64: the Gaussian start block
+ *                  Y_0 (Alg. 1 initialisation); the library computes Z_0 = orth(Y_0).
+ *   refine_rounds  extra p = 1 rounds appended after the schedule.
+ *   flags          LP_FLAG_*.
+ * Asynchronous on the context's stream; lp_result waits for it.
+ */
+lp_status lp_solve(lp_ctx* ctx, int k, const int* p_schedule, int T, lp_aggregator agg,
+                   const double* y0, int refine_rounds, unsigned flags);
+
+/*
+ * lp_result: wait for the last solve and copy its output to host memory.
+ *   z_out      d x k row-major FP64: Z_T = orth(Y_T) (Alg. 1 output), or with
+ *              LP_FLAG_RITZ the Ritz vectors ordered by descending Ritz value.
+ *              The basis is defined up to the sign of each column.  May be NULL.
+ *   sigma_out  k values sqrt(n * lambda_j) (LP_FLAG_RITZ only; else zeros).  May be NULL.
+ *   stats      may be NULL.
+ * Returns LP_ERR_NUMERIC if a device-side check failed during the solve.
+ */
+lp_status lp_result(lp_ctx* ctx, double* z_out, double* sigma_out, lp_stats* stats);
+
+/* lp_destroy: free everything the context owns; NULL is a no-op. */
+void lp_destroy(lp_ctx* ctx);
+
+/* lp_last_error: text of the last failure on this context ("" if none); valid
+ * until the next call on the context.  With ctx == NULL: the last lp_create failure. */
+const char* lp_last_error(const lp_ctx* ctx);
+
+/* ----------------------------------------------------------------------------
+ * Single-kernel entry points, for checking one step of the method at a time.
+ * They run on the context's stream and synchronise before returning.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * lp_power_step: one local power step for every loaded partition,
+ * Y_i = (1/s_i) A_i^T (A_i Z_i) (eq. (2)).
+ *   z      FP64 row-major; if z_shared, one d x k block used by every partition,
+ *          else m consecutive d x k blocks (Z_1, ..., Z_m).
+ *   y_out  m consecutive d x k FP64 blocks.
+ *   space  where z and y_out live.
+ */
+lp_status lp_power_step(lp_ctx* ctx, int k, const double* z, int z_shared, double* y_out, lp_ptr_space space);
+
+/*
+ * lp_orth: Z_b = orth(Y_b) for a batch of `batch` d x k blocks (CholQR2: two
+ * passes of Gram, Cholesky and triangular solve; eq. (1)'s orth, whose column
+ * space is that of a Householder QR).  FP64 row-major in and out (`space`).
+ * A block whose Gram matrix is not numerically positive definite yields
+ * LP_ERR_NUMERIC.
+ */
+lp_status lp_orth(lp_ctx* ctx, int batch, int64_t d, int k, const double* y, double* z, lp_ptr_space space);
+
+/*
+ * lp_align_aggregate: Y = sum_i w_i Y_i D_i with D_b = I and D_i from `agg`
+ * computed between Z_i and Z_b (eqs. (3)-(4); Alg. 1 aggregation).
+ *   ys, zs   m consecutive d x k FP64 blocks each; w: m weights; base: b.
+ *   y_out    d x k FP64; d_out (may be NULL) m consecutive k x k FP64 D_i.
+ */
+lp_status lp_align_aggregate(lp_ctx* ctx, int m, int64_t d, int k, lp_aggregator agg, int base,
+                             const double* w, const double* ys, const double* zs,
+                             double* y_out, double* d_out, lp_ptr_space space);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOCALPOWER_H */

@@ -1,0 +1,277 @@
+"""Python binding of the LocalPower C ABI (include/localpower.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Host data are NumPy arrays (pointer space LP_HOST); device data are CUDA
+torch tensors (LP_DEVICE, via ``data_ptr()``), torch being used only as a
+holder of device memory and streams.  The functions keep the C names.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+LP_OK, LP_ERR_INVALID, LP_ERR_STATE, LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_NUMERIC, LP_ERR_TIMEOUT, LP_ERR_UNSUPPORTED = range(8)
+STATUS_NAMES = ["LP_OK", "LP_ERR_INVALID", "LP_ERR_STATE", "LP_ERR_OOM", "LP_ERR_CUDA", "LP_ERR_NUMERIC",
+                "LP_ERR_TIMEOUT", "LP_ERR_UNSUPPORTED"]
+LP_F32, LP_BF16, LP_FP8_E4M3 = 0, 1, 2
+LP_AGG_IDENTITY, LP_AGG_SIGN, LP_AGG_OPT = 0, 1, 2
+LP_HOST, LP_DEVICE = 0, 1
+LP_FLAG_RITZ, LP_FLAG_TIMING = 1, 2
+LP_MAX_K = 32
+
+AGG = {"identity": LP_AGG_IDENTITY, "sign": LP_AGG_SIGN, "opt": LP_AGG_OPT}
+DTYPE = {"f32": LP_F32, "bf16": LP_BF16, "e4m3": LP_FP8_E4M3}
+
+# Every symbol the header declares, in declaration order.
+EXPORTS = ["lp_create", "lp_load_partitions", "lp_solve", "lp_result", "lp_destroy", "lp_last_error",
+           "lp_power_step", "lp_orth", "lp_align_aggregate"]
+
+
+class lp_stats(C.Structure):
+    _fields_ = [("rounds", C.c_int32), ("local_steps", C.c_int32), ("step_launches", C.c_int32), ("k", C.c_int32),
+                ("n", C.c_int64), ("d", C.c_int64), ("m", C.c_int32), ("path", C.c_int32),
+                ("a_bytes", C.c_double), ("ms_solve", C.c_double), ("ms_step_kernels", C.c_double),
+                ("kernel_launches", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class LPError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {message}")
+
+
+_lib: C.CDLL | None = None
+
+
+def lib_path() -> str:
+    from . import build
+    return build.LIB_PATH
+
+
+def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
+    """Load the shared library (building it first if it is absent).  Raises if
+    it cannot be built or loaded: there is no fallback path."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        from . import build
+        path = build.build() if build_if_missing else build.LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"LocalPower CUDA library not found at {path}")
+    L = C.CDLL(path)
+    P, I, I64, U = C.c_void_p, C.c_int, C.c_int64, C.c_uint
+    L.lp_create.argtypes = [C.POINTER(P), I, C.c_size_t, P]
+    L.lp_load_partitions.argtypes = [P, I, C.POINTER(I64), I64, I, C.POINTER(P), C.POINTER(P), I]
+    L.lp_solve.argtypes = [P, I, C.POINTER(I), I, I, P, I, U]
+    L.lp_result.argtypes = [P, P, P, C.POINTER(lp_stats)]
+    L.lp_destroy.argtypes = [P]
+    L.lp_destroy.restype = None
+    L.lp_last_error.argtypes = [P]
+    L.lp_last_error.restype = C.c_char_p
+    L.lp_power_step.argtypes = [P, I, P, I, P, I]
+    L.lp_orth.argtypes = [P, I, I64, I, P, P, I]
+    L.lp_align_aggregate.argtypes = [P, I, I64, I, I, I, P, P, P, P, P, I]
+    for name in EXPORTS:
+        if name not in ("lp_destroy", "lp_last_error"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(ctx, status: int):
+    if status != LP_OK:
+        msg = load().lp_last_error(ctx).decode(errors="replace")
+        raise LPError(status, msg)
+
+
+# --------------------------------------------------------------------------- marshalling
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype=None):
+    """(pointer, space, keepalive) for a NumPy array or a CUDA torch tensor."""
+    if _is_torch(x):
+        if not x.is_cuda:
+            x = x.numpy()
+        else:
+            if not x.is_contiguous():
+                raise ValueError("device tensors must be contiguous")
+            return C.c_void_p(x.data_ptr()), LP_DEVICE, x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return C.c_void_p(a.ctypes.data), LP_HOST, a
+
+
+def lp_create(device: int = 0, hbm_budget_bytes: int = 0, stream=None):
+    """Open a context; returns an opaque handle (c_void_p)."""
+    L = load()
+    ctx = C.c_void_p()
+    s = C.c_void_p(stream.cuda_stream) if stream is not None and hasattr(stream, "cuda_stream") else C.c_void_p(stream)
+    _check(None, L.lp_create(C.byref(ctx), device, hbm_budget_bytes, s))
+    return ctx
+
+
+def lp_destroy(ctx) -> None:
+    load().lp_destroy(ctx)
+
+
+def lp_last_error(ctx=None) -> str:
+    return load().lp_last_error(ctx).decode(errors="replace")
+
+
+def lp_load_partitions(ctx, parts, dtype: str = "f32", row_scales=None) -> None:
+    """parts: list of s_i x d arrays (float32, or uint16 BF16 bits, or uint8 E4M3
+    codes) all on the host or all on the device; row_scales: list of float32
+    arrays (E4M3 only)."""
+    L = load()
+    m = len(parts)
+    np_dt = {"f32": np.float32, "bf16": np.uint16, "e4m3": np.uint8}[dtype]
+    ptrs, keep, spaces = [], [], set()
+    for p in parts:
+        q, sp, k = _ptr(p, np_dt)
+        ptrs.append(q.value)
+        keep.append(k)
+        spaces.add(sp)
+    if len(spaces) != 1:
+        raise ValueError("partitions must all be host or all device")
+    space = spaces.pop()
+    rows = (C.c_int64 * m)(*[int(p.shape[0]) for p in parts])
+    d = int(parts[0].shape[1])
+    arr = (C.c_void_p * m)(*ptrs)
+    sarr = None
+    if row_scales is not None:
+        sp_list = []
+        for s in row_scales:
+            q, sp, k = _ptr(s, np.float32)
+            if sp != space:
+                raise ValueError("row scales must live where the partitions do")
+            sp_list.append(q.value)
+            keep.append(k)
+        sarr = (C.c_void_p * m)(*sp_list)
+    _check(ctx, L.lp_load_partitions(ctx, m, rows, d, DTYPE[dtype], arr, sarr, space))
+
+
+def lp_solve(ctx, k: int, p_schedule, agg: str, y0: np.ndarray, refine_rounds: int = 0, flags: int = 0) -> None:
+    L = load()
+    sched = np.ascontiguousarray(np.asarray(p_schedule, dtype=np.int32))
+    T = int(sched.shape[0])
+    y0c = np.ascontiguousarray(y0, dtype=np.float64)
+    _check(ctx, L.lp_solve(ctx, int(k), sched.ctypes.data_as(C.POINTER(C.c_int)) if T else None, T, AGG[agg],
+                           C.c_void_p(y0c.ctypes.data), int(refine_rounds), int(flags)))
+
+
+def lp_result(ctx, d: int, k: int):
+    """(Z d x k FP64, sigma k FP64, stats dict)."""
+    L = load()
+    Z = np.empty((d, k), dtype=np.float64)
+    sig = np.empty(k, dtype=np.float64)
+    st = lp_stats()
+    status = L.lp_result(ctx, C.c_void_p(Z.ctypes.data), C.c_void_p(sig.ctypes.data), C.byref(st))
+    _check(ctx, status)
+    return Z, sig, st.as_dict()
+
+
+def lp_power_step(ctx, k: int, z, z_shared: bool, m: int, d: int, out=None):
+    """Y_i = M_i Z_i for every loaded partition; returns (m, d, k) FP64 (NumPy,
+    or the given device tensor ``out``)."""
+    L = load()
+    zp, zsp, keep = _ptr(z, np.float64)
+    if out is None:
+        if zsp == LP_DEVICE:
+            import torch
+            out = torch.empty((m, d, k), dtype=torch.float64, device=z.device)
+        else:
+            out = np.empty((m, d, k), dtype=np.float64)
+    yp, ysp, keep2 = _ptr(out, np.float64)
+    if ysp != zsp:
+        raise ValueError("z and out must share a pointer space")
+    _check(ctx, L.lp_power_step(ctx, int(k), zp, 1 if z_shared else 0, yp, zsp))
+    return out
+
+
+def lp_orth(ctx, Y):
+    """Z_b = orth(Y_b) for a (batch, d, k) FP64 array (host) or tensor (device)."""
+    L = load()
+    b, d, k = Y.shape
+    yp, sp, keep = _ptr(Y, np.float64)
+    if sp == LP_DEVICE:
+        import torch
+        Z = torch.empty_like(Y)
+    else:
+        Z = np.empty((b, d, k), dtype=np.float64)
+    zp, _, keep2 = _ptr(Z, np.float64)
+    _check(ctx, L.lp_orth(ctx, int(b), int(d), int(k), yp, zp, sp))
+    return Z
+
+
+def lp_align_aggregate(ctx, agg: str, base: int, w, Ys, Zs):
+    """(Y d x k, D (m, k, k)) for host FP64 inputs Ys, Zs of shape (m, d, k)."""
+    L = load()
+    m, d, k = Ys.shape
+    Ys = np.ascontiguousarray(Ys, dtype=np.float64)
+    Zs = np.ascontiguousarray(Zs, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    Y = np.empty((d, k), dtype=np.float64)
+    D = np.empty((m, k, k), dtype=np.float64)
+    _check(ctx, L.lp_align_aggregate(ctx, int(m), int(d), int(k), AGG[agg], int(base), C.c_void_p(w.ctypes.data),
+                                     C.c_void_p(Ys.ctypes.data), C.c_void_p(Zs.ctypes.data),
+                                     C.c_void_p(Y.ctypes.data), C.c_void_p(D.ctypes.data), LP_HOST))
+    return Y, D
+
+
+# --------------------------------------------------------------------------- convenience
+
+class LocalPower:
+    """A context with loaded partitions: ``LocalPower(parts).solve(k, schedule, agg, y0)``."""
+
+    def __init__(self, parts, dtype: str = "f32", row_scales=None, device: int = 0, hbm_budget_bytes: int = 0,
+                 stream=None):
+        self.ctx = lp_create(device, hbm_budget_bytes, stream)
+        try:
+            lp_load_partitions(self.ctx, parts, dtype, row_scales)
+        except Exception:
+            lp_destroy(self.ctx)
+            self.ctx = None
+            raise
+        self.m = len(parts)
+        self.d = int(parts[0].shape[1])
+        self.sizes = [int(p.shape[0]) for p in parts]
+
+    def solve(self, k: int, schedule, agg: str, y0, refine_rounds: int = 0, ritz: bool = False, timing: bool = False):
+        flags = (LP_FLAG_RITZ if ritz else 0) | (LP_FLAG_TIMING if timing else 0)
+        lp_solve(self.ctx, k, schedule, agg, y0, refine_rounds, flags)
+        return lp_result(self.ctx, self.d, k)
+
+    def submit(self, k: int, schedule, agg: str, y0, refine_rounds: int = 0, ritz: bool = False, timing: bool = False):
+        flags = (LP_FLAG_RITZ if ritz else 0) | (LP_FLAG_TIMING if timing else 0)
+        lp_solve(self.ctx, k, schedule, agg, y0, refine_rounds, flags)
+
+    def result(self, k: int):
+        return lp_result(self.ctx, self.d, k)
+
+    def power_step(self, k: int, z, shared: bool = True):
+        return lp_power_step(self.ctx, k, z, shared, self.m, self.d)
+
+    def close(self) -> None:
+        if self.ctx is not None:
+            lp_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,691 @@
+// C ABI and round scheduler of the LocalPower library.
+//
+// The host side drives Alg. 1 round by round on one CUDA stream:
+//   round start   Z = orth(Y)                          (cholqr2, batch 1)
+//   local steps   Z_i = orth(Y_i) (j > 1, batch m)      (cholqr2)
+//                 P = A^T (A Z_i) per row segment       (fused step kernel)
+//                 Y_i = (1/s_i) sum of P over i's slots (reduce)
+//   aggregation   D_i (sign / OPT, skipped when p_t = 1) then Y = sum_i p_i Y_i D_i
+//   output        Z_T = orth(Y), optionally Rayleigh-Ritz
+// Device state is FP32 d x K blocks (K = k rounded up to 8, 16 or 32, padding
+// columns zero); the k x k factorisations run in FP64 inside the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lp_internal.cuh"
+
+using lp::Segment;
+
+struct lp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;
+  size_t used = 0;
+  int sms = 0;
+  std::string err;
+
+  // partitions
+  int m = 0;
+  int64_t d = 0, ld = 0, n = 0;
+  lp_dtype dtype = LP_F32;
+  std::vector<int64_t> rows, row_off;
+  void* dA = nullptr;
+  size_t dA_bytes = 0;
+  float* dScales = nullptr;
+  int base = 0;
+
+  // step-kernel schedule
+  int grid = 0;
+  int nslots = 0;
+  Segment* dSegs = nullptr;
+  int* dSegPtr = nullptr;
+  int* dSlotBegin = nullptr;
+  float* dInvS = nullptr;
+  float* dW = nullptr;
+
+  // solve state (capacity in K)
+  int Kcap = 0;
+  float *dP = nullptr, *dYl = nullptr, *dZl = nullptr, *dY = nullptr, *dZ = nullptr, *dG = nullptr, *dMZ = nullptr;
+  double *dZout = nullptr, *dSigma = nullptr, *dStage = nullptr;
+  size_t stage_bytes = 0;
+  int* dStatus = nullptr;
+
+  // last solve
+  bool solved = false;
+  int k = 0;
+  bool ritz = false;
+  lp_stats stats{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> step_ev;
+  int step_ev_used = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+lp_status fail(lp_ctx* c, lp_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_err = msg;
+  return st;
+}
+
+lp_status cuda_fail(lp_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, LP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LP_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+  } while (0)
+
+// Device allocation against the context's budget.  Nothing is allocated on failure.
+template <typename T>
+lp_status dalloc(lp_ctx* c, T** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) / 256 * 256;
+  if (c->budget && c->used + bytes > c->budget)
+    return fail(c, LP_ERR_OOM, "HBM budget exceeded: need " + std::to_string(bytes) + " more bytes, budget " +
+                                   std::to_string(c->budget) + ", in use " + std::to_string(c->used));
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(c, LP_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " +
+                                   cudaGetErrorString(e));
+  }
+  c->used += bytes;
+  *p = static_cast<T*>(q);
+  return LP_OK;
+}
+
+template <typename T>
+void dfree(lp_ctx* c, T*& p, size_t bytes) {
+  if (p) {
+    cudaFree(p);
+    if (bytes == 0) bytes = 16;
+    c->used -= (bytes + 255) / 256 * 256;
+    p = nullptr;
+  }
+}
+
+int kcap_of(int k) { return k <= 8 ? 8 : (k <= 16 ? 16 : 32); }
+size_t elem_bytes(lp_dtype t) { return t == LP_F32 ? 4 : (t == LP_BF16 ? 2 : 1); }
+
+struct StateSizes {
+  size_t P, Yl, Y, G, stage;
+};
+StateSizes state_sizes(const lp_ctx* c, int K) {
+  StateSizes s;
+  s.P = size_t(c->nslots) * c->d * K * 4;
+  s.Yl = size_t(c->m) * c->d * K * 4;
+  s.Y = size_t(c->d) * K * 4;
+  s.G = size_t(c->m) * K * K * 4;
+  s.stage = size_t(c->m) * c->d * K * 8;
+  return s;
+}
+
+void free_state(lp_ctx* c) {
+  if (!c->Kcap) return;
+  StateSizes s = state_sizes(c, c->Kcap);
+  dfree(c, c->dP, s.P);
+  dfree(c, c->dYl, s.Yl);
+  dfree(c, c->dZl, s.Yl);
+  dfree(c, c->dY, s.Y);
+  dfree(c, c->dZ, s.Y);
+  dfree(c, c->dMZ, s.Y);
+  dfree(c, c->dG, s.G);
+  dfree(c, c->dZout, size_t(c->d) * LP_MAX_K * 8);
+  dfree(c, c->dSigma, LP_MAX_K * 8);
+  dfree(c, c->dStage, c->stage_bytes);
+  c->stage_bytes = 0;
+  c->Kcap = 0;
+}
+
+lp_status ensure_state(lp_ctx* c, int K) {
+  if (c->Kcap >= K) return LP_OK;
+  free_state(c);
+  StateSizes s = state_sizes(c, K);
+  lp_status st;
+  if ((st = dalloc(c, &c->dP, s.P)) || (st = dalloc(c, &c->dYl, s.Yl)) || (st = dalloc(c, &c->dZl, s.Yl)) ||
+      (st = dalloc(c, &c->dY, s.Y)) || (st = dalloc(c, &c->dZ, s.Y)) || (st = dalloc(c, &c->dMZ, s.Y)) ||
+      (st = dalloc(c, &c->dG, s.G)) || (st = dalloc(c, &c->dZout, size_t(c->d) * LP_MAX_K * 8)) ||
+      (st = dalloc(c, &c->dSigma, LP_MAX_K * 8)) || (st = dalloc(c, &c->dStage, s.stage))) {
+    c->Kcap = K;  // free what was allocated
+    free_state(c);
+    return st;
+  }
+  c->stage_bytes = s.stage;
+  c->Kcap = K;
+  return LP_OK;
+}
+
+void free_partitions(lp_ctx* c) {
+  dfree(c, c->dA, c->dA_bytes);
+  dfree(c, c->dScales, size_t(c->n) * 4);
+  dfree(c, c->dSegs, (size_t(c->grid) + c->m) * sizeof(Segment));
+  dfree(c, c->dSegPtr, (size_t(c->grid) + 1) * 4);
+  dfree(c, c->dSlotBegin, (size_t(c->m) + 1) * 4);
+  dfree(c, c->dInvS, size_t(c->m) * 4);
+  dfree(c, c->dW, size_t(c->m) * 4);
+  free_state(c);
+  c->m = 0;
+  c->n = 0;
+  c->dA_bytes = 0;
+  c->solved = false;
+}
+
+// Copy a d x k (or batch of) FP64 array from `space` to the device staging buffer.
+lp_status stage_in(lp_ctx* c, const double* src, size_t count, lp_ptr_space space, const double** dev) {
+  if (space == LP_DEVICE) {
+    *dev = src;
+    return LP_OK;
+  }
+  if (count * 8 > c->stage_bytes) return fail(c, LP_ERR_INVALID, "staging buffer too small");
+  LP_CUDA(cudaMemcpyAsync(c->dStage, src, count * 8, cudaMemcpyHostToDevice, c->stream));
+  *dev = c->dStage;
+  return LP_OK;
+}
+
+lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool timing) {
+  lp::StepArgs a;
+  a.A = c->dA;
+  a.ld = c->ld;
+  a.d = static_cast<int>(c->d);
+  a.scales = c->dScales;
+  a.segs = c->dSegs;
+  a.seg_ptr = c->dSegPtr;
+  a.Z = Z;
+  a.z_stride = z_stride;
+  a.P = c->dP;
+  a.grid = c->grid;
+  if (timing) {
+    const size_t need = size_t(c->step_ev_used) + 2;
+    while (c->step_ev.size() < need) {
+      cudaEvent_t e;
+      LP_CUDA(cudaEventCreate(&e));
+      c->step_ev.push_back(e);
+    }
+    LP_CUDA(cudaEventRecord(c->step_ev[c->step_ev_used], c->stream));
+  }
+  cudaError_t e = lp::launch_step_simt(a, c->dtype, K, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fused power-step launch");
+  if (timing) {
+    LP_CUDA(cudaEventRecord(c->step_ev[c->step_ev_used + 1], c->stream));
+    c->step_ev_used += 2;
+  }
+  c->stats.step_launches++;
+  c->stats.kernel_launches++;
+  c->stats.a_bytes += double(c->n) * double(c->d) * double(elem_bytes(c->dtype)) +
+                      (c->dtype == LP_FP8_E4M3 ? 4.0 * double(c->n) : 0.0);
+  return LP_OK;
+}
+
+lp_status check_launch(lp_ctx* c, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return cuda_fail(c, e, what);
+  c->stats.kernel_launches++;
+  return LP_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+lp_status lp_create(lp_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
+  if (!out) return fail(nullptr, LP_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    (void)cudaGetLastError();
+    return fail(nullptr, LP_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  if (device < 0 || device >= ndev) return fail(nullptr, LP_ERR_INVALID, "device index out of range");
+  lp_ctx* c = new (std::nothrow) lp_ctx();
+  if (!c) return fail(nullptr, LP_ERR_OOM, "host allocation failed");
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) {
+    if (cuda_stream) {
+      c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+      c->own_stream = e == cudaSuccess;
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e == cudaSuccess && dalloc(c, &c->dStatus, 16) != LP_OK) e = cudaErrorMemoryAllocation;
+  if (e != cudaSuccess) {
+    std::string msg = std::string("context setup failed: ") + cudaGetErrorString(e);
+    lp_destroy(c);
+    return fail(nullptr, LP_ERR_CUDA, msg);
+  }
+  *out = c;
+  return LP_OK;
+}
+
+void lp_destroy(lp_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_partitions(c);
+  dfree(c, c->dStatus, 16);
+  for (cudaEvent_t e : c->step_ev) cudaEventDestroy(e);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* lp_last_error(const lp_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, lp_dtype dtype,
+                             const void* const* parts, const float* const* row_scales, lp_ptr_space space) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  if (m < 1 || !rows || !parts) return fail(c, LP_ERR_INVALID, "need m >= 1 and non-NULL rows/parts");
+  if (d < 1 || d > (1 << 20)) return fail(c, LP_ERR_INVALID, "d out of range");
+  if (dtype != LP_F32 && dtype != LP_BF16 && dtype != LP_FP8_E4M3) return fail(c, LP_ERR_INVALID, "unknown dtype");
+  if (space != LP_HOST && space != LP_DEVICE) return fail(c, LP_ERR_INVALID, "unknown pointer space");
+  if (dtype == LP_FP8_E4M3 && !row_scales) return fail(c, LP_ERR_INVALID, "FP8 partitions need row_scales");
+  int64_t n = 0;
+  for (int i = 0; i < m; ++i) {
+    if (rows[i] < 1) return fail(c, LP_ERR_INVALID, "partition " + std::to_string(i) + " has no rows");
+    if (!parts[i]) return fail(c, LP_ERR_INVALID, "partition " + std::to_string(i) + " pointer is NULL");
+    if (dtype == LP_FP8_E4M3 && !row_scales[i])
+      return fail(c, LP_ERR_INVALID, "partition " + std::to_string(i) + " scales pointer is NULL");
+    n += rows[i];
+  }
+  LP_CUDA(cudaSetDevice(c->device));
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  free_partitions(c);
+
+  const size_t eb = elem_bytes(dtype);
+  const int64_t per16 = 16 / static_cast<int64_t>(eb);
+  c->m = m;
+  c->d = d;
+  c->ld = (d + per16 - 1) / per16 * per16;
+  c->n = n;
+  c->dtype = dtype;
+  c->rows.assign(rows, rows + m);
+  c->row_off.resize(m);
+  int64_t o = 0;
+  for (int i = 0; i < m; ++i) {
+    c->row_off[i] = o;
+    o += rows[i];
+  }
+  c->base = static_cast<int>(std::max_element(c->rows.begin(), c->rows.end()) - c->rows.begin());
+
+  // Row segments: CTA g owns global rows [g n / G, (g+1) n / G), cut at partition ends.
+  const int64_t min_rows = 32;
+  c->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->sms, n / min_rows)));
+  std::vector<Segment> segs;
+  std::vector<int> seg_ptr(c->grid + 1, 0);
+  std::vector<int> slot_begin(m + 1, 0);
+  int part = 0;
+  for (int g = 0; g < c->grid; ++g) {
+    seg_ptr[g] = static_cast<int>(segs.size());
+    int64_t r0 = n * g / c->grid, r1 = n * (g + 1) / c->grid;
+    while (r0 < r1) {
+      while (c->row_off[part] + c->rows[part] <= r0) ++part;
+      const int64_t pend = c->row_off[part] + c->rows[part];
+      const int64_t e = std::min(r1, pend);
+      Segment s;
+      s.row0 = r0;
+      s.row1 = e;
+      s.part = part;
+      s.slot = static_cast<int>(segs.size());
+      segs.push_back(s);
+      r0 = e;
+    }
+  }
+  seg_ptr[c->grid] = static_cast<int>(segs.size());
+  c->nslots = static_cast<int>(segs.size());
+  {
+    int s = 0;
+    for (int i = 0; i < m; ++i) {
+      while (s < c->nslots && segs[s].part < i) ++s;
+      slot_begin[i] = s;
+    }
+    slot_begin[m] = c->nslots;
+  }
+  std::vector<float> invs(m), w(m);
+  for (int i = 0; i < m; ++i) {
+    invs[i] = static_cast<float>(1.0 / double(rows[i]));
+    w[i] = static_cast<float>(double(rows[i]) / double(n));
+  }
+
+  c->dA_bytes = size_t(n) * size_t(c->ld) * eb;
+  lp_status st;
+  if ((st = dalloc(c, &c->dA, c->dA_bytes)) ||
+      (dtype == LP_FP8_E4M3 && (st = dalloc(c, &c->dScales, size_t(n) * 4))) ||
+      (st = dalloc(c, &c->dSegs, (size_t(c->grid) + m) * sizeof(Segment))) ||
+      (st = dalloc(c, &c->dSegPtr, (size_t(c->grid) + 1) * 4)) ||
+      (st = dalloc(c, &c->dSlotBegin, (size_t(m) + 1) * 4)) || (st = dalloc(c, &c->dInvS, size_t(m) * 4)) ||
+      (st = dalloc(c, &c->dW, size_t(m) * 4))) {
+    std::string msg = c->err;
+    free_partitions(c);
+    c->err = msg;
+    return st;
+  }
+  const cudaMemcpyKind kind = space == LP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (c->ld != d) LP_CUDA(cudaMemsetAsync(c->dA, 0, c->dA_bytes, c->stream));
+  for (int i = 0; i < m; ++i) {
+    char* dst = static_cast<char*>(c->dA) + size_t(c->row_off[i]) * c->ld * eb;
+    LP_CUDA(cudaMemcpy2DAsync(dst, size_t(c->ld) * eb, parts[i], size_t(d) * eb, size_t(d) * eb, size_t(rows[i]), kind,
+                              c->stream));
+    if (dtype == LP_FP8_E4M3)
+      LP_CUDA(cudaMemcpyAsync(c->dScales + c->row_off[i], row_scales[i], size_t(rows[i]) * 4, kind, c->stream));
+  }
+  LP_CUDA(cudaMemcpyAsync(c->dSegs, segs.data(), segs.size() * sizeof(Segment), cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dSegPtr, seg_ptr.data(), seg_ptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dSlotBegin, slot_begin.data(), slot_begin.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dInvS, invs.data(), m * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dW, w.data(), m * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  return LP_OK;
+}
+
+static lp_status validate_k(lp_ctx* c, int k) {
+  if (c->m == 0) return fail(c, LP_ERR_STATE, "no partitions loaded");
+  if (k < 1 || k > LP_MAX_K) return fail(c, LP_ERR_INVALID, "k must be in [1, 32]");
+  if (k > c->d) return fail(c, LP_ERR_INVALID, "k exceeds d");
+  const int64_t smin = *std::min_element(c->rows.begin(), c->rows.end());
+  if (k > smin)
+    return fail(c, LP_ERR_INVALID, "k exceeds the smallest partition's row count (its local Y_i would be rank deficient)");
+  const int K = kcap_of(k);
+  if (lp::step_simt_smem(static_cast<int>(c->d), c->ld, c->dtype, K, nullptr) == 0)
+    return fail(c, LP_ERR_UNSUPPORTED, "no step kernel for d=" + std::to_string(c->d) + ", k=" + std::to_string(k));
+  return LP_OK;
+}
+
+lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, const double* y0,
+                   int refine_rounds, unsigned flags) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  lp_status st = validate_k(c, k);
+  if (st) return st;
+  if (T < 0 || refine_rounds < 0 || T + refine_rounds < 1)
+    return fail(c, LP_ERR_INVALID, "need T >= 0, refine_rounds >= 0 and at least one round");
+  if (T > 0 && !p_schedule) return fail(c, LP_ERR_INVALID, "p_schedule is NULL");
+  for (int t = 0; t < T; ++t)
+    if (p_schedule[t] < 1) return fail(c, LP_ERR_INVALID, "p_schedule entries must be >= 1");
+  if (agg != LP_AGG_IDENTITY && agg != LP_AGG_SIGN && agg != LP_AGG_OPT)
+    return fail(c, LP_ERR_INVALID, "unknown aggregator");
+  if (!y0) return fail(c, LP_ERR_INVALID, "y0 is NULL");
+  LP_CUDA(cudaSetDevice(c->device));
+  const int K = kcap_of(k);
+  if ((st = ensure_state(c, K))) return st;
+
+  const int d = static_cast<int>(c->d);
+  const int m = c->m;
+  const bool timing = (flags & LP_FLAG_TIMING) != 0;
+  c->solved = false;
+  c->k = k;
+  c->ritz = (flags & LP_FLAG_RITZ) != 0;
+  std::memset(&c->stats, 0, sizeof(c->stats));
+  c->step_ev_used = 0;
+
+  LP_CUDA(cudaMemsetAsync(c->dStatus, 0, 4, c->stream));
+  LP_CUDA(cudaEventRecord(c->ev0, c->stream));
+  const double* dy0;
+  if ((st = stage_in(c, y0, size_t(d) * k, LP_HOST, &dy0))) return st;
+  if ((st = check_launch(c, lp::launch_pack(dy0, c->dY, 1, d, k, K, c->stream), "pack"))) return st;
+  if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream), "orth"))) return st;
+
+  const int rounds = T + refine_rounds;
+  const int64_t zs = int64_t(d) * K;
+  for (int t = 0; t < rounds; ++t) {
+    const int p = t < T ? p_schedule[t] : 1;
+    for (int j = 0; j < p; ++j) {
+      if (j > 0 && (st = check_launch(c, lp::launch_cholqr2(c->dYl, c->dZl, m, d, k, K, c->dStatus, c->stream),
+                                      "local orth")))
+        return st;
+      if ((st = launch_step(c, K, j == 0 ? c->dZ : c->dZl, j == 0 ? 0 : zs, timing))) return st;
+      if ((st = check_launch(c, lp::launch_reduce(c->dP, c->dSlotBegin, c->dInvS, m, d, K, c->dYl, c->stream),
+                             "reduce")))
+        return st;
+      c->stats.local_steps++;
+    }
+    const bool align = p > 1 && agg != LP_AGG_IDENTITY;
+    if (align) {
+      // The last basis each partition multiplied this round is Z_i (orth of its previous Y_i).
+      if ((st = check_launch(c, lp::launch_align(c->dZl, zs, c->dZl + zs * c->base, m, d, k, K, c->base, agg, c->dG,
+                                                 c->dStatus, c->stream),
+                             "align")))
+        return st;
+    }
+    if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, align ? c->dG : nullptr, agg == LP_AGG_SIGN ? 1 : 0,
+                                                   m, d, K, c->dY, c->stream),
+                           "aggregate")))
+      return st;
+    if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream), "orth")))
+      return st;
+    c->stats.rounds++;
+  }
+  if (c->ritz) {
+    if ((st = launch_step(c, K, c->dZ, 0, timing))) return st;
+    if ((st = check_launch(c, lp::launch_reduce(c->dP, c->dSlotBegin, c->dInvS, m, d, K, c->dYl, c->stream), "reduce")))
+      return st;
+    if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, nullptr, 0, m, d, K, c->dMZ, c->stream),
+                           "aggregate")))
+      return st;
+    if ((st = check_launch(c, lp::launch_ritz(c->dZ, c->dMZ, d, k, K, double(c->n), c->dZout, c->dSigma, c->dStatus,
+                                              c->stream),
+                           "ritz")))
+      return st;
+  } else {
+    if ((st = check_launch(c, lp::launch_unpack(c->dZ, c->dZout, 1, d, k, K, c->stream), "unpack"))) return st;
+  }
+  LP_CUDA(cudaEventRecord(c->ev1, c->stream));
+  c->stats.k = k;
+  c->stats.n = c->n;
+  c->stats.d = c->d;
+  c->stats.m = m;
+  c->stats.path = 0;
+  c->solved = true;
+  return LP_OK;
+}
+
+lp_status lp_result(lp_ctx* c, double* z_out, double* sigma_out, lp_stats* stats) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  if (!c->solved) return fail(c, LP_ERR_STATE, "no solve to report");
+  LP_CUDA(cudaSetDevice(c->device));
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  int status = 0;
+  LP_CUDA(cudaMemcpy(&status, c->dStatus, 4, cudaMemcpyDeviceToHost));
+  float ms = 0.f;
+  LP_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  c->stats.ms_solve = ms;
+  double step_ms = 0.0;
+  for (int e = 0; e + 1 < c->step_ev_used; e += 2) {
+    float x = 0.f;
+    LP_CUDA(cudaEventElapsedTime(&x, c->step_ev[e], c->step_ev[e + 1]));
+    step_ms += x;
+  }
+  c->stats.ms_step_kernels = step_ms;
+  if (z_out)
+    LP_CUDA(cudaMemcpy(z_out, c->dZout, size_t(c->d) * c->k * 8, cudaMemcpyDeviceToHost));
+  if (sigma_out) {
+    if (c->ritz) LP_CUDA(cudaMemcpy(sigma_out, c->dSigma, size_t(c->k) * 8, cudaMemcpyDeviceToHost));
+    else std::memset(sigma_out, 0, size_t(c->k) * 8);
+  }
+  if (stats) *stats = c->stats;
+  if (status & lp::ST_CHOL) return fail(c, LP_ERR_NUMERIC, "Cholesky breakdown (non-positive or non-finite pivot)");
+  if (status & lp::ST_NONFINITE) return fail(c, LP_ERR_NUMERIC, "non-finite iterate");
+  if (status & lp::ST_JACOBI) return fail(c, LP_ERR_NUMERIC, "Jacobi iteration did not converge or singular block");
+  if (status & lp::ST_TIMEOUT) return fail(c, LP_ERR_TIMEOUT, "device wait timed out");
+  return LP_OK;
+}
+
+lp_status lp_power_step(lp_ctx* c, int k, const double* z, int z_shared, double* y_out, lp_ptr_space space) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  lp_status st = validate_k(c, k);
+  if (st) return st;
+  if (!z || !y_out) return fail(c, LP_ERR_INVALID, "z and y_out must be non-NULL");
+  LP_CUDA(cudaSetDevice(c->device));
+  const int K = kcap_of(k);
+  if ((st = ensure_state(c, K))) return st;
+  const int d = static_cast<int>(c->d);
+  const int nb = z_shared ? 1 : c->m;
+  const double* dz;
+  if ((st = stage_in(c, z, size_t(nb) * d * k, space, &dz))) return st;
+  float* Zt = z_shared ? c->dZ : c->dZl;
+  if ((st = check_launch(c, lp::launch_pack(dz, Zt, nb, d, k, K, c->stream), "pack"))) return st;
+  if ((st = launch_step(c, K, Zt, z_shared ? 0 : int64_t(d) * K, false))) return st;
+  if ((st = check_launch(c, lp::launch_reduce(c->dP, c->dSlotBegin, c->dInvS, c->m, d, K, c->dYl, c->stream),
+                         "reduce")))
+    return st;
+  double* dst = space == LP_DEVICE ? y_out : c->dStage;
+  if ((st = check_launch(c, lp::launch_unpack(c->dYl, dst, c->m, d, k, K, c->stream), "unpack"))) return st;
+  if (space == LP_HOST)
+    LP_CUDA(cudaMemcpyAsync(y_out, dst, size_t(c->m) * d * k * 8, cudaMemcpyDeviceToHost, c->stream));
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  return LP_OK;
+}
+
+}  // extern "C"
+
+// Scratch-owning helper for the standalone small-kernel entry points.
+namespace {
+struct Scratch {
+  lp_ctx* c;
+  std::vector<std::pair<void*, size_t>> bufs;
+  ~Scratch() {
+    for (auto& b : bufs) {
+      void* p = b.first;
+      dfree(c, p, b.second);
+    }
+  }
+  template <typename T>
+  lp_status get(T** p, size_t bytes) {
+    lp_status st = dalloc(c, p, bytes);
+    if (!st) bufs.push_back({static_cast<void*>(*p), bytes});
+    return st;
+  }
+};
+
+lp_status to_device(lp_ctx* c, Scratch& s, const double* src, size_t count, lp_ptr_space space, const double** dev) {
+  if (space == LP_DEVICE) {
+    *dev = src;
+    return LP_OK;
+  }
+  double* p;
+  lp_status st = s.get(&p, count * 8);
+  if (st) return st;
+  LP_CUDA(cudaMemcpyAsync(p, src, count * 8, cudaMemcpyHostToDevice, c->stream));
+  *dev = p;
+  return LP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lp_status lp_orth(lp_ctx* c, int batch, int64_t d, int k, const double* y, double* z, lp_ptr_space space) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  if (batch < 1 || d < 1 || k < 1 || k > LP_MAX_K || k > d || !y || !z)
+    return fail(c, LP_ERR_INVALID, "need batch >= 1, 1 <= k <= min(32, d), non-NULL y and z");
+  LP_CUDA(cudaSetDevice(c->device));
+  const int K = kcap_of(k);
+  Scratch s{c, {}};
+  lp_status st;
+  const double* dy;
+  float *Y, *Z;
+  double* dz;
+  const size_t blk = size_t(batch) * d;
+  if ((st = to_device(c, s, y, blk * k, space, &dy)) || (st = s.get(&Y, blk * K * 4)) ||
+      (st = s.get(&Z, blk * K * 4)))
+    return st;
+  if (space == LP_DEVICE) dz = z;
+  else if ((st = s.get(&dz, blk * k * 8))) return st;
+  LP_CUDA(cudaMemsetAsync(c->dStatus, 0, 4, c->stream));
+  if ((st = check_launch(c, lp::launch_pack(dy, Y, batch, static_cast<int>(d), k, K, c->stream), "pack"))) return st;
+  if ((st = check_launch(c, lp::launch_cholqr2(Y, Z, batch, static_cast<int>(d), k, K, c->dStatus, c->stream),
+                         "orth")))
+    return st;
+  if ((st = check_launch(c, lp::launch_unpack(Z, dz, batch, static_cast<int>(d), k, K, c->stream), "unpack")))
+    return st;
+  if (space == LP_HOST) LP_CUDA(cudaMemcpyAsync(z, dz, blk * k * 8, cudaMemcpyDeviceToHost, c->stream));
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  int status = 0;
+  LP_CUDA(cudaMemcpy(&status, c->dStatus, 4, cudaMemcpyDeviceToHost));
+  if (status & lp::ST_CHOL) return fail(c, LP_ERR_NUMERIC, "Cholesky breakdown in orth");
+  return LP_OK;
+}
+
+lp_status lp_align_aggregate(lp_ctx* c, int m, int64_t d, int k, lp_aggregator agg, int base, const double* w,
+                             const double* ys, const double* zs, double* y_out, double* d_out, lp_ptr_space space) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  if (m < 1 || d < 1 || k < 1 || k > LP_MAX_K || k > d || base < 0 || base >= m || !w || !ys || !zs || !y_out)
+    return fail(c, LP_ERR_INVALID, "bad arguments to lp_align_aggregate");
+  if (agg != LP_AGG_IDENTITY && agg != LP_AGG_SIGN && agg != LP_AGG_OPT)
+    return fail(c, LP_ERR_INVALID, "unknown aggregator");
+  LP_CUDA(cudaSetDevice(c->device));
+  const int K = kcap_of(k);
+  const int di = static_cast<int>(d);
+  Scratch s{c, {}};
+  lp_status st;
+  const double *dys, *dzs, *dw;
+  float *Yl, *Zl, *G, *Y, *W;
+  double *dy, *dG;
+  const size_t blk = size_t(m) * d;
+  if ((st = to_device(c, s, ys, blk * k, space, &dys)) || (st = to_device(c, s, zs, blk * k, space, &dzs)) ||
+      (st = to_device(c, s, w, m, space, &dw)) || (st = s.get(&Yl, blk * K * 4)) || (st = s.get(&Zl, blk * K * 4)) ||
+      (st = s.get(&G, size_t(m) * K * K * 4)) || (st = s.get(&Y, size_t(d) * K * 4)) || (st = s.get(&W, m * 4)) ||
+      (st = s.get(&dG, size_t(m) * k * k * 8)))
+    return st;
+  if (space == LP_DEVICE) dy = y_out;
+  else if ((st = s.get(&dy, size_t(d) * k * 8))) return st;
+  LP_CUDA(cudaMemsetAsync(c->dStatus, 0, 4, c->stream));
+  if ((st = check_launch(c, lp::launch_pack(dys, Yl, m, di, k, K, c->stream), "pack")) ||
+      (st = check_launch(c, lp::launch_pack(dzs, Zl, m, di, k, K, c->stream), "pack")) ||
+      (st = check_launch(c, lp::launch_pack(dw, W, 1, m, 1, 1, c->stream), "pack")))
+    return st;
+  const bool align = agg != LP_AGG_IDENTITY;
+  if (align && (st = check_launch(c, lp::launch_align(Zl, int64_t(d) * K, Zl + int64_t(d) * K * base, m, di, k, K, base,
+                                                      agg, G, c->dStatus, c->stream),
+                                  "align")))
+    return st;
+  if ((st = check_launch(c, lp::launch_aggregate(Yl, W, align ? G : nullptr, agg == LP_AGG_SIGN ? 1 : 0, m, di, K, Y,
+                                                 c->stream),
+                         "aggregate")))
+    return st;
+  if ((st = check_launch(c, lp::launch_unpack(Y, dy, 1, di, k, K, c->stream), "unpack"))) return st;
+  if (space == LP_HOST) LP_CUDA(cudaMemcpyAsync(y_out, dy, size_t(d) * k * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (d_out) {
+    // G_i (K x K float) -> k x k FP64; identity blocks when agg is identity.
+    std::vector<float> hG(size_t(m) * K * K, 0.f);
+    if (align) LP_CUDA(cudaMemcpyAsync(hG.data(), G, hG.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    LP_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<double> out(size_t(m) * k * k);
+    for (int i = 0; i < m; ++i)
+      for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b)
+          out[(size_t(i) * k + a) * k + b] = align ? hG[(size_t(i) * K + a) * K + b] : (a == b ? 1.0 : 0.0);
+    if (space == LP_DEVICE) LP_CUDA(cudaMemcpy(d_out, out.data(), out.size() * 8, cudaMemcpyHostToDevice));
+    else std::memcpy(d_out, out.data(), out.size() * 8);
+  }
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  int status = 0;
+  LP_CUDA(cudaMemcpy(&status, c->dStatus, 4, cudaMemcpyDeviceToHost));
+  if (status & lp::ST_JACOBI) return fail(c, LP_ERR_NUMERIC, "Jacobi SVD did not converge or singular block");
+  return LP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Internal declarations of the LocalPower CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "localpower.h"
+
+namespace lp {
+
+// Bits of the device status word (OR-ed by kernels, read by lp_result).
+enum StatusBits : int {
+  ST_CHOL = 1,        // non-positive or non-finite Cholesky pivot
+  ST_NONFINITE = 2,   // non-finite value in an iterate
+  ST_JACOBI = 4,      // Jacobi sweeps hit their limit
+  ST_TIMEOUT = 8,     // a bounded wait gave up
+};
+
+// One contiguous run of rows of one partition processed by one CTA of the
+// fused step kernel.  Global row indices into the packed A buffer.
+struct Segment {
+  int64_t row0, row1;  // [row0, row1)
+  int part;            // partition index i
+  int slot;            // output slot of the CTA's partial A_i^T A_i Z_i
+};
+
+// ---- fused local power step (SIMT) ---------------------------------------
+struct StepArgs {
+  const void* A;          // packed partitions, row pitch `ld` elements
+  int64_t ld;             // elements
+  int d;                  // columns
+  const float* scales;    // FP8 row scales (global row index) or nullptr
+  const Segment* segs;    // all segments, CTA-major
+  const int* seg_ptr;     // CTA g owns segs[seg_ptr[g] .. seg_ptr[g+1])
+  const float* Z;         // d x K blocks (FP32, columns >= k are zero)
+  int64_t z_stride;       // floats between partitions' Z blocks (0: shared)
+  float* P;               // slots x d x K partial sums of A_i^T (A_i Z_i)
+  int grid;               // CTAs
+};
+
+// Returns cudaErrorInvalidConfiguration when no SIMT instantiation fits.
+cudaError_t launch_step_simt(const StepArgs& a, lp_dtype dtype, int K, cudaStream_t s);
+// Shared memory the SIMT step needs (0 if unsupported); used to validate up front.
+size_t step_simt_smem(int d, int64_t ld, lp_dtype dtype, int K, int* rows_per_tile);
+
+// ---- small kernels --------------------------------------------------------
+// Y_i = scale_i * sum_{slot in [slot_begin[i], slot_begin[i+1])} P[slot]
+cudaError_t launch_reduce(const float* P, const int* slot_begin, const float* scale, int m, int d, int K,
+                          float* Y, cudaStream_t s);
+// Z_b = orth(Y_b) (CholQR2, FP32 data, FP64 k x k factors), batch blocks of d x K.
+cudaError_t launch_cholqr2(const float* Y, float* Z, int batch, int d, int k, int K, int* status, cudaStream_t s);
+// G_i = aligning matrices (K x K, FP32) for agg in {SIGN, OPT}; base gets I.
+cudaError_t launch_align(const float* Zl, int64_t z_stride, const float* Zb, int m, int d, int k, int K, int base,
+                         lp_aggregator agg, float* G, int* status, cudaStream_t s);
+// Y = sum_i w_i Y_i G_i  (G == nullptr: identity; diag_only: G_i diagonal)
+cudaError_t launch_aggregate(const float* Yl, const float* w, const float* G, int diag_only, int m, int d, int K,
+                             float* Y, cudaStream_t s);
+// Ritz: H = Z^T MZ (FP64), eig (FP64 Jacobi), Zout = Z W (FP64), sigma = sqrt(n lambda)
+cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, double n, double* Zout, double* sigma,
+                        int* status, cudaStream_t s);
+// FP64 d x k (row-major) <-> FP32 d x K padded blocks
+cudaError_t launch_pack(const double* src, float* dst, int batch, int d, int k, int K, cudaStream_t s);
+cudaError_t launch_unpack(const float* src, double* dst, int batch, int d, int k, int K, cudaStream_t s);
+
+}  // namespace lp

@@ -1,0 +1,478 @@
+// The d x k and k x k kernels around the fused power step:
+//   reduce     Y_i = (1/s_i) sum of the step kernel's per-CTA partials (fixed order)
+//   cholqr2    Z = orth(Y) by two passes of Gram / Cholesky / triangular solve
+//   align      sign-fixing (eq. (4)) or orthogonal Procrustes (eq. (3)) matrices
+//   aggregate  Y = sum_i p_i Y_i D_i (Alg. 1 aggregation)
+//   ritz       Rayleigh-Ritz on span(Z): ordered basis and sigma_j = sqrt(n lambda_j)
+// Precision: the d-sized work (Gram, solves, averaging) is FP32; the k x k
+// factorisations (Cholesky, triangular inverse, Jacobi SVD / eigen) are FP64,
+// as are the sign-fix inner products that decide D_i.
+#include <cfloat>
+
+#include "lp_internal.cuh"
+
+namespace lp {
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- pack / unpack
+__global__ void pack_kernel(const double* __restrict__ src, float* __restrict__ dst, int batch, int d, int k, int K) {
+  const int64_t total = int64_t(batch) * d * K;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int j = static_cast<int>(e % K);
+    const int64_t row = e / K;  // b * d + c
+    dst[e] = j < k ? static_cast<float>(src[row * k + j]) : 0.f;
+  }
+}
+__global__ void unpack_kernel(const float* __restrict__ src, double* __restrict__ dst, int batch, int d, int k, int K) {
+  const int64_t total = int64_t(batch) * d * k;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int j = static_cast<int>(e % k);
+    const int64_t row = e / k;
+    dst[e] = static_cast<double>(src[row * K + j]);
+  }
+}
+
+// ---------------------------------------------------------------- reduce
+__global__ void reduce_kernel(const float* __restrict__ P, const int* __restrict__ slot_begin,
+                              const float* __restrict__ scale, int d, int K, float* __restrict__ Y) {
+  const int i = blockIdx.y;
+  const int64_t n4 = int64_t(d) * K / 4;
+  const int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (e >= n4) return;
+  const int sb = slot_begin[i], se = slot_begin[i + 1];
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int s = sb; s < se; ++s) {
+    const float4 v = reinterpret_cast<const float4*>(P + int64_t(s) * d * K)[e];
+    acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+  }
+  const float sc = scale[i];
+  acc.x *= sc; acc.y *= sc; acc.z *= sc; acc.w *= sc;
+  reinterpret_cast<float4*>(Y + int64_t(i) * d * K)[e] = acc;
+}
+
+// ---------------------------------------------------------------- k x k helpers (warp 0, FP64)
+// Cholesky G = L L^T in place into L (lower, k x k, stride K).  Returns false on breakdown
+// (non-positive or non-finite pivot); the pivot is then replaced by 1 so the caller can finish.
+__device__ bool warp_cholesky(const double* G, double* L, int k, int K) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int j = 0; j < k; ++j) {
+    if (lane == 0) {
+      double s = G[j * K + j];
+      for (int p = 0; p < j; ++p) s -= L[j * K + p] * L[j * K + p];
+      if (!(s > 0.0) || !isfinite(s)) {
+        ok = false;
+        s = 1.0;
+      }
+      L[j * K + j] = sqrt(s);
+    }
+    __syncwarp();
+    const double ljj = L[j * K + j];
+    for (int i = j + 1 + lane; i < k; i += 32) {
+      double s = G[i * K + j];
+      for (int p = 0; p < j; ++p) s -= L[i * K + p] * L[j * K + p];
+      L[i * K + j] = s / ljj;
+    }
+    __syncwarp();
+  }
+  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+// X = L^{-1} (lower triangular), column c computed by lane c.
+__device__ void warp_lower_inverse(const double* L, double* X, int k, int K) {
+  const int c = threadIdx.x & 31;
+  if (c < k) {
+    X[c * K + c] = 1.0 / L[c * K + c];
+    for (int i = c + 1; i < k; ++i) {
+      double s = 0.0;
+      for (int p = c; p < i; ++p) s += L[i * K + p] * X[p * K + c];
+      X[i * K + c] = -s / L[i * K + i];
+    }
+  }
+  __syncwarp();
+}
+
+// One-sided (Hestenes) Jacobi on the k x k matrix C (stride K, in smem), accumulating the
+// rotations in V.  On return C's columns are mutually orthogonal: C_in V = C_out, so
+// C_in = U Sigma V^T with sigma_j = ||C_out[:, j]||, U[:, j] = C_out[:, j] / sigma_j.
+// Returns false if the sweep limit was hit.
+__device__ bool warp_jacobi(double* C, double* V, int k, int K) {
+  const int lane = threadIdx.x & 31;
+  for (int r = lane; r < k; r += 32)
+    for (int j = 0; j < k; ++j) V[r * K + j] = (r == j) ? 1.0 : 0.0;
+  __syncwarp();
+  const double tol = 1e-14;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    int rotated = 0;
+    for (int p = 0; p < k - 1; ++p) {
+      for (int q = p + 1; q < k; ++q) {
+        double a = 0.0, b = 0.0, g = 0.0;
+        if (lane < k) {
+          const double cp = C[lane * K + p], cq = C[lane * K + q];
+          a = cp * cp;
+          b = cq * cq;
+          g = cp * cq;
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (fabs(g) > tol * sqrt(a * b) && fabs(g) > 1e-300) {
+          rotated = 1;
+          const double zeta = (b - a) / (2.0 * g);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t);
+          const double s = c * t;
+          if (lane < k) {
+            const double cp = C[lane * K + p], cq = C[lane * K + q];
+            C[lane * K + p] = c * cp - s * cq;
+            C[lane * K + q] = s * cp + c * cq;
+            const double vp = V[lane * K + p], vq = V[lane * K + q];
+            V[lane * K + p] = c * vp - s * vq;
+            V[lane * K + q] = s * vp + c * vq;
+          }
+          __syncwarp();
+        }
+      }
+    }
+    if (!rotated) return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------- CholQR2
+// One CTA per block.  Shared: G (double K*K), L (double K*K), X (double K*K),
+// Ri (float K*K), a staged chunk of rows (float kChunk*K).
+constexpr int kChunk = 64;
+
+__device__ void gram_fp32(const float* __restrict__ Y, int d, int k, int K, float* chunk, double* G) {
+  const int t = threadIdx.x;
+  const int NP = K * K;
+  const int RS = NP >= kT ? 1 : kT / NP;        // row slices
+  const int PP = NP >= kT ? NP / kT : 1;        // pairs per thread
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int r0 = 0; r0 < d; r0 += kChunk) {
+    const int nr = min(kChunk, d - r0);
+    __syncthreads();
+    for (int e = t; e < nr * K / 4; e += kT)
+      reinterpret_cast<float4*>(chunk)[e] = reinterpret_cast<const float4*>(Y + int64_t(r0) * K)[e];
+    __syncthreads();
+    for (int pp = 0; pp < PP; ++pp) {
+      const int idx = t + kT * pp;
+      const int pair = idx % NP, slice = idx / NP;
+      const int a = pair / K, b = pair % K;
+      if (slice < RS) {
+        float s = acc[pp];
+        for (int r = slice; r < nr; r += RS) s = fmaf(chunk[r * K + a], chunk[r * K + b], s);
+        acc[pp] = s;
+      }
+    }
+  }
+  __syncthreads();
+  // combine slices through the (now free) chunk buffer, then widen to FP64
+  if (RS > 1) {
+    chunk[t] = acc[0];
+    __syncthreads();
+    if (t < NP) {
+      float s = 0.f;
+      for (int sl = 0; sl < RS; ++sl) s += chunk[sl * NP + t];
+      G[t] = static_cast<double>(s);
+    }
+  } else {
+    for (int pp = 0; pp < PP; ++pp) G[t + kT * pp] = static_cast<double>(acc[pp]);
+  }
+  __syncthreads();
+  (void)k;
+}
+
+__device__ void tri_solve_rows(const float* Yin, float* Zout, const float* Ri, int d, int k, int K) {
+  // Z[r][j] = sum_{p <= j} Y[r][p] Ri[p][j]; K threads per row, so a warp holds whole rows
+  // and may update them in place (all its loads precede its stores).
+  const int t = threadIdx.x;
+  const int j = t % K;
+  const int rpb = kT / K;
+  for (int rb = 0; rb < d; rb += rpb) {
+    const int r = rb + t / K;
+    const bool act = r < d;
+    float yr[32];
+#pragma unroll
+    for (int p = 0; p < 32; ++p) yr[p] = (act && p < K) ? Yin[int64_t(r) * K + p] : 0.f;
+    __syncwarp();
+    if (act) {
+      float s = 0.f;
+#pragma unroll
+      for (int p = 0; p < 32; ++p)
+        if (p < K && p <= j && j < k) s = fmaf(yr[p], Ri[p * K + j], s);
+      Zout[int64_t(r) * K + j] = s;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kT) cholqr2_kernel(const float* __restrict__ Yall, float* __restrict__ Zall, int d,
+                                                     int k, int K, int* status) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double* G = reinterpret_cast<double*>(sm);
+  double* L = G + K * K;
+  double* X = L + K * K;
+  float* Ri = reinterpret_cast<float*>(X + K * K);
+  float* chunk = Ri + K * K;
+  const float* Y = Yall + int64_t(blockIdx.x) * d * K;
+  float* Z = Zall + int64_t(blockIdx.x) * d * K;
+  const int t = threadIdx.x;
+  for (int pass = 0; pass < 2; ++pass) {
+    const float* src = pass == 0 ? Y : Z;
+    gram_fp32(src, d, k, K, chunk, G);
+    if (t < 32) {
+      for (int e = t; e < K * K; e += 32) { L[e] = 0.0; X[e] = 0.0; }
+      __syncwarp();
+      const bool ok = warp_cholesky(G, L, k, K);
+      if (!ok && t == 0) atomicOr(status, ST_CHOL);
+      warp_lower_inverse(L, X, k, K);
+      for (int e = t; e < K * K; e += 32) {
+        const int p = e / K, j = e % K;  // Ri = (L^{-1})^T, upper triangular
+        Ri[e] = (p < k && j < k && p <= j) ? static_cast<float>(X[j * K + p]) : 0.f;
+      }
+    }
+    __syncthreads();
+    tri_solve_rows(src, Z, Ri, d, k, K);
+    __syncthreads();
+  }
+}
+
+size_t cholqr2_smem(int K) { return size_t(3) * K * K * 8 + size_t(K) * K * 4 + size_t(kChunk) * K * 4 + 16; }
+
+// ---------------------------------------------------------------- align
+// One CTA per partition.  G_i (K x K float, row-major) = D_i (sign) or O_i (OPT).
+__global__ void __launch_bounds__(kT) align_kernel(const float* __restrict__ Zl, int64_t z_stride,
+                                                   const float* __restrict__ Zb, int d, int k, int K, int base,
+                                                   int opt, float* __restrict__ Gout, int* status) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double* C = reinterpret_cast<double*>(sm);   // K*K
+  double* V = C + K * K;                        // K*K
+  double* part = V + K * K;                     // kT doubles
+  const int i = blockIdx.x;
+  const int t = threadIdx.x;
+  float* Gi = Gout + int64_t(i) * K * K;
+  if (i == base) {
+    for (int e = t; e < K * K; e += kT) Gi[e] = ((e / K) == (e % K) && (e / K) < k) ? 1.f : 0.f;
+    return;
+  }
+  const float* Zi = Zl + z_stride * i;
+  if (!opt) {
+    // sgn <Z_i[:, j], Z_b[:, j]> with FP64 accumulation; sgn(0) = +1.
+    const int j = t % K, sl = t / K, RS = kT / K;
+    double s = 0.0;
+    for (int r = sl; r < d; r += RS) s += static_cast<double>(Zi[int64_t(r) * K + j]) * Zb[int64_t(r) * K + j];
+    part[t] = s;
+    __syncthreads();
+    if (t < K) {
+      double tot = 0.0;
+      for (int q = 0; q < RS; ++q) tot += part[q * K + t];
+      part[kT - K + t] = tot;  // scratch beyond the first RS*K entries is not re-read
+    }
+    __syncthreads();
+    for (int e = t; e < K * K; e += kT) {
+      const int a = e / K, b = e % K;
+      float v = 0.f;
+      if (a == b && a < k) v = part[kT - K + a] < 0.0 ? -1.f : 1.f;
+      Gi[e] = v;
+    }
+    return;
+  }
+  // OPT: C = Z_i^T Z_b (FP32 products, FP32 partial sums, FP64 combine), SVD by Jacobi.
+  const int NP = K * K;
+  const int RS = NP >= kT ? 1 : kT / NP;
+  const int PP = NP >= kT ? NP / kT : 1;
+  for (int pp = 0; pp < PP; ++pp) {
+    const int idx = t + kT * pp;
+    const int pair = idx % NP, sl = idx / NP;
+    const int a = pair / K, b = pair % K;
+    float s = 0.f;
+    if (sl < RS)
+      for (int r = sl; r < d; r += RS) s = fmaf(Zi[int64_t(r) * K + a], Zb[int64_t(r) * K + b], s);
+    if (RS > 1) part[t] = s;
+    else C[idx] = s;
+  }
+  __syncthreads();
+  if (RS > 1) {
+    if (t < NP) {
+      double s = 0.0;
+      for (int sl = 0; sl < RS; ++sl) s += part[sl * NP + t];
+      C[t] = s;
+    }
+    __syncthreads();
+  }
+  if (t < 32) {
+    const bool ok = warp_jacobi(C, V, k, K);
+    if (!ok && t == 0) atomicOr(status, ST_JACOBI);
+    // U[:, j] = C[:, j] / sigma_j ; O = U V^T
+    for (int j = 0; j < k; ++j) {
+      double nrm = 0.0;
+      if (t < k) nrm = C[t * K + j] * C[t * K + j];
+      nrm = sqrt(warp_sum(nrm));
+      if (t < k) C[t * K + j] = nrm > 1e-300 ? C[t * K + j] / nrm : 0.0;
+      if (!(nrm > 1e-300) && t == 0) atomicOr(status, ST_JACOBI);
+    }
+    __syncwarp();
+    for (int e = t; e < K * K; e += 32) {
+      const int a = e / K, b = e % K;
+      double s = 0.0;
+      if (a < k && b < k)
+        for (int j = 0; j < k; ++j) s += C[a * K + j] * V[b * K + j];
+      Gi[e] = static_cast<float>(s);
+    }
+  }
+}
+
+size_t align_smem(int K) { return size_t(2) * K * K * 8 + size_t(kT) * 8 + 16; }
+
+// ---------------------------------------------------------------- aggregate
+__global__ void aggregate_kernel(const float* __restrict__ Yl, const float* __restrict__ w,
+                                 const float* __restrict__ G, int diag_only, int m, int d, int K,
+                                 float* __restrict__ Y) {
+  const int t = threadIdx.x;
+  const int j = t % K;
+  const int r = blockIdx.x * (kT / K) + t / K;
+  if (r >= d) return;
+  float acc = 0.f;
+  for (int i = 0; i < m; ++i) {
+    const float* yi = Yl + (int64_t(i) * d + r) * K;
+    float v;
+    if (G == nullptr) {
+      v = yi[j];
+    } else if (diag_only) {
+      v = yi[j] * G[int64_t(i) * K * K + j * K + j];
+    } else {
+      const float* gi = G + int64_t(i) * K * K;
+      v = 0.f;
+      for (int l = 0; l < K; ++l) v = fmaf(yi[l], gi[l * K + j], v);
+    }
+    acc = fmaf(w[i], v, acc);
+  }
+  Y[int64_t(r) * K + j] = acc;
+}
+
+// ---------------------------------------------------------------- Ritz
+__global__ void __launch_bounds__(kT) ritz_kernel(const float* __restrict__ Z, const float* __restrict__ MZ, int d,
+                                                  int k, int K, double n, double* __restrict__ Zout,
+                                                  double* __restrict__ sigma, int* status) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double* H = reinterpret_cast<double*>(sm);  // K*K
+  double* V = H + K * K;                       // K*K
+  double* lam = V + K * K;                     // K
+  int* order = reinterpret_cast<int*>(lam + K);
+  const int t = threadIdx.x;
+  // H = Z^T (M Z) with FP64 accumulation.
+  for (int e = t; e < K * K; e += kT) {
+    const int a = e / K, b = e % K;
+    double s = 0.0;
+    if (a < k && b < k)
+      for (int r = 0; r < d; ++r) s += static_cast<double>(Z[int64_t(r) * K + a]) * MZ[int64_t(r) * K + b];
+    H[e] = s;
+  }
+  __syncthreads();
+  if (t < 32) {
+    // symmetrise
+    for (int e = t; e < K * K; e += 32) {
+      const int a = e / K, b = e % K;
+      if (a < b) {
+        const double s = 0.5 * (H[a * K + b] + H[b * K + a]);
+        H[a * K + b] = s;
+        H[b * K + a] = s;
+      }
+    }
+    __syncwarp();
+    // H is symmetric positive semidefinite: its one-sided Jacobi SVD is its eigendecomposition.
+    const bool ok = warp_jacobi(H, V, k, K);
+    if (!ok && t == 0) atomicOr(status, ST_JACOBI);
+    for (int j = 0; j < k; ++j) {
+      double s = 0.0;
+      if (t < k) s = H[t * K + j] * H[t * K + j];
+      s = sqrt(warp_sum(s));
+      if (t == 0) lam[j] = s;
+    }
+    __syncwarp();
+    if (t == 0) {
+      for (int j = 0; j < k; ++j) order[j] = j;
+      for (int a = 0; a < k; ++a)
+        for (int b = a + 1; b < k; ++b)
+          if (lam[order[b]] > lam[order[a]]) {
+            const int tmp = order[a];
+            order[a] = order[b];
+            order[b] = tmp;
+          }
+      for (int j = 0; j < k; ++j) sigma[j] = sqrt(n * lam[order[j]]);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // Zout = Z V(:, order), FP64
+  for (int64_t e = t; e < int64_t(d) * k; e += kT) {
+    const int r = static_cast<int>(e / k), j = static_cast<int>(e % k);
+    const int oj = order[j];
+    double s = 0.0;
+    for (int l = 0; l < k; ++l) s += static_cast<double>(Z[int64_t(r) * K + l]) * V[l * K + oj];
+    Zout[e] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const double* src, float* dst, int batch, int d, int k, int K, cudaStream_t s) {
+  const int64_t total = int64_t(batch) * d * K;
+  const int64_t nb = (total + kT - 1) / kT;
+  const int blocks = static_cast<int>(nb < 4096 ? (nb > 0 ? nb : 1) : 4096);
+  pack_kernel<<<blocks, kT, 0, s>>>(src, dst, batch, d, k, K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const float* src, double* dst, int batch, int d, int k, int K, cudaStream_t s) {
+  const int64_t total = int64_t(batch) * d * k;
+  const int64_t nb = (total + kT - 1) / kT;
+  const int blocks = static_cast<int>(nb < 4096 ? (nb > 0 ? nb : 1) : 4096);
+  unpack_kernel<<<blocks, kT, 0, s>>>(src, dst, batch, d, k, K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const float* P, const int* slot_begin, const float* scale, int m, int d, int K, float* Y,
+                          cudaStream_t s) {
+  const int64_t n4 = int64_t(d) * K / 4;
+  dim3 grid(static_cast<unsigned>((n4 + kT - 1) / kT), static_cast<unsigned>(m));
+  reduce_kernel<<<grid, kT, 0, s>>>(P, slot_begin, scale, d, K, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cholqr2(const float* Y, float* Z, int batch, int d, int k, int K, int* status, cudaStream_t s) {
+  const size_t sm = cholqr2_smem(K);
+  cholqr2_kernel<<<batch, kT, sm, s>>>(Y, Z, d, k, K, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_align(const float* Zl, int64_t z_stride, const float* Zb, int m, int d, int k, int K, int base,
+                         lp_aggregator agg, float* G, int* status, cudaStream_t s) {
+  align_kernel<<<m, kT, align_smem(K), s>>>(Zl, z_stride, Zb, d, k, K, base, agg == LP_AGG_OPT ? 1 : 0, G, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aggregate(const float* Yl, const float* w, const float* G, int diag_only, int m, int d, int K,
+                             float* Y, cudaStream_t s) {
+  const int rpb = kT / K;
+  aggregate_kernel<<<(d + rpb - 1) / rpb, kT, 0, s>>>(Yl, w, G, diag_only, m, d, K, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, double n, double* Zout, double* sigma,
+                        int* status, cudaStream_t s) {
+  const size_t sm = size_t(2) * K * K * 8 + size_t(K) * 8 + size_t(K) * 4 + 16;
+  ritz_kernel<<<1, kT, sm, s>>>(Z, MZ, d, k, K, n, Zout, sigma, status);
+  return cudaGetLastError();
+}
+
+}  // namespace lp

