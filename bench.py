@@ -45,6 +45,8 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=None,
+                    help="override n (same spectrum and partition count): a smaller case for profiler captures")
     return ap.parse_args()
 
 
@@ -110,10 +112,12 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _workload(rank: int):
+def _workload(rank: int, rows: int | None = None):
     import synth
-    c = synth.CONFIGS[WORKLOAD]
-    A, sizes, Y0 = synth.make_config_data(WORKLOAD)
+    c = dict(synth.CONFIGS[WORKLOAD])
+    if rows:
+        c["n"] = int(rows)
+    A, sizes, Y0 = synth.make_config_data(WORKLOAD, n=c["n"])
     return c, A, sizes, Y0, synth.config_schedule(WORKLOAD)
 
 
@@ -135,7 +139,7 @@ def run_reference(args):
     if rank != 0:
         return
     import synth
-    c, A, sizes, Y0, sched = _workload(0)
+    c, A, sizes, Y0, sched = _workload(0, args.rows)
     parts = synth.split_rows(A, sizes)
     sample = parts[:16]
     for _ in range(args.warmup):
@@ -178,7 +182,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    c, A, sizes, Y0, sched = _workload(rank)
+    c, A, sizes, Y0, sched = _workload(rank, args.rows)
     parts = synth.split_rows(A, sizes)
     k = c["k"]
     stream = torch.cuda.Stream(device=dev)
@@ -230,10 +234,12 @@ def run_ours(args):
     alu_peak = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12      # FP32 FMA lanes x 2 flop x max SM clock
 
     # ---------------- end to end through the public API, host buffers
-    pinned = torch.from_numpy(A).pin_memory()
-    host_parts = [t.numpy() for t in torch.split(pinned, sizes)]
+    d = c["d"]
     e2e_ms = []
-    for it in range(args.e2e_steps + 1):
+    if args.e2e_steps > 0:
+        pinned = torch.from_numpy(A).pin_memory()
+        host_parts = [t.numpy() for t in torch.split(pinned, sizes)]
+    for it in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -245,14 +251,16 @@ def run_ours(args):
         barrier()
         if it > 0:   # the first is a warm-up
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_t = max(e2e_ms) if world == 1 else None
-    if world > 1:
-        t = torch.tensor([max(e2e_ms)], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_val = world * bytes_solve / (e2e_t / 1e3) / 1e9
-    h2d = A.nbytes + Y0.nbytes
-    d2h = Ze.nbytes + 8 * k
+    e2e = None
+    if e2e_ms:
+        e2e_t = max(e2e_ms)
+        if world > 1:
+            t = torch.tensor([e2e_t], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_t = float(t.item())
+        e2e = {"value": world * bytes_solve / (e2e_t / 1e3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": int(A.nbytes + Y0.nbytes), "d2h_bytes_per_step": int(d * k * 8 + 8 * k),
+               "ms_per_step": e2e_t}
 
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -261,8 +269,7 @@ def run_ours(args):
             "latency_ms": {"p50": p50, "p99": p99, "samples": len(lat)},
             "clocks": clk,
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
-            "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "ms_per_step": e2e_t},
+            "e2e": e2e,
             "roofline": {"kernel": "step_simt_kernel (fused A_i^T (A_i Z_i))", "bound": "alu",
                          "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
                          "traffic": None, "launch_ms": step_ms,

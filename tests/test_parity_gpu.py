@@ -48,7 +48,7 @@ def _relF(a, b):
     ([96, 96], 1024, 16),              # widest SIMT column count
     ([40, 41, 42], 64, 32),            # k = 32
     ([20], 7, 1),                      # tiny d, k = 1
-    ([300, 17], 512, 24),              # k padded to 32, partition of 17 rows
+    ([300, 29], 512, 24),              # k padded to 32, partition of 29 rows
 ])
 def test_power_step_matches_oracle(gpu_lib, dtype, sizes, d, k):
     stored, exact, scales = _parts(sizes, d, 100 + d + k, dtype)
