@@ -62,6 +62,7 @@ typedef enum lp_ptr_space { LP_HOST = 0, LP_DEVICE = 1 } lp_ptr_space;
 /* lp_solve flags */
 #define LP_FLAG_RITZ   1u   /* finish with a Rayleigh-Ritz step: ordered basis + sigma */
 #define LP_FLAG_TIMING 2u   /* record CUDA events around every fused power-step launch */
+#define LP_FLAG_SIMT   4u   /* BF16 data: use the SIMT FP32 step kernel instead of the tensor-core one */
 
 typedef struct lp_ctx lp_ctx;
 
@@ -72,7 +73,7 @@ typedef struct lp_stats {
     int32_t k;
     int64_t n, d;
     int32_t m;
-    int32_t path;              /* 0 = SIMT FP32 step kernel, 1 = tcgen05 tensor-core step */
+    int32_t path;              /* 0 = SIMT FP32 step kernel, 1 = tcgen05 tensor-core step (BF16) */
     double a_bytes;            /* algorithmic bytes of A read by the step kernels     */
     double ms_solve;           /* solve wall time on the stream (events)              */
     double ms_step_kernels;    /* summed step-kernel time (LP_FLAG_TIMING only)       */

@@ -49,6 +49,15 @@ struct lp_ctx {
   float* dInvS = nullptr;
   float* dW = nullptr;
 
+  // tensor-core step schedule (BF16 partitions): one segment list per cluster
+  bool tc_ready = false;
+  lp::TcPlan tc;
+  int nslots_tc = 0;
+  Segment* dSegsTc = nullptr;
+  int* dSegPtrTc = nullptr;
+  int* dSlotBeginTc = nullptr;
+  bool use_tc = false;  // path of the current solve / step
+
   // solve state (capacity in K)
   int Kcap = 0;
   float *dP = nullptr, *dYl = nullptr, *dZl = nullptr, *dY = nullptr, *dZ = nullptr, *dG = nullptr, *dMZ = nullptr;
@@ -125,7 +134,7 @@ struct StateSizes {
 };
 StateSizes state_sizes(const lp_ctx* c, int K) {
   StateSizes s;
-  s.P = size_t(c->nslots) * c->d * K * 4;
+  s.P = size_t(std::max(c->nslots, c->nslots_tc)) * c->d * K * 4;
   s.Yl = size_t(c->m) * c->d * K * 4;
   s.Y = size_t(c->d) * K * 4;
   s.G = size_t(c->m) * K * K * 4;
@@ -176,7 +185,12 @@ void free_partitions(lp_ctx* c) {
   dfree(c, c->dSlotBegin, (size_t(c->m) + 1) * 4);
   dfree(c, c->dInvS, size_t(c->m) * 4);
   dfree(c, c->dW, size_t(c->m) * 4);
+  dfree(c, c->dSegsTc, (size_t(c->tc.nclusters) + c->m) * sizeof(Segment));
+  dfree(c, c->dSegPtrTc, (size_t(c->tc.nclusters) + 1) * 4);
+  dfree(c, c->dSlotBeginTc, (size_t(c->m) + 1) * 4);
   free_state(c);
+  c->nslots_tc = 0;
+  c->tc_ready = false;
   c->m = 0;
   c->n = 0;
   c->dA_bytes = 0;
@@ -194,6 +208,45 @@ lp_status stage_in(lp_ctx* c, const double* src, size_t count, lp_ptr_space spac
   *dev = c->dStage;
   return LP_OK;
 }
+
+// Contiguous row ranges for G workers (CTAs or clusters): worker g owns rows
+// [g n / G, (g+1) n / G), cut at partition ends; one output slot per piece.
+// Partition i's slots are the contiguous range [slot_begin[i], slot_begin[i+1]).
+void build_segments(const lp_ctx* c, int G, std::vector<Segment>& segs, std::vector<int>& seg_ptr,
+                    std::vector<int>& slot_begin) {
+  const int64_t n = c->n;
+  const int m = c->m;
+  segs.clear();
+  seg_ptr.assign(G + 1, 0);
+  slot_begin.assign(m + 1, 0);
+  int part = 0;
+  for (int g = 0; g < G; ++g) {
+    seg_ptr[g] = static_cast<int>(segs.size());
+    int64_t r0 = n * g / G, r1 = n * (g + 1) / G;
+    while (r0 < r1) {
+      while (c->row_off[part] + c->rows[part] <= r0) ++part;
+      const int64_t pend = c->row_off[part] + c->rows[part];
+      const int64_t e = std::min(r1, pend);
+      Segment s;
+      s.row0 = r0;
+      s.row1 = e;
+      s.part = part;
+      s.slot = static_cast<int>(segs.size());
+      segs.push_back(s);
+      r0 = e;
+    }
+  }
+  seg_ptr[G] = static_cast<int>(segs.size());
+  const int nslots = static_cast<int>(segs.size());
+  int s = 0;
+  for (int i = 0; i < m; ++i) {
+    while (s < nslots && segs[s].part < i) ++s;
+    slot_begin[i] = s;
+  }
+  slot_begin[m] = nslots;
+}
+
+const int* slot_begin_of(const lp_ctx* c) { return c->use_tc ? c->dSlotBeginTc : c->dSlotBegin; }
 
 lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool timing) {
   lp::StepArgs a;
@@ -216,7 +269,9 @@ lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool t
     }
     LP_CUDA(cudaEventRecord(c->step_ev[c->step_ev_used], c->stream));
   }
-  cudaError_t e = lp::launch_step_simt(a, c->dtype, K, c->stream);
+  cudaError_t e = c->use_tc ? lp::launch_step_tc(c->tc, c->dSegsTc, c->dSegPtrTc, Z, z_stride, c->dP,
+                                                  static_cast<int>(c->d), c->dStatus, c->stream)
+                            : lp::launch_step_simt(a, c->dtype, K, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "fused power-step launch");
   if (timing) {
     LP_CUDA(cudaEventRecord(c->step_ev[c->step_ev_used + 1], c->stream));
@@ -328,38 +383,23 @@ lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, l
   }
   c->base = static_cast<int>(std::max_element(c->rows.begin(), c->rows.end()) - c->rows.begin());
 
-  // Row segments: CTA g owns global rows [g n / G, (g+1) n / G), cut at partition ends.
+  // Row segments of the SIMT step kernel: CTA g owns rows [g n / G, (g+1) n / G), cut at partition ends.
   const int64_t min_rows = 32;
   c->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->sms, n / min_rows)));
   std::vector<Segment> segs;
-  std::vector<int> seg_ptr(c->grid + 1, 0);
-  std::vector<int> slot_begin(m + 1, 0);
-  int part = 0;
-  for (int g = 0; g < c->grid; ++g) {
-    seg_ptr[g] = static_cast<int>(segs.size());
-    int64_t r0 = n * g / c->grid, r1 = n * (g + 1) / c->grid;
-    while (r0 < r1) {
-      while (c->row_off[part] + c->rows[part] <= r0) ++part;
-      const int64_t pend = c->row_off[part] + c->rows[part];
-      const int64_t e = std::min(r1, pend);
-      Segment s;
-      s.row0 = r0;
-      s.row1 = e;
-      s.part = part;
-      s.slot = static_cast<int>(segs.size());
-      segs.push_back(s);
-      r0 = e;
-    }
-  }
-  seg_ptr[c->grid] = static_cast<int>(segs.size());
+  std::vector<int> seg_ptr, slot_begin;
+  build_segments(c, c->grid, segs, seg_ptr, slot_begin);
   c->nslots = static_cast<int>(segs.size());
-  {
-    int s = 0;
-    for (int i = 0; i < m; ++i) {
-      while (s < c->nslots && segs[s].part < i) ++s;
-      slot_begin[i] = s;
-    }
-    slot_begin[m] = c->nslots;
+  // Tensor-core step kernel (BF16): one segment table per cluster of CTAs.
+  std::vector<Segment> segs_tc;
+  std::vector<int> seg_ptr_tc, slot_begin_tc;
+  c->tc_ready = false;
+  if (dtype == LP_BF16 && lp::tc_plan(static_cast<int>(d), LP_MAX_K, c->sms, &c->tc)) {
+    const int G = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->tc.nclusters, (n + 127) / 128)));
+    c->tc.nclusters = G;
+    build_segments(c, G, segs_tc, seg_ptr_tc, slot_begin_tc);
+    c->nslots_tc = static_cast<int>(segs_tc.size());
+    c->tc_ready = true;
   }
   std::vector<float> invs(m), w(m);
   for (int i = 0; i < m; ++i) {
@@ -374,11 +414,26 @@ lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, l
       (st = dalloc(c, &c->dSegs, (size_t(c->grid) + m) * sizeof(Segment))) ||
       (st = dalloc(c, &c->dSegPtr, (size_t(c->grid) + 1) * 4)) ||
       (st = dalloc(c, &c->dSlotBegin, (size_t(m) + 1) * 4)) || (st = dalloc(c, &c->dInvS, size_t(m) * 4)) ||
-      (st = dalloc(c, &c->dW, size_t(m) * 4))) {
+      (st = dalloc(c, &c->dW, size_t(m) * 4)) ||
+      (c->tc_ready && ((st = dalloc(c, &c->dSegsTc, (size_t(c->tc.nclusters) + m) * sizeof(Segment))) ||
+                       (st = dalloc(c, &c->dSegPtrTc, (size_t(c->tc.nclusters) + 1) * 4)) ||
+                       (st = dalloc(c, &c->dSlotBeginTc, (size_t(m) + 1) * 4))))) {
     std::string msg = c->err;
     free_partitions(c);
     c->err = msg;
     return st;
+  }
+  if (c->tc_ready) {
+    if (lp::tc_encode_map(c->dA, n, static_cast<int>(d), c->ld, &c->tc) != cudaSuccess) {
+      c->tc_ready = false;  // no tensor map: BF16 solves use the SIMT step kernel
+    } else {
+      LP_CUDA(cudaMemcpyAsync(c->dSegsTc, segs_tc.data(), segs_tc.size() * sizeof(Segment), cudaMemcpyHostToDevice,
+                              c->stream));
+      LP_CUDA(cudaMemcpyAsync(c->dSegPtrTc, seg_ptr_tc.data(), seg_ptr_tc.size() * 4, cudaMemcpyHostToDevice,
+                              c->stream));
+      LP_CUDA(cudaMemcpyAsync(c->dSlotBeginTc, slot_begin_tc.data(), slot_begin_tc.size() * 4,
+                              cudaMemcpyHostToDevice, c->stream));
+    }
   }
   const cudaMemcpyKind kind = space == LP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   if (c->ld != d) LP_CUDA(cudaMemsetAsync(c->dA, 0, c->dA_bytes, c->stream));
@@ -406,8 +461,26 @@ static lp_status validate_k(lp_ctx* c, int k) {
   if (k > smin)
     return fail(c, LP_ERR_INVALID, "k exceeds the smallest partition's row count (its local Y_i would be rank deficient)");
   const int K = kcap_of(k);
-  if (lp::step_simt_smem(static_cast<int>(c->d), c->ld, c->dtype, K, nullptr) == 0)
+  if (!c->tc_ready && lp::step_simt_smem(static_cast<int>(c->d), c->ld, c->dtype, K, nullptr) == 0)
     return fail(c, LP_ERR_UNSUPPORTED, "no step kernel for d=" + std::to_string(c->d) + ", k=" + std::to_string(k));
+  return LP_OK;
+}
+
+// Picks the step kernel: tensor cores for BF16 partitions unless LP_FLAG_SIMT asks
+// otherwise (or the shape has no tensor-core plan), else the SIMT FP32 kernel.
+static lp_status select_path(lp_ctx* c, int k, unsigned flags) {
+  c->use_tc = false;
+  if (c->tc_ready && !(flags & LP_FLAG_SIMT)) {
+    lp::TcPlan p;
+    if (lp::tc_plan(static_cast<int>(c->d), k, c->sms, &p) && p.cluster == c->tc.cluster && p.nch == c->tc.nch) {
+      c->tc.K = p.K;
+      c->tc.smem = p.smem;
+      c->use_tc = true;
+    }
+  }
+  if (!c->use_tc && lp::step_simt_smem(static_cast<int>(c->d), c->ld, c->dtype, kcap_of(k), nullptr) == 0)
+    return fail(c, LP_ERR_UNSUPPORTED,
+                "no step kernel for d=" + std::to_string(c->d) + ", k=" + std::to_string(k) + " on this path");
   return LP_OK;
 }
 
@@ -427,6 +500,7 @@ lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator
   if (!y0) return fail(c, LP_ERR_INVALID, "y0 is NULL");
   LP_CUDA(cudaSetDevice(c->device));
   const int K = kcap_of(k);
+  if ((st = select_path(c, k, flags))) return st;
   if ((st = ensure_state(c, K))) return st;
 
   const int d = static_cast<int>(c->d);
@@ -454,7 +528,7 @@ lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator
                                       "local orth")))
         return st;
       if ((st = launch_step(c, K, j == 0 ? c->dZ : c->dZl, j == 0 ? 0 : zs, timing))) return st;
-      if ((st = check_launch(c, lp::launch_reduce(c->dP, c->dSlotBegin, c->dInvS, m, d, K, c->dYl, c->stream),
+      if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream),
                              "reduce")))
         return st;
       c->stats.local_steps++;
@@ -477,7 +551,7 @@ lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator
   }
   if (c->ritz) {
     if ((st = launch_step(c, K, c->dZ, 0, timing))) return st;
-    if ((st = check_launch(c, lp::launch_reduce(c->dP, c->dSlotBegin, c->dInvS, m, d, K, c->dYl, c->stream), "reduce")))
+    if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream), "reduce")))
       return st;
     if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, nullptr, 0, m, d, K, c->dMZ, c->stream),
                            "aggregate")))
@@ -494,7 +568,7 @@ lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator
   c->stats.n = c->n;
   c->stats.d = c->d;
   c->stats.m = m;
-  c->stats.path = 0;
+  c->stats.path = c->use_tc ? 1 : 0;
   c->solved = true;
   return LP_OK;
 }
@@ -539,7 +613,9 @@ lp_status lp_power_step(lp_ctx* c, int k, const double* z, int z_shared, double*
   if (!z || !y_out) return fail(c, LP_ERR_INVALID, "z and y_out must be non-NULL");
   LP_CUDA(cudaSetDevice(c->device));
   const int K = kcap_of(k);
+  if ((st = select_path(c, k, 0))) return st;
   if ((st = ensure_state(c, K))) return st;
+  LP_CUDA(cudaMemsetAsync(c->dStatus, 0, 4, c->stream));
   const int d = static_cast<int>(c->d);
   const int nb = z_shared ? 1 : c->m;
   const double* dz;
@@ -547,7 +623,7 @@ lp_status lp_power_step(lp_ctx* c, int k, const double* z, int z_shared, double*
   float* Zt = z_shared ? c->dZ : c->dZl;
   if ((st = check_launch(c, lp::launch_pack(dz, Zt, nb, d, k, K, c->stream), "pack"))) return st;
   if ((st = launch_step(c, K, Zt, z_shared ? 0 : int64_t(d) * K, false))) return st;
-  if ((st = check_launch(c, lp::launch_reduce(c->dP, c->dSlotBegin, c->dInvS, c->m, d, K, c->dYl, c->stream),
+  if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, c->m, d, K, c->dYl, c->stream),
                          "reduce")))
     return st;
   double* dst = space == LP_DEVICE ? y_out : c->dStage;

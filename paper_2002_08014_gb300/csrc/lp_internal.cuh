@@ -43,6 +43,22 @@ cudaError_t launch_step_simt(const StepArgs& a, lp_dtype dtype, int K, cudaStrea
 // Shared memory the SIMT step needs (0 if unsupported); used to validate up front.
 size_t step_simt_smem(int d, int64_t ld, lp_dtype dtype, int K, int* rows_per_tile);
 
+// ---- fused local power step (tcgen05 tensor cores, BF16 A) ---------------
+struct TcPlan {
+  int K = 0;           // padded k (8, 16, 32); MMA N = 2K
+  int nch = 0;         // 64-column chunks per CTA (2 or 4)
+  int cluster = 0;     // CTAs per cluster splitting d
+  int nclusters = 0;   // clusters in the grid (one CTA per SM)
+  size_t smem = 0;     // dynamic shared memory per CTA
+  alignas(64) unsigned char tmap[128];  // CUtensorMap of the packed BF16 A
+};
+// Fills the geometry for (d, k); false when the shape has no tensor-core kernel.
+bool tc_plan(int d, int k, int sms, TcPlan* p);
+// Encodes the 2-D tensor map of A (n rows, d columns, row pitch ld elements).
+cudaError_t tc_encode_map(void* A, int64_t n, int d, int64_t ld, TcPlan* p);
+cudaError_t launch_step_tc(const TcPlan& p, const Segment* segs, const int* seg_ptr, const float* Z, int64_t z_stride,
+                           float* P, int d, int* status, cudaStream_t s);
+
 // ---- small kernels --------------------------------------------------------
 // Y_i = scale_i * sum_{slot in [slot_begin[i], slot_begin[i+1])} P[slot]
 cudaError_t launch_reduce(const float* P, const int* slot_begin, const float* scale, int m, int d, int K,

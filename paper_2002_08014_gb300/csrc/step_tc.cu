@@ -1,0 +1,528 @@
+// Fused local power step on the 5th-generation tensor cores (tcgen05), for A
+// stored in BF16:  P[slot] = A_seg^T (A_seg Z_i)  (the unscaled local product of
+// eq. (2)), FP32 accumulation in tensor memory.
+//
+// Geometry.  Rows are processed in tiles of 128 (the MMA's M).  The d columns
+// are split over a thread-block cluster of CL CTAs (CL in {1, 2, 4, 8}); CTA c
+// owns columns [c*DC, (c+1)*DC) with DC = 64*NCH, so one row tile of its slice
+// (128 x DC BF16 = 16*NCH KB) stays resident in shared memory for both
+// contractions and A is read from HBM exactly once.
+//
+// Per tile (all CTAs of a cluster walk the same row tiles):
+//   TMA    A tile slice -> smem (SWIZZLE_128B boxes of 64 columns x 128 rows)
+//   C1     D1 = A_slice [Z_hi | Z_lo]          M=128, N=2K, K-major A and B
+//   epi    W_partial = D1[:, :K] + D1[:, K:]; summed over the cluster through
+//          distributed shared memory (owner CTAs reduce 128/CL rows each);
+//          rows outside the segment are zeroed; W -> [W_hi | W_lo] in BF16
+//   C2     D2[b] += A_slice^T [W_hi | W_lo]    M=128 d-columns, N=2K, MN-major A
+// After a segment's last tile, Y = D2[:, :K] + D2[:, K:] is written to P.
+// The hi/lo splits keep Z and W at about 16 significant bits, so the products
+// carry FP32-level accuracy although the tensor cores take BF16 operands.
+//
+// Roles (256 threads): warp 0 lane 0 issues TMA; warp 1 lane 0 issues MMAs;
+// warps 4-7 (one per TMEM lane quadrant) run the epilogue; every warp helps
+// stage Z at segment starts.  Every mbarrier wait is bounded: on expiry the
+// kernel records ST_TIMEOUT, stops issuing work and unwinds.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "lp_internal.cuh"
+
+namespace lp {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBM = 128;
+constexpr int kChunkBytes = kBM * 128;  // 128 rows x 64 BF16
+constexpr long long kTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+struct TcArgs {
+  const Segment* segs;
+  const int* seg_ptr;  // per cluster
+  const float* Z;
+  int64_t z_stride;
+  float* P;
+  int d;
+  int* status;
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t su32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok) : "r"(addr), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_try_cluster(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok) : "r"(addr), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit TMEM columns; lane i of the warp gets lane (base + i).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, SWIZZLE_128B, tcgen05 format (version field = 1).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32, dense.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn_major, bool b_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((b_mn_major ? 1u : 0u) << 16) |
+         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// Byte offset of element (row n, k-index kk) of a K-major SWIZZLE_128B operand
+// whose rows hold 64 BF16 per 128-byte chunk; chunks of `rows` rows are contiguous.
+__device__ __forceinline__ uint32_t sw128_off(int n, int kk, int rows) {
+  const int chunk = kk >> 6, k2 = (kk & 63) * 2;
+  return static_cast<uint32_t>(chunk * rows * 128 + n * 128 + ((((k2 >> 4) ^ (n & 7))) << 4) + (k2 & 15));
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_val(uint16_t b) { return __uint_as_float(static_cast<uint32_t>(b) << 16); }
+
+template <int K, int NCH>
+struct TcLayout {
+  static constexpr int N = 2 * K;
+  static constexpr int DC = 64 * NCH;
+  static constexpr int STAGE = NCH * kChunkBytes;
+  static constexpr int B1 = NCH * N * 128;
+  static constexpr int B2 = 2 * N * 128;
+  static constexpr int NB2 = NCH / 2;
+  static constexpr int off_A = 0;
+  static constexpr int off_B1 = off_A + 2 * STAGE;
+  static constexpr int off_B2 = off_B1 + B1;
+  static constexpr int off_Wred = off_B2 + 2 * B2;
+  static constexpr int off_Wfull = off_Wred + kBM * K * 4;
+  static constexpr int off_bar = off_Wfull + kBM * K * 4;
+  static constexpr int kBars = 16;
+  static constexpr int bytes = off_bar + kBars * 8 + 16;
+  static constexpr int alloc_bytes = bytes + 1024;  // room to align the base to 1024
+  static constexpr uint32_t tmem_used = 2 * N + NB2 * N;
+  static constexpr uint32_t tmem_cols = tmem_used <= 32 ? 32 : tmem_used <= 64 ? 64 : tmem_used <= 128 ? 128
+                                        : tmem_used <= 256 ? 256 : 512;
+};
+
+enum BarId { B_FULL0 = 0, B_EMPTY0 = 2, B_D1FULL0 = 4, B_D1EMPTY0 = 6, B_B2FULL0 = 8, B_B2FREE0 = 10, B_D2FULL = 12,
+             B_REDFULL = 13, B_WFULL = 14, B_DONE = 15 };
+
+template <int K, int NCH>
+__global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
+  using L = TcLayout<K, NCH>;
+  constexpr int N = L::N;
+  constexpr int DC = L::DC;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sA = base + L::off_A;
+  unsigned char* sB1 = base + L::off_B1;
+  unsigned char* sB2 = base + L::off_B2;
+  float* sWred = reinterpret_cast<float*>(base + L::off_Wred);
+  float* sWfull = reinterpret_cast<float*>(base + L::off_Wfull);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + L::off_bar);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + L::kBars);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t crank = cluster_rank();
+  const uint32_t CL = cluster_size();
+  const int RPC = kBM / static_cast<int>(CL);
+  const int cluster_id = blockIdx.x / CL;
+  const int c0 = static_cast<int>(crank) * DC;
+
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&bar[B_FULL0 + s], 1);
+      mbar_init(&bar[B_EMPTY0 + s], 1);
+      mbar_init(&bar[B_D1FULL0 + s], 1);
+      mbar_init(&bar[B_D1EMPTY0 + s], 4);
+      mbar_init(&bar[B_B2FULL0 + s], kBM);
+      mbar_init(&bar[B_B2FREE0 + s], 1);
+    }
+    mbar_init(&bar[B_D2FULL], 1);
+    mbar_init(&bar[B_REDFULL], kBM);
+    mbar_init(&bar[B_WFULL], 4 * CL);
+    mbar_init(&bar[B_DONE], 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_holder)),
+                 "r"(L::tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // every CTA's barriers exist before any remote arrive
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  auto wait = [&](int id, uint32_t parity, bool cluster_scope) -> bool {
+    const uint32_t addr = su32(&bar[id]);
+    const long long t0 = clock64();
+    while (true) {
+      if (cluster_scope ? mbar_try_cluster(addr, parity) : mbar_try(addr, parity)) return true;
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kTimeoutCycles) {
+        *abort_flag = 1;
+        atomicOr(a.status, ST_TIMEOUT);
+        return false;
+      }
+    }
+  };
+
+  constexpr uint32_t idesc1 = idesc_bf16(128, N, false, false);
+  constexpr uint32_t idesc2 = idesc_bf16(128, N, true, false);
+
+  const int sb = a.seg_ptr[cluster_id], se = a.seg_ptr[cluster_id + 1];
+  uint32_t T = 0;  // tiles processed so far (identical in every CTA of the cluster)
+  for (int si = sb; si < se; ++si) {
+    const Segment sg = a.segs[si];
+    const int ntiles = static_cast<int>((sg.row1 - sg.row0 + kBM - 1) / kBM);
+
+    // ---- stage Z slice as [Z_hi | Z_lo]^T (N rows x DC, K-major, SWIZZLE_128B)
+    __syncthreads();
+    {
+      const float* Zg = a.Z + a.z_stride * sg.part;
+      for (int e = tid; e < DC * K; e += kThreads) {
+        const int c = e / K, j = e % K;
+        const float z = (c0 + c < a.d) ? Zg[static_cast<int64_t>(c0 + c) * K + j] : 0.f;
+        const uint16_t hi = bf16_bits(z);
+        const uint16_t lo = bf16_bits(z - bf16_val(hi));
+        *reinterpret_cast<uint16_t*>(sB1 + sw128_off(j, c, N)) = hi;
+        *reinterpret_cast<uint16_t*>(sB1 + sw128_off(K + j, c, N)) = lo;
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+
+    if (warp == 0 && lane == 0) {
+      // ------------------------------------------------------------ TMA producer
+      for (int t = 0; t < ntiles; ++t) {
+        const uint32_t Tg = T + t, s = Tg & 1;
+        if (!wait(B_EMPTY0 + s, ((Tg >> 1) + 1) & 1, false)) break;
+        mbar_expect_tx(&bar[B_FULL0 + s], L::STAGE);
+        const int row = static_cast<int>(sg.row0) + t * kBM;
+        for (int ch = 0; ch < NCH; ++ch)
+          tma_load_2d(su32(sA + s * L::STAGE + ch * kChunkBytes), &tmap, c0 + ch * 64, row, &bar[B_FULL0 + s]);
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ------------------------------------------------------------ MMA issuer
+      auto c1 = [&](uint32_t Tg) -> bool {
+        const uint32_t s = Tg & 1, b = Tg & 1;
+        if (!wait(B_FULL0 + s, (Tg >> 1) & 1, false)) return false;
+        if (!wait(B_D1EMPTY0 + b, ((Tg >> 1) + 1) & 1, false)) return false;
+        tc_fence_after();
+        const uint32_t aS = su32(sA + s * L::STAGE), bS = su32(sB1);
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = sdesc(aS + ch * kChunkBytes + kk * 32, 16, 1024);
+            const uint64_t bd = sdesc(bS + ch * N * 128 + kk * 32, 16, 1024);
+            mma_bf16(tmem + b * N, ad, bd, idesc1, (ch | kk) != 0);
+          }
+        mma_commit(&bar[B_D1FULL0 + b]);
+        return true;
+      };
+      auto c2 = [&](uint32_t Tg, bool first) -> bool {
+        const uint32_t s = Tg & 1, b = Tg & 1;
+        if (!wait(B_B2FULL0 + b, (Tg >> 1) & 1, false)) return false;
+        tc_fence_after();
+        const uint32_t aS = su32(sA + s * L::STAGE), bS = su32(sB2 + b * L::B2);
+#pragma unroll
+        for (int mb = 0; mb < L::NB2; ++mb)
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            // A^T: M = 128 d-columns (two 64-column chunks, LBO apart), K = 16 rows (two 8-row groups, SBO apart)
+            const uint64_t ad = sdesc(aS + (2 * mb) * kChunkBytes + kk * 2048, kChunkBytes, 1024);
+            const uint64_t bd = sdesc(bS + (kk >> 2) * N * 128 + (kk & 3) * 32, 16, 1024);
+            mma_bf16(tmem + 2 * N + mb * N, ad, bd, idesc2, (first && kk == 0) ? 0u : 1u);
+          }
+        mma_commit(&bar[B_EMPTY0 + s]);
+        mma_commit(&bar[B_B2FREE0 + b]);
+        return true;
+      };
+      bool ok = c1(T);
+      for (int t = 0; ok && t < ntiles; ++t) {
+        if (t + 1 < ntiles && !c1(T + t + 1)) break;
+        ok = c2(T + t, t == 0);
+      }
+      mma_commit(&bar[B_D2FULL]);
+    } else if (warp >= 4) {
+      // ------------------------------------------------------------ epilogue
+      const int r = (warp - 4) * 32 + lane;
+      const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
+      bool ok = true;
+      for (int t = 0; ok && t < ntiles; ++t) {
+        const uint32_t Tg = T + t, b = Tg & 1;
+        if (!(ok = wait(B_D1FULL0 + b, (Tg >> 1) & 1, false))) break;
+        tc_fence_after();
+        float w[K];
+#pragma unroll
+        for (int q = 0; q < N / 16; ++q) {
+          float v[16];
+          tmem_ld16(tmem + lane_base + b * N + q * 16, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int col = q * 16 + i;
+            if (col < K) w[col] = v[i];
+            else w[col - K] += v[i];
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar[B_D1EMPTY0 + b]);
+        const bool valid = sg.row0 + static_cast<int64_t>(t) * kBM + r < sg.row1;
+        if (!valid) {
+#pragma unroll
+          for (int j = 0; j < K; ++j) w[j] = 0.f;
+        }
+        if (CL > 1) {
+          // partial row r -> its owner's reduction slots
+          const uint32_t owner = static_cast<uint32_t>(r / RPC);
+          const uint32_t dst = mapa(su32(sWred + (crank * RPC + (r % RPC)) * K), owner);
+#pragma unroll
+          for (int j = 0; j < K; ++j) st_cluster_f32(dst + 4 * j, w[j]);
+          mbar_arrive_remote(mapa(su32(&bar[B_REDFULL]), owner));
+          // owner: sum this CTA's RPC rows over the cluster, broadcast the sums
+          if (!(ok = wait(B_REDFULL, Tg & 1, true))) break;
+          const int per = RPC * K / kBM;  // values per epilogue thread
+          const int v0 = r * per;
+          for (int e = 0; e < per; ++e) {
+            const int idx = v0 + e, rl = idx / K, col = idx % K;
+            float s = 0.f;
+            for (uint32_t src = 0; src < CL; ++src) s += sWred[(src * RPC + rl) * K + col];
+            const uint32_t loc = su32(sWfull + (crank * RPC + rl) * K + col);
+            for (uint32_t dsti = 0; dsti < CL; ++dsti) st_cluster_f32(mapa(loc, dsti), s);
+          }
+          fence_cluster();
+          __syncwarp();
+          if (lane == 0)
+            for (uint32_t dsti = 0; dsti < CL; ++dsti) mbar_arrive_remote(mapa(su32(&bar[B_WFULL]), dsti));
+          if (!(ok = wait(B_WFULL, Tg & 1, true))) break;
+#pragma unroll
+          for (int j = 0; j < K; ++j) w[j] = sWfull[r * K + j];
+        }
+        // [W_hi | W_lo]^T into B2[b]: row n = output column, k-index = tile row r
+        if (!(ok = wait(B_B2FREE0 + b, ((Tg >> 1) + 1) & 1, false))) break;
+        unsigned char* B2 = sB2 + b * L::B2;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+          const uint16_t hi = bf16_bits(w[j]);
+          const uint16_t lo = bf16_bits(w[j] - bf16_val(hi));
+          *reinterpret_cast<uint16_t*>(B2 + sw128_off(j, r, N)) = hi;
+          *reinterpret_cast<uint16_t*>(B2 + sw128_off(K + j, r, N)) = lo;
+        }
+        fence_async_smem();
+        mbar_arrive(&bar[B_B2FULL0 + b]);
+      }
+      // segment end: Y slice = D2[:, :K] + D2[:, K:] -> P[slot]
+      if (ok && wait(B_D2FULL, (si - sb) & 1, false)) {
+        tc_fence_after();
+        float* Pd = a.P + static_cast<int64_t>(sg.slot) * a.d * K;
+        for (int mb = 0; mb < L::NB2; ++mb) {
+          float y[K];
+#pragma unroll
+          for (int q = 0; q < N / 16; ++q) {
+            float v[16];
+            tmem_ld16(tmem + lane_base + 2 * N + mb * N + q * 16, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int col = q * 16 + i;
+              if (col < K) y[col] = v[i];
+              else y[col - K] += v[i];
+            }
+          }
+          const int dcol = c0 + mb * 128 + (warp & 3) * 32 + lane;
+          if (dcol < a.d) {
+            float4* dst = reinterpret_cast<float4*>(Pd + static_cast<int64_t>(dcol) * K);
+#pragma unroll
+            for (int j = 0; j < K; j += 4) dst[j / 4] = make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]);
+          }
+        }
+        tc_fence_before();
+      }
+    }
+    T += ntiles;
+  }
+
+  // ---- teardown: all MMAs retired, no remote traffic in flight, then free TMEM
+  if (warp == 1 && lane == 0) mma_commit(&bar[B_DONE]);
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t addr = su32(&bar[B_DONE]);
+    const long long t0 = clock64();
+    while (!mbar_try(addr, 0) && clock64() - t0 < kTimeoutCycles) {
+    }
+  }
+  __syncthreads();
+  cluster_sync_all();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::tmem_cols) : "memory");
+  }
+}
+
+template <int K, int NCH>
+cudaError_t launch_tc_t(const TcPlan& p, const TcArgs& a, cudaStream_t s) {
+  using L = TcLayout<K, NCH>;
+  auto kern = step_tc_kernel<K, NCH>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::alloc_bytes);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(p.nclusters * p.cluster), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = L::alloc_bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(p.cluster);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(p.tmap);
+  return cudaLaunchKernelEx(&cfg, kern, *map, a);
+}
+
+}  // namespace
+
+bool tc_plan(int d, int k, int sms, TcPlan* p) {
+  const int K = k <= 8 ? 8 : (k <= 16 ? 16 : 32);
+  const int nch = d <= 128 ? 2 : 4;
+  const int dc = 64 * nch;
+  int cl = (d + dc - 1) / dc;
+  int c2 = 1;
+  while (c2 < cl) c2 *= 2;
+  if (c2 > 8) return false;
+  p->K = K;
+  p->nch = nch;
+  p->cluster = c2;
+  p->nclusters = sms / c2;
+  if (p->nclusters < 1) return false;
+  size_t bytes;
+  if (nch == 2) bytes = K == 8 ? TcLayout<8, 2>::alloc_bytes : K == 16 ? TcLayout<16, 2>::alloc_bytes : TcLayout<32, 2>::alloc_bytes;
+  else bytes = K == 8 ? TcLayout<8, 4>::alloc_bytes : K == 16 ? TcLayout<16, 4>::alloc_bytes : TcLayout<32, 4>::alloc_bytes;
+  p->smem = bytes;
+  return bytes <= 232448;
+}
+
+cudaError_t tc_encode_map(void* A, int64_t n, int d, int64_t ld, TcPlan* p) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  static_assert(sizeof(CUtensorMap) <= sizeof(p->tmap), "tensor map storage");
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(d), static_cast<cuuint64_t>(n)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+  cuuint32_t box[2] = {64, static_cast<cuuint32_t>(kBM)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(reinterpret_cast<CUtensorMap*>(p->tmap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, dims, strides,
+                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_tc(const TcPlan& p, const Segment* segs, const int* seg_ptr, const float* Z, int64_t z_stride,
+                           float* P, int d, int* status, cudaStream_t s) {
+  TcArgs a;
+  a.segs = segs;
+  a.seg_ptr = seg_ptr;
+  a.Z = Z;
+  a.z_stride = z_stride;
+  a.P = P;
+  a.d = d;
+  a.status = status;
+  if (p.nch == 2) {
+    if (p.K == 8) return launch_tc_t<8, 2>(p, a, s);
+    if (p.K == 16) return launch_tc_t<16, 2>(p, a, s);
+    return launch_tc_t<32, 2>(p, a, s);
+  }
+  if (p.K == 8) return launch_tc_t<8, 4>(p, a, s);
+  if (p.K == 16) return launch_tc_t<16, 4>(p, a, s);
+  return launch_tc_t<32, 4>(p, a, s);
+}
+
+}  // namespace lp

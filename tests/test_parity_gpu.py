@@ -18,6 +18,10 @@ from paper_2002_08014_gb300 import binding as B
 
 pytestmark = pytest.mark.gpu
 
+# BF16-stored A runs on the tensor cores with Z and W split into BF16 hi + lo
+# parts (each split leaves at most 2^-18 relative error), FP32 accumulation.
+TC_STEP_TOL = 1e-5
+
 
 def _parts(sizes, d, seed, dtype="f32", spikes=6):
     n = sum(sizes)
@@ -54,16 +58,17 @@ def test_power_step_matches_oracle(gpu_lib, dtype, sizes, d, k):
     stored, exact, scales = _parts(sizes, d, 100 + d + k, dtype)
     rng = np.random.default_rng(1)
     Z = O.orth(rng.standard_normal((d, k)))
+    tol = TC_STEP_TOL if dtype == "bf16" else 2e-6
     with B.LocalPower(stored, dtype=dtype, row_scales=scales) as lp:
         Y = lp.power_step(k, Z, shared=True)
         for i, P in enumerate(exact):
             ref = O.local_step(P, Z)
-            assert _relF(Y[i], ref) < 2e-6, (i, _relF(Y[i], ref))
+            assert _relF(Y[i], ref) < tol, (i, _relF(Y[i], ref))
         # per-partition bases
         Zs = np.stack([O.orth(rng.standard_normal((d, k))) for _ in sizes])
         Y2 = B.lp_power_step(lp.ctx, k, Zs, False, len(sizes), d)
         for i, P in enumerate(exact):
-            assert _relF(Y2[i], O.local_step(P, Zs[i])) < 2e-6
+            assert _relF(Y2[i], O.local_step(P, Zs[i])) < tol
 
 
 @pytest.mark.parametrize("d,k,batch", [(100, 5, 3), (1024, 16, 4), (257, 32, 2), (9, 1, 5), (2048, 32, 1)])
@@ -157,17 +162,49 @@ def test_fp32_workload_shape_decay_schedule(gpu_lib, agg):
     assert st["rounds"] == len(sched) and st["local_steps"] == sum(sched)
 
 
-@pytest.mark.parametrize("dtype", ["bf16", "e4m3"])
-def test_reduced_precision_storage_end_to_end(gpu_lib, dtype):
-    """BF16 / FP8-E4M3 stored A: the oracle runs on the decoded stored values."""
+@pytest.mark.parametrize("dtype,simt", [("bf16", False), ("bf16", True), ("e4m3", False)])
+def test_reduced_precision_storage_end_to_end(gpu_lib, dtype, simt):
+    """BF16 / FP8-E4M3 stored A: the oracle runs on the decoded stored values.
+    BF16 runs on the tensor cores unless the SIMT kernel is forced."""
     sizes = [900, 1100, 1000, 1000]
     stored, exact, scales = _parts(sizes, 200, 55, dtype, spikes=10)
     Y0 = synth.gaussian_start(200, 8, 56)
     sched = [4] * 6 + [1] * 3
     ref = O.localpower(exact, 8, sched, "sign", Y0)
     with B.LocalPower(stored, dtype=dtype, row_scales=scales) as lp:
-        Z, _, _ = lp.solve(8, sched, "sign", Y0)
-    assert O.subspace_dist(Z, ref["Z"]) < 1e-6
+        B.lp_solve(lp.ctx, 8, sched, "sign", Y0, 0, B.LP_FLAG_SIMT if simt else 0)
+        Z, _, st = lp.result(8)
+    tc = dtype == "bf16" and not simt
+    assert st["path"] == (1 if tc else 0)
+    assert O.subspace_dist(Z, ref["Z"]) < (1e-5 if tc else 1e-6)
+
+
+@pytest.mark.parametrize("d,k,sizes", [
+    (1024, 16, [700, 1300, 999, 1001]),   # 4-CTA clusters, partitions straddle clusters
+    (2048, 32, [640, 385]),               # 8-CTA clusters, k = 32
+    (300, 5, [129, 2000, 77]),            # 2-CTA clusters, last slice mostly past d
+    (100, 8, [260, 140]),                 # one CTA, two 64-column chunks
+    (513, 13, [3000]),                    # one partition, ragged everything
+])
+def test_tensor_core_step_cluster_shapes(gpu_lib, d, k, sizes):
+    stored, exact, _ = _parts(sizes, d, 7 * d + k, "bf16")
+    rng = np.random.default_rng(d)
+    Zs = np.stack([O.orth(rng.standard_normal((d, k))) for _ in sizes])
+    with B.LocalPower(stored, dtype="bf16") as lp:
+        Y = B.lp_power_step(lp.ctx, k, Zs, False, len(sizes), d)
+        for i, P in enumerate(exact):
+            assert _relF(Y[i], O.local_step(P, Zs[i])) < TC_STEP_TOL, (i, _relF(Y[i], O.local_step(P, Zs[i])))
+        # the whole solve on the tensor cores against the oracle and against the SIMT kernel
+        Y0 = synth.gaussian_start(d, k, 3)
+        sched = [4, 4, 2, 1]
+        Zt, _, st = lp.solve(k, sched, "opt", Y0)
+        assert st["path"] == 1
+        B.lp_solve(lp.ctx, k, sched, "opt", Y0, 0, B.LP_FLAG_SIMT)
+        Zs_, _, st2 = lp.result(k)
+        assert st2["path"] == 0
+    ref = O.localpower(exact, k, sched, "opt", Y0)
+    assert O.subspace_dist(Zt, ref["Z"]) < 1e-5
+    assert O.subspace_dist(Zs_, ref["Z"]) < 1e-6
 
 
 def test_uneven_partitions_base_not_first(gpu_lib):
