@@ -45,6 +45,7 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage (tensor-core) run of the workload")
     ap.add_argument("--rows", type=int, default=None,
                     help="override n (same spectrum and partition count): a smaller case for profiler captures")
     return ap.parse_args()
@@ -168,6 +169,63 @@ def _config(c, sched):
             "l2": "inputs larger than L2 (A is 4.1 GB; L2 is 129 MB)"}
 
 
+def _timed(torch, dist, world, dev, stream, lp, k, sched, agg, steps, clocks=None):
+    """K back-to-back solves on the library's stream, bracketed by a barrier and a
+    device synchronize; CUDA events on that stream.  Returns (ms, stats, Z, sigma, clocks)."""
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+    barrier()
+    if clocks:
+        clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats, Z, sig = [], None, None
+    for _ in range(steps):
+        lp.submit(k, sched, agg, _timed.y0, ritz=True, timing=True)
+        Z, sig, st = lp.result(k)
+        stats.append(st)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop() if clocks else None
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, stats, Z, sig, clk
+
+
+def _summary(world, steps, ms, stats, elem_bytes, c):
+    """Throughput, latency percentiles and the step kernel's live launch time."""
+    bytes_solve = stats[-1]["a_bytes"]
+    lat = sorted(s["ms_solve"] for s in stats)
+    step_ms = sum(s["ms_step_kernels"] for s in stats) / sum(s["step_launches"] for s in stats)
+    return {"gbs": world * steps * bytes_solve / (ms / 1e3) / 1e9,
+            "solves_per_s": world * steps / (ms / 1e3),
+            "ms_per_solve": ms / steps,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "samples": len(lat)},
+            "step_ms": step_ms,
+            "launch_bytes": float(c["n"]) * c["d"] * elem_bytes,
+            "launch_flops": 4.0 * c["n"] * c["d"] * c["k"],
+            "launches": int(sum(s["kernel_launches"] for s in stats)),
+            "path": stats[-1]["path"],
+            "bytes_solve": bytes_solve}
+
+
+def _truth(parts, c):
+    """Top-k eigenvectors / eigenvalues of M = A^T A / n (FP64, on the host)."""
+    M = np.zeros((c["d"], c["d"]))
+    for i in range(0, len(parts), 8):
+        blk = np.concatenate(parts[i:i + 8]).astype(np.float64)
+        M += blk.T @ blk
+    lam, V = np.linalg.eigh(M / c["n"])
+    return V[:, ::-1][:, :c["k"]], lam[::-1][:c["k"]]
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -183,74 +241,44 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     c, A, sizes, Y0, sched = _workload(rank, args.rows)
+    _timed.y0 = Y0
     parts = synth.split_rows(A, sizes)
-    k = c["k"]
+    k, d = c["k"], c["d"]
     stream = torch.cuda.Stream(device=dev)
-    lp = B.LocalPower(parts, device=local, stream=stream)
-
-    def one_solve():
-        lp.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
-        return lp.result(k)
-
-    for _ in range(args.warmup):
-        one_solve()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-
-    # ---------------- device-resident timed region
-    clocks = Clocks(local)
-    barrier()
-    clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    stats, Z, sig = [], None, None
-    for _ in range(args.steps):
-        Z, sig, st = one_solve()
-        stats.append(st)
-    ev1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-
-    bytes_solve = stats[-1]["a_bytes"]
-    value = world * args.steps * bytes_solve / (ms / 1e3) / 1e9
-    lat = sorted(s["ms_solve"] for s in stats)
-    p50 = float(np.percentile(lat, 50))
-    p99 = float(np.percentile(lat, 99))
-    step_ms = sum(s["ms_step_kernels"] for s in stats) / sum(s["step_launches"] for s in stats)
-    launch_bytes = float(c["n"]) * c["d"] * 4
-    launch_flops = 4.0 * c["n"] * c["d"] * k
     hbm_peak, sm_max_mhz, peak_src = _peaks()
-    achieved_gbs = launch_bytes / (step_ms / 1e3) / 1e9
-    achieved_tf = launch_flops / (step_ms / 1e3) / 1e12
     alu_peak = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12      # FP32 FMA lanes x 2 flop x max SM clock
 
-    # ---------------- end to end through the public API, host buffers
-    d = c["d"]
+    # ---------------- plain FP32 path: device-resident timed region
+    lp = B.LocalPower(parts, device=local, stream=stream)
+    for _ in range(args.warmup):
+        lp.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
+        lp.result(k)
+    ms, stats, Z, sig, clk = _timed(torch, dist, world, dev, stream, lp, k, sched, args.agg, args.steps,
+                                    Clocks(local))
+    f32 = _summary(world, args.steps, ms, stats, 4, c)
+    achieved_tf = f32["launch_flops"] / (f32["step_ms"] / 1e3) / 1e12
+    achieved_gbs = f32["launch_bytes"] / (f32["step_ms"] / 1e3) / 1e9
+
+    # ---------------- end to end through the public API, host buffers (pinned)
     e2e_ms = []
     if args.e2e_steps > 0:
         pinned = torch.from_numpy(A).pin_memory()
         host_parts = [t.numpy() for t in torch.split(pinned, sizes)]
-    for it in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        B.lp_load_partitions(lp.ctx, host_parts, "f32")
-        lp.submit(k, sched, args.agg, Y0, ritz=True)
-        Ze, _, _ = lp.result(k)
-        e1.record(stream)
-        barrier()
-        if it > 0:   # the first is a warm-up
-            e2e_ms.append(e0.elapsed_time(e1))
+        for it in range(args.e2e_steps + 1):
+            torch.cuda.synchronize(dev)
+            if world > 1:
+                dist.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.lp_load_partitions(lp.ctx, host_parts, "f32")
+            lp.submit(k, sched, args.agg, Y0, ritz=True)
+            lp.result(k)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if it > 0:   # the first is a warm-up
+                e2e_ms.append(e0.elapsed_time(e1))
+        del pinned, host_parts
     e2e = None
     if e2e_ms:
         e2e_t = max(e2e_ms)
@@ -258,43 +286,62 @@ def run_ours(args):
             t = torch.tensor([e2e_t], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_t = float(t.item())
-        e2e = {"value": world * bytes_solve / (e2e_t / 1e3) / 1e9, "unit": "GB/s",
+        e2e = {"value": world * f32["bytes_solve"] / (e2e_t / 1e3) / 1e9, "unit": "GB/s",
                "h2d_bytes_per_step": int(A.nbytes + Y0.nbytes), "d2h_bytes_per_step": int(d * k * 8 + 8 * k),
                "ms_per_step": e2e_t}
+    lp.close()
 
-    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+    line = {"metric": METRIC, "value": f32["gbs"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": f32["ms_per_solve"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(c, sched),
-            "solves_per_s": world * args.steps / (ms / 1e3),
-            "latency_ms": {"p50": p50, "p99": p99, "samples": len(lat)},
-            "clocks": clk,
-            "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
-            "e2e": e2e,
-            "roofline": {"kernel": "step_simt_kernel (fused A_i^T (A_i Z_i))", "bound": "alu",
+            "solves_per_s": f32["solves_per_s"], "latency_ms": f32["latency_ms"], "clocks": clk,
+            "gpu_launches": f32["launches"], "e2e": e2e,
+            "roofline": {"kernel": "step_simt_kernel (fused A_i^T (A_i Z_i), FP32)", "bound": "alu",
                          "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
-                         "traffic": None, "launch_ms": step_ms,
-                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz"},
+                         "traffic": None, "launch_ms": f32["step_ms"],
+                         "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz"},
             "roofline_hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                              "frac": achieved_gbs / hbm_peak, "peak_source": f"{peak_src} HBM copy bandwidth",
                              "frac_of_nominal_8000": achieved_gbs / 8000.0}}
 
+    # ---------------- the same workload stored in BF16 (tensor-core step kernel)
+    Zb = None
+    if not args.no_bf16:
+        bits = [synth.f32_to_bf16_bits(p) for p in parts]
+        lpb = B.LocalPower(bits, dtype="bf16", device=local, stream=stream)
+        for _ in range(args.warmup):
+            lpb.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
+            lpb.result(k)
+        msb, statsb, Zb, sigb, clkb = _timed(torch, dist, world, dev, stream, lpb, k, sched, args.agg, args.steps,
+                                             Clocks(local))
+        b16 = _summary(world, args.steps, msb, statsb, 2, c)
+        lpb.close()
+        gbs_b = b16["launch_bytes"] / (b16["step_ms"] / 1e3) / 1e9
+        line["precision_path"] = {
+            "dtype": "bf16 storage, FP32 accumulation (hi/lo BF16 operands)", "step_kernel":
+            "step_tc_kernel (tcgen05)" if b16["path"] == 1 else "step_simt_kernel", "gbs": b16["gbs"],
+            "solves_per_s": b16["solves_per_s"], "ms_per_solve": b16["ms_per_solve"],
+            "latency_ms": b16["latency_ms"], "clocks": clkb, "gpu_launches": b16["launches"],
+            "speedup_solves_vs_fp32": b16["solves_per_s"] / f32["solves_per_s"],
+            "roofline": {"bound": "hbm", "achieved": gbs_b, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs_b / hbm_peak, "traffic": None, "launch_ms": b16["step_ms"],
+                         "peak_source": f"{peak_src} HBM copy bandwidth"}}
+
     if rank == 0 and not args.no_accuracy:
-        Zo = oracle.orth(Z)
-        M = np.zeros((c["d"], c["d"]))
-        for i in range(0, len(parts), 8):
-            blk = np.concatenate(parts[i:i + 8]).astype(np.float64)
-            M += blk.T @ blk
-        lam, V = np.linalg.eigh(M / c["n"])
-        line["accuracy"] = {"dist_to_eigh_topk": oracle.subspace_dist(Zo, V[:, ::-1][:, :k]),
-                            "orthonormality": float(np.abs(Z.T @ Z - np.eye(k)).max()),
-                            "sigma_rel_err": float(np.max(np.abs(sig - np.sqrt(c["n"] * lam[::-1][:k]))
-                                                          / np.sqrt(c["n"] * lam[::-1][:k])))}
+        V, lam = _truth(parts, c)
+        acc = {"dist_to_eigh_topk": oracle.subspace_dist(oracle.orth(Z), V),
+               "orthonormality": float(np.abs(Z.T @ Z - np.eye(k)).max()),
+               "sigma_rel_err": float(np.max(np.abs(sig - np.sqrt(c["n"] * lam)) / np.sqrt(c["n"] * lam)))}
+        line["accuracy"] = acc
+        if Zb is not None:
+            line["precision_path"]["accuracy"] = {
+                "dist_to_eigh_topk_of_fp32_problem": oracle.subspace_dist(oracle.orth(Zb), V),
+                "dist_to_fp32_path_output": oracle.subspace_dist(oracle.orth(Zb), oracle.orth(Z))}
     if rank == 0 and not args.no_cpu_baseline:
         gbs, dt = _oracle_sample_gbps(parts, Y0, 3)
         line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"3 FP64 oracle local power steps (eq. (2)) over all 64 partitions "
                                           f"({dt:.1f} s)"}
-    lp.close()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

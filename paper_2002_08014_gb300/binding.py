@@ -18,7 +18,7 @@ STATUS_NAMES = ["LP_OK", "LP_ERR_INVALID", "LP_ERR_STATE", "LP_ERR_OOM", "LP_ERR
 LP_F32, LP_BF16, LP_FP8_E4M3 = 0, 1, 2
 LP_AGG_IDENTITY, LP_AGG_SIGN, LP_AGG_OPT = 0, 1, 2
 LP_HOST, LP_DEVICE = 0, 1
-LP_FLAG_RITZ, LP_FLAG_TIMING = 1, 2
+LP_FLAG_RITZ, LP_FLAG_TIMING, LP_FLAG_SIMT = 1, 2, 4
 LP_MAX_K = 32
 
 AGG = {"identity": LP_AGG_IDENTITY, "sign": LP_AGG_SIGN, "opt": LP_AGG_OPT}

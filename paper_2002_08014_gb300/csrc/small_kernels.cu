@@ -148,105 +148,146 @@ __device__ bool warp_jacobi(double* C, double* V, int k, int K) {
 }
 
 // ---------------------------------------------------------------- CholQR2
-// One CTA per block.  Shared: G (double K*K), L (double K*K), X (double K*K),
-// Ri (float K*K), a staged chunk of rows (float kChunk*K).
-constexpr int kChunk = 64;
+// One CTA per block, two passes of:
+//   G = Y^T Y        FP32 products and partial sums over row slices, combined in FP64
+//   G = L L^T        FP64 right-looking Cholesky on warp 0 (parallel trailing updates)
+//   Z = Y L^{-T}     per-row forward substitution in FP32, one thread per row
+// The column space is Y's whatever the precision of L; the second pass restores
+// orthonormality lost to the FP32 Gram.  A pivot that is not positive and finite
+// sets ST_CHOL (the pivot is then taken as 1 so the kernel can finish).
+constexpr int kChunk = 128;
 
-__device__ void gram_fp32(const float* __restrict__ Y, int d, int k, int K, float* chunk, double* G) {
+template <int K>
+__device__ void gram_fp32(const float* __restrict__ Y, int d, float* chunk, double* G) {
+  constexpr int NP = K * K;
+  constexpr int RS = NP >= kT ? 1 : kT / NP;  // row slices
+  constexpr int PP = NP >= kT ? NP / kT : 1;  // pairs per thread
   const int t = threadIdx.x;
-  const int NP = K * K;
-  const int RS = NP >= kT ? 1 : kT / NP;        // row slices
-  const int PP = NP >= kT ? NP / kT : 1;        // pairs per thread
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float acc[PP];
+#pragma unroll
+  for (int pp = 0; pp < PP; ++pp) acc[pp] = 0.f;
   for (int r0 = 0; r0 < d; r0 += kChunk) {
     const int nr = min(kChunk, d - r0);
     __syncthreads();
     for (int e = t; e < nr * K / 4; e += kT)
       reinterpret_cast<float4*>(chunk)[e] = reinterpret_cast<const float4*>(Y + int64_t(r0) * K)[e];
     __syncthreads();
+#pragma unroll
     for (int pp = 0; pp < PP; ++pp) {
       const int idx = t + kT * pp;
       const int pair = idx % NP, slice = idx / NP;
       const int a = pair / K, b = pair % K;
-      if (slice < RS) {
-        float s = acc[pp];
-        for (int r = slice; r < nr; r += RS) s = fmaf(chunk[r * K + a], chunk[r * K + b], s);
-        acc[pp] = s;
+      float s0 = 0.f, s1 = 0.f;
+      int r = slice;
+      for (; r + RS < nr; r += 2 * RS) {
+        s0 = fmaf(chunk[r * K + a], chunk[r * K + b], s0);
+        s1 = fmaf(chunk[(r + RS) * K + a], chunk[(r + RS) * K + b], s1);
       }
+      if (r < nr) s0 = fmaf(chunk[r * K + a], chunk[r * K + b], s0);
+      acc[pp] += s0 + s1;
     }
   }
   __syncthreads();
-  // combine slices through the (now free) chunk buffer, then widen to FP64
   if (RS > 1) {
     chunk[t] = acc[0];
     __syncthreads();
     if (t < NP) {
-      float s = 0.f;
+      double s = 0.0;
       for (int sl = 0; sl < RS; ++sl) s += chunk[sl * NP + t];
-      G[t] = static_cast<double>(s);
+      G[t] = s;
     }
   } else {
+#pragma unroll
     for (int pp = 0; pp < PP; ++pp) G[t + kT * pp] = static_cast<double>(acc[pp]);
   }
   __syncthreads();
-  (void)k;
 }
 
-__device__ void tri_solve_rows(const float* Yin, float* Zout, const float* Ri, int d, int k, int K) {
-  // Z[r][j] = sum_{p <= j} Y[r][p] Ri[p][j]; K threads per row, so a warp holds whole rows
-  // and may update them in place (all its loads precede its stores).
-  const int t = threadIdx.x;
-  const int j = t % K;
-  const int rpb = kT / K;
-  for (int rb = 0; rb < d; rb += rpb) {
-    const int r = rb + t / K;
-    const bool act = r < d;
-    float yr[32];
-#pragma unroll
-    for (int p = 0; p < 32; ++p) yr[p] = (act && p < K) ? Yin[int64_t(r) * K + p] : 0.f;
-    __syncwarp();
-    if (act) {
-      float s = 0.f;
-#pragma unroll
-      for (int p = 0; p < 32; ++p)
-        if (p < K && p <= j && j < k) s = fmaf(yr[p], Ri[p * K + j], s);
-      Zout[int64_t(r) * K + j] = s;
+// Right-looking Cholesky of G (k x k, stride K, FP64, overwritten) by one warp.
+// Writes L in FP32 (lower, stride K) and 1 / L[j][j] in FP32; returns false on breakdown.
+template <int K>
+__device__ bool warp_cholesky_rl(double* G, float* Lf, float* invd, int k) {
+  const int lane = threadIdx.x & 31;
+  bool ok = true;
+  for (int j = 0; j < k; ++j) {
+    double piv = G[j * K + j];
+    if (!(piv > 0.0) || !isfinite(piv)) {
+      ok = false;
+      piv = 1.0;
     }
+    const double ljj = sqrt(piv);
+    const double inv = 1.0 / ljj;
+    // column j below the diagonal
+    for (int i = j + 1 + lane; i < k; i += 32) G[i * K + j] *= inv;
+    if (lane == 0) {
+      G[j * K + j] = ljj;
+      invd[j] = static_cast<float>(inv);
+    }
+    __syncwarp();
+    // trailing update G[i][l] -= L[i][j] L[l][j] for j < l <= i < k
+    const int m = k - j - 1;
+    for (int e = lane; e < m * m; e += 32) {
+      const int i = j + 1 + e / m, l = j + 1 + e % m;
+      if (l <= i) G[i * K + l] -= G[i * K + j] * G[l * K + j];
+    }
+    __syncwarp();
+  }
+  for (int e = lane; e < K * K; e += 32) {
+    const int i = e / K, l = e % K;
+    Lf[e] = (i < k && l <= i) ? static_cast<float>(G[e]) : 0.f;
+  }
+  __syncwarp();
+  return ok;
+}
+
+// Z[r][:] = Y[r][:] L^{-T}: z_j = (y_j - sum_{p<j} z_p L[j][p]) / L[j][j], one thread per row.
+template <int K>
+__device__ void forward_rows(const float* Yin, float* Zout, const float* Lf_, const float* invd, int d, int k) {
+  // Read L through a volatile view so the compiler re-reads the broadcast
+  // shared values per row instead of holding all K(K+1)/2 of them in registers.
+  const volatile float* Lf = Lf_;
+  for (int r = threadIdx.x; r < d; r += kT) {
+    float y[K];
+    const float4* src = reinterpret_cast<const float4*>(Yin + int64_t(r) * K);
+#pragma unroll
+    for (int q = 0; q < K / 4; ++q) {
+      const float4 v = src[q];
+      y[4 * q] = v.x; y[4 * q + 1] = v.y; y[4 * q + 2] = v.z; y[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      float s = y[j];
+#pragma unroll
+      for (int p = 0; p < j; ++p) s = fmaf(-y[p], Lf[j * K + p], s);
+      y[j] = j < k ? s * invd[j] : 0.f;
+    }
+    float4* dst = reinterpret_cast<float4*>(Zout + int64_t(r) * K);
+#pragma unroll
+    for (int q = 0; q < K / 4; ++q) dst[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
   }
 }
 
+template <int K>
 __global__ void __launch_bounds__(kT) cholqr2_kernel(const float* __restrict__ Yall, float* __restrict__ Zall, int d,
-                                                     int k, int K, int* status) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  double* G = reinterpret_cast<double*>(sm);
-  double* L = G + K * K;
-  double* X = L + K * K;
-  float* Ri = reinterpret_cast<float*>(X + K * K);
-  float* chunk = Ri + K * K;
+                                                     int k, int* status) {
+  __shared__ __align__(16) double G[K * K];
+  __shared__ __align__(16) float Lf[K * K];
+  __shared__ float invd[K];
+  __shared__ __align__(16) float chunk[kChunk * K];
   const float* Y = Yall + int64_t(blockIdx.x) * d * K;
   float* Z = Zall + int64_t(blockIdx.x) * d * K;
-  const int t = threadIdx.x;
   for (int pass = 0; pass < 2; ++pass) {
     const float* src = pass == 0 ? Y : Z;
-    gram_fp32(src, d, k, K, chunk, G);
-    if (t < 32) {
-      for (int e = t; e < K * K; e += 32) { L[e] = 0.0; X[e] = 0.0; }
-      __syncwarp();
-      const bool ok = warp_cholesky(G, L, k, K);
-      if (!ok && t == 0) atomicOr(status, ST_CHOL);
-      warp_lower_inverse(L, X, k, K);
-      for (int e = t; e < K * K; e += 32) {
-        const int p = e / K, j = e % K;  // Ri = (L^{-1})^T, upper triangular
-        Ri[e] = (p < k && j < k && p <= j) ? static_cast<float>(X[j * K + p]) : 0.f;
-      }
+    gram_fp32<K>(src, d, chunk, G);
+    if (threadIdx.x < 32) {
+      const bool ok = warp_cholesky_rl<K>(G, Lf, invd, k);
+      if (!ok && threadIdx.x == 0) atomicOr(status, ST_CHOL);
     }
     __syncthreads();
-    tri_solve_rows(src, Z, Ri, d, k, K);
+    forward_rows<K>(src, Z, Lf, invd, d, k);
     __syncthreads();
   }
 }
-
-size_t cholqr2_smem(int K) { return size_t(3) * K * K * 8 + size_t(K) * K * 4 + size_t(kChunk) * K * 4 + 16; }
 
 // ---------------------------------------------------------------- align
 // One CTA per partition.  G_i (K x K float, row-major) = D_i (sign) or O_i (OPT).
@@ -450,8 +491,12 @@ cudaError_t launch_reduce(const float* P, const int* slot_begin, const float* sc
 }
 
 cudaError_t launch_cholqr2(const float* Y, float* Z, int batch, int d, int k, int K, int* status, cudaStream_t s) {
-  const size_t sm = cholqr2_smem(K);
-  cholqr2_kernel<<<batch, kT, sm, s>>>(Y, Z, d, k, K, status);
+  switch (K) {
+    case 8: cholqr2_kernel<8><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
+    case 16: cholqr2_kernel<16><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
+    case 32: cholqr2_kernel<32><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
