@@ -297,6 +297,262 @@ __global__ void __launch_bounds__(kThreads, 1) step_simt_kernel(StepArgs a, Geo 
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 kernel, second design (512 threads).  Phase 1 maps a warp onto all
+// (R/4) x (K/4) micro-tiles of W for 32/MT d-slices, so lanes that share rows
+// (or output columns) read the same shared-memory words and the reads
+// broadcast: about 8 wavefronts per 64 FMAs instead of 24.  The slices of a
+// warp are combined with shuffles, the warps through shared memory.  A's
+// shared row stride is 8 floats past a multiple of 32 and Z's 4-row blocks
+// swap row pairs on odd quads, which keeps both read patterns conflict free.
+// Phase 2 is the design above with two columns per thread.
+constexpr int kThreads2 = 512;
+
+struct Geo2 {
+  int S;    // d-slices (16 warps x slices per warp)
+  int Qp;   // quads, padded to a multiple of S
+  int lds;  // A tile row stride (floats)
+};
+
+template <int K, int R>
+struct Simt2 {
+  static constexpr int MT = (R / 4) * (K / 4);  // micro-tiles
+  static constexpr int SPW = 32 / MT;           // slices per warp
+  static_assert(MT <= 32 && 32 % MT == 0, "micro-tiles must tile a warp");
+  static Geo2 geo(int d, int64_t ld) {
+    Geo2 g;
+    g.S = 16 * SPW;
+    const int q = (d + 3) / 4;
+    g.Qp = g.S * ((q + g.S - 1) / g.S);
+    int l = static_cast<int>(ld) > 4 * g.Qp ? static_cast<int>(ld) : 4 * g.Qp;
+    g.lds = (l + 31) / 32 * 32 + 8;
+    return g;
+  }
+  static size_t bytes(const Geo2& g) {
+    return size_t(4) * (2 * R * g.lds + 4 * g.Qp * K + 16 * MT * 16 + R * K) + 16;
+  }
+};
+
+template <int K, int CPT, int R>
+__global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Geo2 g) {
+  using G2 = Simt2<K, R>;
+  constexpr int MT = G2::MT, SPW = G2::SPW, RG = R / 4;
+  extern __shared__ __align__(16) float sm2[];
+  float* buf0 = sm2;
+  float* buf1 = buf0 + R * g.lds;
+  float* Zs = buf1 + R * g.lds;
+  float* red = Zs + 4 * g.Qp * K;
+  float* Ws = red + 16 * MT * 16;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int d = a.d;
+  const float* A = static_cast<const float*>(a.A);
+  const int cpr = static_cast<int>(a.ld / 4);  // 16-byte chunks per row
+  const int sp = lane / MT, mt = lane % MT;
+  const int rg = mt / (K / 4), jg = mt % (K / 4);
+  const int s_id = warp * SPW + sp;
+  const int nq = g.Qp / g.S;
+
+  for (int r = 0; r < R; ++r)
+    for (int c = static_cast<int>(a.ld) + tid; c < g.lds; c += kThreads2) {
+      buf0[r * g.lds + c] = 0.f;
+      buf1[r * g.lds + c] = 0.f;
+    }
+
+  float y[CPT][K];
+#pragma unroll
+  for (int q = 0; q < CPT; ++q)
+#pragma unroll
+    for (int j = 0; j < K; ++j) y[q][j] = 0.f;
+
+  int cur_part = -1;
+  const int sb = a.seg_ptr[blockIdx.x], se = a.seg_ptr[blockIdx.x + 1];
+  for (int si = sb; si < se; ++si) {
+    const Segment sg = a.segs[si];
+    const int ntiles = static_cast<int>((sg.row1 - sg.row0 + R - 1) / R);
+    if (sg.part != cur_part) {
+      __syncthreads();
+      cur_part = sg.part;
+      const float* Zg = a.Z + a.z_stride * sg.part;
+      for (int e = tid; e < g.Qp * 4 * (K / 4); e += kThreads2) {
+        const int c = e / (K / 4), jz = e % (K / 4);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < d) v = *reinterpret_cast<const float4*>(Zg + size_t(c) * K + 4 * jz);
+        const int q = c >> 2, i = c & 3;
+        *reinterpret_cast<float4*>(Zs + (size_t(q) * 4 + (i ^ (q & 1))) * K + 4 * jz) = v;
+      }
+    }
+    auto issue = [&](int t, float* buf) {
+      const int64_t r0 = sg.row0 + int64_t(t) * R;
+      for (int e = tid; e < R * cpr; e += kThreads2) {
+        const int r = e / cpr, ch = e % cpr;
+        const int64_t grow = r0 + r;
+        const bool ok = grow < sg.row1;
+        cp_async16(buf + size_t(r) * g.lds + ch * 4, A + (ok ? grow : sg.row0) * a.ld + int64_t(ch) * 4, ok ? 16 : 0);
+      }
+      cp_async_commit();
+    };
+    issue(0, buf0);
+    for (int t = 0; t < ntiles; ++t) {
+      const float* T = (t & 1) ? buf1 : buf0;
+      if (t + 1 < ntiles) {
+        issue(t + 1, (t & 1) ? buf0 : buf1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+
+      // ---- phase 1: rows {rg + RG*aa}, columns {4jg .. 4jg+3}, quads q = s_id + S*u
+      float acc[4][4];
+#pragma unroll
+      for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[aa][b] = 0.f;
+#pragma unroll 2
+      for (int u = 0; u < nq; ++u) {
+        const int q = s_id + g.S * u;
+        float4 av[4];
+#pragma unroll
+        for (int aa = 0; aa < 4; ++aa)
+          av[aa] = *reinterpret_cast<const float4*>(T + size_t(rg + RG * aa) * g.lds + 4 * q);
+        const float* zq = Zs + size_t(q) * 4 * K + 4 * jg;
+        const int sw = q & 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 z = *reinterpret_cast<const float4*>(zq + (i ^ sw) * K);
+#pragma unroll
+          for (int aa = 0; aa < 4; ++aa) {
+            const float ai = i == 0 ? av[aa].x : i == 1 ? av[aa].y : i == 2 ? av[aa].z : av[aa].w;
+            acc[aa][0] = fmaf(ai, z.x, acc[aa][0]);
+            acc[aa][1] = fmaf(ai, z.y, acc[aa][1]);
+            acc[aa][2] = fmaf(ai, z.z, acc[aa][2]);
+            acc[aa][3] = fmaf(ai, z.w, acc[aa][3]);
+          }
+        }
+      }
+      // slices of this warp -> lane group sp == 0
+#pragma unroll
+      for (int off = MT; off < 32; off <<= 1)
+#pragma unroll
+        for (int aa = 0; aa < 4; ++aa)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[aa][b] += __shfl_xor_sync(0xffffffffu, acc[aa][b], off);
+      if (sp == 0) {
+        float* dst = red + (size_t(warp) * MT + mt) * 16;
+#pragma unroll
+        for (int aa = 0; aa < 4; ++aa)
+          *reinterpret_cast<float4*>(dst + 4 * aa) = make_float4(acc[aa][0], acc[aa][1], acc[aa][2], acc[aa][3]);
+      }
+      __syncthreads();
+      for (int e = tid; e < R * K; e += kThreads2) {
+        const int r = e / K, j = e % K;
+        const int m2 = (r % RG) * (K / 4) + j / 4, el = (r / RG) * 4 + (j & 3);
+        float sum = 0.f;
+#pragma unroll 4
+        for (int w = 0; w < 16; ++w) sum += red[(size_t(w) * MT + m2) * 16 + el];
+        Ws[e] = sum;
+      }
+      __syncthreads();
+
+      // ---- phase 2: Y += T^T W
+#pragma unroll 2
+      for (int r = 0; r < R; ++r) {
+        float w[K];
+#pragma unroll
+        for (int j = 0; j < K; j += 4) {
+          const float4 v = *reinterpret_cast<const float4*>(Ws + r * K + j);
+          w[j] = v.x; w[j + 1] = v.y; w[j + 2] = v.z; w[j + 3] = v.w;
+        }
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+          const int c = tid + kThreads2 * q;
+          if (c < d) {
+            const float av = T[size_t(r) * g.lds + c];
+#pragma unroll
+            for (int j = 0; j < K; ++j) y[q][j] = fmaf(av, w[j], y[q][j]);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    float* Pd = a.P + size_t(sg.slot) * d * K;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int c = tid + kThreads2 * q;
+      if (c < d) {
+#pragma unroll
+        for (int j = 0; j < K; j += 4)
+          *reinterpret_cast<float4*>(Pd + size_t(c) * K + j) = make_float4(y[q][j], y[q][j + 1], y[q][j + 2], y[q][j + 3]);
+      }
+#pragma unroll
+      for (int j = 0; j < K; ++j) y[q][j] = 0.f;
+    }
+  }
+}
+
+constexpr size_t kSmemLimit2 = 227 * 1024;
+
+template <int K, int CPT, int R>
+cudaError_t launch_two(const StepArgs& a, const Geo2& g, size_t bytes, cudaStream_t s) {
+  auto kern = step_simt2_kernel<K, CPT, R>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  if (e != cudaSuccess) return e;
+  kern<<<a.grid, kThreads2, bytes, s>>>(a, g);
+  return cudaGetLastError();
+}
+
+// Chooses the row tile (16, else 8) whose shared memory fits; returns false if none.
+template <int K>
+bool simt2_pick(int d, int64_t ld, int* R, Geo2* g, size_t* bytes) {
+  if (d > 2 * kThreads2 || (d + kThreads2 - 1) / kThreads2 * K > 64) return false;
+  const Geo2 g16 = Simt2<K, 16>::geo(d, ld);
+  if (32 % Simt2<K, 16>::MT == 0 && Simt2<K, 16>::bytes(g16) <= kSmemLimit2) {
+    *R = 16; *g = g16; *bytes = Simt2<K, 16>::bytes(g16);
+    return true;
+  }
+  const Geo2 g8 = Simt2<K, 8>::geo(d, ld);
+  if (Simt2<K, 8>::bytes(g8) <= kSmemLimit2) {
+    *R = 8; *g = g8; *bytes = Simt2<K, 8>::bytes(g8);
+    return true;
+  }
+  return false;
+}
+
+template <int K>
+cudaError_t launch_v2(const StepArgs& a, cudaStream_t s) {
+  int R;
+  Geo2 g;
+  size_t bytes;
+  if (!simt2_pick<K>(a.d, a.ld, &R, &g, &bytes)) return cudaErrorInvalidConfiguration;
+  const bool two = a.d > kThreads2;
+  if (R == 16) return two ? launch_two<K, 2, 16>(a, g, bytes, s) : launch_two<K, 1, 16>(a, g, bytes, s);
+  return two ? launch_two<K, 2, 8>(a, g, bytes, s) : launch_two<K, 1, 8>(a, g, bytes, s);
+}
+
+bool v2_supported(int d, int64_t ld, int K) {
+  int R;
+  Geo2 g;
+  size_t b;
+  switch (K) {
+    case 8: return simt2_pick<8>(d, ld, &R, &g, &b);
+    case 16: return simt2_pick<16>(d, ld, &R, &g, &b);
+    case 32: return simt2_pick<32>(d, ld, &R, &g, &b);
+  }
+  return false;
+}
+
+cudaError_t launch_f32(const StepArgs& a, int K, cudaStream_t s) {
+  if (v2_supported(a.d, a.ld, K)) {
+    switch (K) {
+      case 8: return launch_v2<8>(a, s);
+      case 16: return launch_v2<16>(a, s);
+      case 32: return launch_v2<32>(a, s);
+    }
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
 template <typename Tin, int K, int CPT, int R>
 cudaError_t launch_one(const StepArgs& a, cudaStream_t s) {
   const Geo g = make_geo(a.d, a.ld, R, K, sizeof(Tin));
@@ -361,7 +617,7 @@ size_t smem_for(int d, int64_t ld, int K, int* rows) {
 
 cudaError_t launch_step_simt(const StepArgs& a, lp_dtype dtype, int K, cudaStream_t s) {
   switch (dtype) {
-    case LP_F32: return launch_k<float>(a, K, s);
+    case LP_F32: return v2_supported(a.d, a.ld, K) ? launch_f32(a, K, s) : launch_k<float>(a, K, s);
     case LP_BF16: return launch_k<uint16_t>(a, K, s);
     case LP_FP8_E4M3: return launch_k<uint8_t>(a, K, s);
   }
