@@ -139,7 +139,8 @@ lp_status lp_result(lp_ctx* ctx, double* z_out, double* sigma_out, lp_stats* sta
 void lp_destroy(lp_ctx* ctx);
 
 /* lp_last_error: text of the last failure on this context ("" if none); valid
- * until the next call on the context.  With ctx == NULL: the last lp_create failure. */
+ * until the next call on the context.  With ctx == NULL: the last failure of a
+ * call that has no context (lp_create, lp_power_step_static) on this thread. */
 const char* lp_last_error(const lp_ctx* ctx);
 
 /* ----------------------------------------------------------------------------
@@ -175,6 +176,37 @@ lp_status lp_orth(lp_ctx* ctx, int batch, int64_t d, int k, const double* y, dou
 lp_status lp_align_aggregate(lp_ctx* ctx, int m, int64_t d, int k, lp_aggregator agg, int base,
                              const double* w, const double* ys, const double* zs,
                              double* y_out, double* d_out, lp_ptr_space space);
+
+/* ----------------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart: this call exists
+ * for callers that cannot allocate device memory.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * lp_power_step_static: the local power step Y_i = (1/s_i) A_i^T (A_i Z) of
+ * lp_power_step with one Z shared by every partition, run without any device
+ * allocation and without a context.  It is meant for callers that must not
+ * allocate: code running inside a memory pool or allocator it cannot re-enter,
+ * a host that has reserved the device's memory up front, or a place where a
+ * cudaMalloc would synchronise the device at the wrong moment.  Its scratch
+ * (partial sums, row-segment table, padded Z and Y) lives in one 32 MiB array
+ * inside the library, held on every GPU that loads the library until exit.
+ *   A       device, FP32: the m partitions back to back, row-major, row pitch
+ *           d; d a multiple of 4 and A 16-byte aligned.
+ *   rows    host, m row counts s_i >= 1, with k <= min s_i.
+ *   z       device, d x k FP64 row-major.
+ *   y       device, m consecutive d x k FP64 blocks (output).
+ *   stream  cudaStream_t to launch on (NULL: the legacy default stream).
+ * Asynchronous: y holds the result once the stream passes this call's work.
+ * A problem whose scratch would exceed the array fails with LP_ERR_INVALID
+ * and launches nothing; lp_last_error(NULL) describes any failure.  The first
+ * call on a device (made with that device current) looks up the array's
+ * device address; make that first call before any stream capture.  Every call
+ * shares the one array, which keeps the last call's contents: each call
+ * writes everything it reads, but calls whose work overlaps on the GPU race.
+ */
+lp_status lp_power_step_static(const float* A, int m, const int64_t* rows, int64_t d, int k, const double* z,
+                               double* y, void* stream);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,7 @@ DTYPE = {"f32": LP_F32, "bf16": LP_BF16, "e4m3": LP_FP8_E4M3}
 
 # Every symbol the header declares, in declaration order.
 EXPORTS = ["lp_create", "lp_load_partitions", "lp_solve", "lp_result", "lp_destroy", "lp_last_error",
-           "lp_power_step", "lp_orth", "lp_align_aggregate"]
+           "lp_power_step", "lp_orth", "lp_align_aggregate", "lp_power_step_static"]
 
 
 class lp_stats(C.Structure):
@@ -77,6 +77,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
     L.lp_power_step.argtypes = [P, I, P, I, P, I]
     L.lp_orth.argtypes = [P, I, I64, I, P, P, I]
     L.lp_align_aggregate.argtypes = [P, I, I64, I, I, I, P, P, P, P, P, I]
+    L.lp_power_step_static.argtypes = [P, I, C.POINTER(I64), I64, I, P, P, P]
     for name in EXPORTS:
         if name not in ("lp_destroy", "lp_last_error"):
             getattr(L, name).restype = C.c_int
@@ -224,6 +225,22 @@ def lp_align_aggregate(ctx, agg: str, base: int, w, Ys, Zs):
                                      C.c_void_p(Ys.ctypes.data), C.c_void_p(Zs.ctypes.data),
                                      C.c_void_p(Y.ctypes.data), C.c_void_p(D.ctypes.data), LP_HOST))
     return Y, D
+
+
+def lp_power_step_static(A, rows, k: int, z, y, stream=None) -> None:
+    """The allocation-free power step: A (CUDA float32 tensor, partitions back to
+    back), rows (the s_i), z (CUDA float64 d x k), y (CUDA float64 (m, d, k),
+    written).  Asynchronous on ``stream`` (a torch stream or None)."""
+    L = load()
+    for t in (A, z, y):
+        if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+            raise ValueError("A, z and y must be contiguous CUDA tensors")
+    m = len(rows)
+    r = (C.c_int64 * m)(*[int(x) for x in rows])
+    s = C.c_void_p(stream.cuda_stream) if stream is not None else C.c_void_p(None)
+    status = L.lp_power_step_static(C.c_void_p(A.data_ptr()), m, r, int(A.shape[1]), int(k),
+                                    C.c_void_p(z.data_ptr()), C.c_void_p(y.data_ptr()), s)
+    _check(None, status)
 
 
 # --------------------------------------------------------------------------- convenience

@@ -292,6 +292,8 @@ lp_status check_launch(lp_ctx* c, cudaError_t e, const char* what) {
 
 }  // namespace
 
+void lp::set_no_context_error(const char* msg) { g_create_err = msg; }
+
 // =============================================================================
 extern "C" {
 

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <string>
 
 #include "localpower.h"
 
@@ -58,6 +59,10 @@ bool tc_plan(int d, int k, int sms, TcPlan* p);
 cudaError_t tc_encode_map(void* A, int64_t n, int d, int64_t ld, TcPlan* p);
 cudaError_t launch_step_tc(const TcPlan& p, const Segment* segs, const int* seg_ptr, const float* Z, int64_t z_stride,
                            float* P, int d, int* status, cudaStream_t s);
+
+// Message returned by lp_last_error(NULL) (failures of calls without a context).
+void set_no_context_error(const char* msg);
+inline void set_no_context_error(const std::string& msg) { set_no_context_error(msg.c_str()); }
 
 // ---- small kernels --------------------------------------------------------
 // Y_i = scale_i * sum_{slot in [slot_begin[i], slot_begin[i+1])} P[slot]
