@@ -190,12 +190,23 @@ def _timed(torch, dist, world, dev, stream, lp, k, sched, agg, steps, clocks=Non
     ev1.record(stream)
     barrier()
     clk = clocks.stop() if clocks else None
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, dist, world, dev, ev0.elapsed_time(ev1))
     return ms, stats, Z, sig, clk
+
+
+def max_over_ranks(torch, dist, world, dev, ms: float) -> float:
+    """The slowest rank's time (every rank gets it); the identity at world == 1."""
+    if world <= 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, bytes_per_solve: float, ms: float) -> tuple[float, float]:
+    """Whole-job (GB/s, solves/s): every rank solves `steps` problems of
+    `bytes_per_solve` algorithmic bytes; `ms` is the slowest rank's time."""
+    return world * steps * bytes_per_solve / (ms / 1e3) / 1e9, world * steps / (ms / 1e3)
 
 
 def _summary(world, steps, ms, stats, elem_bytes, c):
@@ -203,8 +214,9 @@ def _summary(world, steps, ms, stats, elem_bytes, c):
     bytes_solve = stats[-1]["a_bytes"]
     lat = sorted(s["ms_solve"] for s in stats)
     step_ms = sum(s["ms_step_kernels"] for s in stats) / sum(s["step_launches"] for s in stats)
-    return {"gbs": world * steps * bytes_solve / (ms / 1e3) / 1e9,
-            "solves_per_s": world * steps / (ms / 1e3),
+    gbs, sps = job_throughput(world, steps, bytes_solve, ms)
+    return {"gbs": gbs,
+            "solves_per_s": sps,
             "ms_per_solve": ms / steps,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "samples": len(lat)},
@@ -281,12 +293,8 @@ def run_ours(args):
         del pinned, host_parts
     e2e = None
     if e2e_ms:
-        e2e_t = max(e2e_ms)
-        if world > 1:
-            t = torch.tensor([e2e_t], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_t = float(t.item())
-        e2e = {"value": world * f32["bytes_solve"] / (e2e_t / 1e3) / 1e9, "unit": "GB/s",
+        e2e_t = max_over_ranks(torch, dist, world, dev, max(e2e_ms))
+        e2e = {"value": job_throughput(world, 1, f32["bytes_solve"], e2e_t)[0], "unit": "GB/s",
                "h2d_bytes_per_step": int(A.nbytes + Y0.nbytes), "d2h_bytes_per_step": int(d * k * 8 + 8 * k),
                "ms_per_step": e2e_t}
     lp.close()

@@ -88,13 +88,18 @@ __device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
   return r;
 }
-__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
-  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+// Bulk copy shared::cta -> another CTA's shared memory; completion is counted in
+// bytes on the destination CTA's mbarrier.  Addresses 16-byte aligned, size a
+// multiple of 16.
+__device__ __forceinline__ void bulk_s2s_cluster(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "r"(src), "r"(bytes), "r"(mbar)
+               : "memory");
 }
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
-}
-__device__ __forceinline__ void fence_cluster() { asm volatile("fence.acq_rel.cluster;" ::: "memory"); }
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Named barrier of the four epilogue warps.
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -165,13 +170,16 @@ struct TcLayout {
   static constexpr int STAGE = NCH * kChunkBytes;
   static constexpr int B1 = NCH * N * 128;
   static constexpr int B2 = 2 * N * 128;
+  static constexpr int NB2BUF = K == 32 ? 1 : 2;  // W operand buffers (one at K = 32 to fit shared memory)
   static constexpr int NB2 = NCH / 2;
+  static constexpr int KS = K + 4;                  // W row stride in floats: 16-byte rows, odd in 16-byte units
+  static constexpr int WBYTES = kBM * KS * 4;
   static constexpr int off_A = 0;
   static constexpr int off_B1 = off_A + 2 * STAGE;
   static constexpr int off_B2 = off_B1 + B1;
-  static constexpr int off_Wred = off_B2 + 2 * B2;
-  static constexpr int off_Wfull = off_Wred + kBM * K * 4;
-  static constexpr int off_bar = off_Wfull + kBM * K * 4;
+  static constexpr int off_W = off_B2 + NB2BUF * B2;   // partial W rows, then the cluster sum in place
+  static constexpr int off_Wrecv = off_W + WBYTES;      // partials received for the rows this CTA owns
+  static constexpr int off_bar = off_Wrecv + WBYTES;
   static constexpr int kBars = 16;
   static constexpr int bytes = off_bar + kBars * 8 + 16;
   static constexpr int alloc_bytes = bytes + 1024;  // room to align the base to 1024
@@ -193,8 +201,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
   unsigned char* sA = base + L::off_A;
   unsigned char* sB1 = base + L::off_B1;
   unsigned char* sB2 = base + L::off_B2;
-  float* sWred = reinterpret_cast<float*>(base + L::off_Wred);
-  float* sWfull = reinterpret_cast<float*>(base + L::off_Wfull);
+  float* sW = reinterpret_cast<float*>(base + L::off_W);
+  float* sWrecv = reinterpret_cast<float*>(base + L::off_Wrecv);
   uint64_t* bar = reinterpret_cast<uint64_t*>(base + L::off_bar);
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + L::kBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
@@ -216,8 +224,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
       mbar_init(&bar[B_B2FREE0 + s], 1);
     }
     mbar_init(&bar[B_D2FULL], 1);
-    mbar_init(&bar[B_REDFULL], kBM);
-    mbar_init(&bar[B_WFULL], 4 * CL);
+    mbar_init(&bar[B_REDFULL], 1);  // local expect_tx + bytes of the peers' partial rows
+    mbar_init(&bar[B_WFULL], 1);    // local expect_tx + bytes of the owners' summed rows
     mbar_init(&bar[B_DONE], 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -303,10 +311,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
         return true;
       };
       auto c2 = [&](uint32_t Tg, bool first) -> bool {
-        const uint32_t s = Tg & 1, b = Tg & 1;
-        if (!wait(B_B2FULL0 + b, (Tg >> 1) & 1, false)) return false;
+        const uint32_t s = Tg & 1, bb = Tg % L::NB2BUF;
+        if (!wait(B_B2FULL0 + bb, (Tg / L::NB2BUF) & 1, false)) return false;
         tc_fence_after();
-        const uint32_t aS = su32(sA + s * L::STAGE), bS = su32(sB2 + b * L::B2);
+        const uint32_t aS = su32(sA + s * L::STAGE), bS = su32(sB2 + bb * L::B2);
 #pragma unroll
         for (int mb = 0; mb < L::NB2; ++mb)
 #pragma unroll
@@ -317,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
             mma_bf16(tmem + 2 * N + mb * N, ad, bd, idesc2, (first && kk == 0) ? 0u : 1u);
           }
         mma_commit(&bar[B_EMPTY0 + s]);
-        mma_commit(&bar[B_B2FREE0 + b]);
+        mma_commit(&bar[B_B2FREE0 + bb]);
         return true;
       };
       bool ok = c1(T);
@@ -356,34 +364,58 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
           for (int j = 0; j < K; ++j) w[j] = 0.f;
         }
         if (CL > 1) {
-          // partial row r -> its owner's reduction slots
-          const uint32_t owner = static_cast<uint32_t>(r / RPC);
-          const uint32_t dst = mapa(su32(sWred + (crank * RPC + (r % RPC)) * K), owner);
+          // Cluster sum of W.  Owner o holds rows [o*RPC, (o+1)*RPC).  Every CTA
+          // writes its partial rows to sW and one thread ships each owner its
+          // rows (bulk DSMEM copies, counted in bytes on the owner's barrier);
+          // owners add the partials in source-rank order, in place in sW, and
+          // ship the sums back the same way.  Peers' data land only in rows
+          // whose earlier contents were already consumed (see the waits).
+          const uint32_t rows_bytes = static_cast<uint32_t>(RPC * L::KS * 4);
+          float* wr = sW + r * L::KS;
 #pragma unroll
-          for (int j = 0; j < K; ++j) st_cluster_f32(dst + 4 * j, w[j]);
-          mbar_arrive_remote(mapa(su32(&bar[B_REDFULL]), owner));
-          // owner: sum this CTA's RPC rows over the cluster, broadcast the sums
-          if (!(ok = wait(B_REDFULL, Tg & 1, true))) break;
-          const int per = RPC * K / kBM;  // values per epilogue thread
-          const int v0 = r * per;
-          for (int e = 0; e < per; ++e) {
-            const int idx = v0 + e, rl = idx / K, col = idx % K;
-            float s = 0.f;
-            for (uint32_t src = 0; src < CL; ++src) s += sWred[(src * RPC + rl) * K + col];
-            const uint32_t loc = su32(sWfull + (crank * RPC + rl) * K + col);
-            for (uint32_t dsti = 0; dsti < CL; ++dsti) st_cluster_f32(mapa(loc, dsti), s);
+          for (int j = 0; j < K; j += 4) *reinterpret_cast<float4*>(wr + j) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+          fence_async_smem();
+          epi_bar();
+          if (r == 0) {
+            mbar_expect_tx(&bar[B_REDFULL], (CL - 1) * rows_bytes);
+            for (uint32_t o = 0; o < CL; ++o)
+              if (o != crank)
+                bulk_s2s_cluster(mapa(su32(sWrecv + crank * RPC * L::KS), o), su32(sW + o * RPC * L::KS), rows_bytes,
+                                 mapa(su32(&bar[B_REDFULL]), o));
+            bulk_commit();
+            bulk_wait_read0();
           }
-          fence_cluster();
-          __syncwarp();
-          if (lane == 0)
-            for (uint32_t dsti = 0; dsti < CL; ++dsti) mbar_arrive_remote(mapa(su32(&bar[B_WFULL]), dsti));
+          if (!(ok = wait(B_REDFULL, Tg & 1, true))) break;
+          const int per = RPC * K / kBM;  // values per epilogue thread (K / CL)
+          for (int e = 0; e < per; ++e) {
+            const int idx = r * per + e, rl = idx / K, col = idx % K;
+            float s = 0.f;
+            for (uint32_t src = 0; src < CL; ++src)
+              s += src == crank ? sW[(crank * RPC + rl) * L::KS + col] : sWrecv[(src * RPC + rl) * L::KS + col];
+            sW[(crank * RPC + rl) * L::KS + col] = s;
+          }
+          fence_async_smem();
+          epi_bar();
+          if (r == 0) {
+            mbar_expect_tx(&bar[B_WFULL], (CL - 1) * rows_bytes);
+            for (uint32_t dsti = 0; dsti < CL; ++dsti)
+              if (dsti != crank)
+                bulk_s2s_cluster(mapa(su32(sW + crank * RPC * L::KS), dsti), su32(sW + crank * RPC * L::KS),
+                                 rows_bytes, mapa(su32(&bar[B_WFULL]), dsti));
+            bulk_commit();
+            bulk_wait_read0();
+          }
           if (!(ok = wait(B_WFULL, Tg & 1, true))) break;
 #pragma unroll
-          for (int j = 0; j < K; ++j) w[j] = sWfull[r * K + j];
+          for (int j = 0; j < K; j += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(wr + j);
+            w[j] = v.x; w[j + 1] = v.y; w[j + 2] = v.z; w[j + 3] = v.w;
+          }
         }
-        // [W_hi | W_lo]^T into B2[b]: row n = output column, k-index = tile row r
-        if (!(ok = wait(B_B2FREE0 + b, ((Tg >> 1) + 1) & 1, false))) break;
-        unsigned char* B2 = sB2 + b * L::B2;
+        // [W_hi | W_lo]^T into B2: row n = output column, k-index = tile row r
+        const uint32_t bb = Tg % L::NB2BUF;
+        if (!(ok = wait(B_B2FREE0 + bb, ((Tg / L::NB2BUF) + 1) & 1, false))) break;
+        unsigned char* B2 = sB2 + bb * L::B2;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
           const uint16_t hi = bf16_bits(w[j]);
@@ -392,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
           *reinterpret_cast<uint16_t*>(B2 + sw128_off(K + j, r, N)) = lo;
         }
         fence_async_smem();
-        mbar_arrive(&bar[B_B2FULL0 + b]);
+        mbar_arrive(&bar[B_B2FULL0 + bb]);
       }
       // segment end: Y slice = D2[:, :K] + D2[:, K:] -> P[slot]
       if (ok && wait(B_D2FULL, (si - sb) & 1, false)) {
