@@ -359,11 +359,11 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
       buf1[r * g.lds + c] = 0.f;
     }
 
-  float y[CPT][K];
+  float2 y[CPT][K / 2];
 #pragma unroll
   for (int q = 0; q < CPT; ++q)
 #pragma unroll
-    for (int j = 0; j < K; ++j) y[q][j] = 0.f;
+    for (int j = 0; j < K / 2; ++j) y[q][j] = make_float2(0.f, 0.f);
 
   int cur_part = -1;
   const int sb = a.seg_ptr[blockIdx.x], se = a.seg_ptr[blockIdx.x + 1];
@@ -404,11 +404,13 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
       __syncthreads();
 
       // ---- phase 1: rows {rg + RG*aa}, columns {4jg .. 4jg+3}, quads q = s_id + S*u
-      float acc[4][4];
+      // (packed FP32 FMAs: two output columns per instruction)
+      float2 acc[4][2];
 #pragma unroll
-      for (int aa = 0; aa < 4; ++aa)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[aa][b] = 0.f;
+      for (int aa = 0; aa < 4; ++aa) {
+        acc[aa][0] = make_float2(0.f, 0.f);
+        acc[aa][1] = make_float2(0.f, 0.f);
+      }
 #pragma unroll 2
       for (int u = 0; u < nq; ++u) {
         const int q = s_id + g.S * u;
@@ -421,13 +423,13 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const float4 z = *reinterpret_cast<const float4*>(zq + (i ^ sw) * K);
+          const float2 z01 = make_float2(z.x, z.y), z23 = make_float2(z.z, z.w);
 #pragma unroll
           for (int aa = 0; aa < 4; ++aa) {
             const float ai = i == 0 ? av[aa].x : i == 1 ? av[aa].y : i == 2 ? av[aa].z : av[aa].w;
-            acc[aa][0] = fmaf(ai, z.x, acc[aa][0]);
-            acc[aa][1] = fmaf(ai, z.y, acc[aa][1]);
-            acc[aa][2] = fmaf(ai, z.z, acc[aa][2]);
-            acc[aa][3] = fmaf(ai, z.w, acc[aa][3]);
+            const float2 a2 = make_float2(ai, ai);
+            acc[aa][0] = __ffma2_rn(a2, z01, acc[aa][0]);
+            acc[aa][1] = __ffma2_rn(a2, z23, acc[aa][1]);
           }
         }
       }
@@ -437,12 +439,15 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
 #pragma unroll
         for (int aa = 0; aa < 4; ++aa)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) acc[aa][b] += __shfl_xor_sync(0xffffffffu, acc[aa][b], off);
+          for (int h = 0; h < 2; ++h) {
+            acc[aa][h].x += __shfl_xor_sync(0xffffffffu, acc[aa][h].x, off);
+            acc[aa][h].y += __shfl_xor_sync(0xffffffffu, acc[aa][h].y, off);
+          }
       if (sp == 0) {
         float* dst = red + (size_t(warp) * MT + mt) * 16;
 #pragma unroll
         for (int aa = 0; aa < 4; ++aa)
-          *reinterpret_cast<float4*>(dst + 4 * aa) = make_float4(acc[aa][0], acc[aa][1], acc[aa][2], acc[aa][3]);
+          *reinterpret_cast<float4*>(dst + 4 * aa) = make_float4(acc[aa][0].x, acc[aa][0].y, acc[aa][1].x, acc[aa][1].y);
       }
       __syncthreads();
       for (int e = tid; e < R * K; e += kThreads2) {
@@ -455,22 +460,24 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
       }
       __syncthreads();
 
-      // ---- phase 2: Y += T^T W
+      // ---- phase 2: Y += T^T W (packed FP32 FMAs)
 #pragma unroll 2
       for (int r = 0; r < R; ++r) {
-        float w[K];
+        float2 w[K / 2];
 #pragma unroll
         for (int j = 0; j < K; j += 4) {
           const float4 v = *reinterpret_cast<const float4*>(Ws + r * K + j);
-          w[j] = v.x; w[j + 1] = v.y; w[j + 2] = v.z; w[j + 3] = v.w;
+          w[j / 2] = make_float2(v.x, v.y);
+          w[j / 2 + 1] = make_float2(v.z, v.w);
         }
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
           const int c = tid + kThreads2 * q;
           if (c < d) {
             const float av = T[size_t(r) * g.lds + c];
+            const float2 a2 = make_float2(av, av);
 #pragma unroll
-            for (int j = 0; j < K; ++j) y[q][j] = fmaf(av, w[j], y[q][j]);
+            for (int j = 0; j < K / 2; ++j) y[q][j] = __ffma2_rn(a2, w[j], y[q][j]);
           }
         }
       }
@@ -482,11 +489,12 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
       const int c = tid + kThreads2 * q;
       if (c < d) {
 #pragma unroll
-        for (int j = 0; j < K; j += 4)
-          *reinterpret_cast<float4*>(Pd + size_t(c) * K + j) = make_float4(y[q][j], y[q][j + 1], y[q][j + 2], y[q][j + 3]);
+        for (int j = 0; j < K / 2; j += 2)
+          *reinterpret_cast<float4*>(Pd + size_t(c) * K + 2 * j) = make_float4(y[q][j].x, y[q][j].y, y[q][j + 1].x,
+                                                                              y[q][j + 1].y);
       }
 #pragma unroll
-      for (int j = 0; j < K; ++j) y[q][j] = 0.f;
+      for (int j = 0; j < K / 2; ++j) y[q][j] = make_float2(0.f, 0.f);
     }
   }
 }

@@ -293,11 +293,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
       }
     } else if (warp == 1 && lane == 0) {
       // ------------------------------------------------------------ MMA issuer
-      auto c1 = [&](uint32_t Tg) -> bool {
+      // C1 of tile t+1 and C2 of tile t wait on different events (A landing vs W
+      // ready); the issuer polls both and issues whichever is ready first.
+      auto c1 = [&](uint32_t Tg) {
         const uint32_t s = Tg & 1, b = Tg & 1;
-        if (!wait(B_FULL0 + s, (Tg >> 1) & 1, false)) return false;
-        if (!wait(B_D1EMPTY0 + b, ((Tg >> 1) + 1) & 1, false)) return false;
-        tc_fence_after();
         const uint32_t aS = su32(sA + s * L::STAGE), bS = su32(sB1);
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch)
@@ -308,12 +307,9 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
             mma_bf16(tmem + b * N, ad, bd, idesc1, (ch | kk) != 0);
           }
         mma_commit(&bar[B_D1FULL0 + b]);
-        return true;
       };
-      auto c2 = [&](uint32_t Tg, bool first) -> bool {
+      auto c2 = [&](uint32_t Tg, bool first) {
         const uint32_t s = Tg & 1, bb = Tg % L::NB2BUF;
-        if (!wait(B_B2FULL0 + bb, (Tg / L::NB2BUF) & 1, false)) return false;
-        tc_fence_after();
         const uint32_t aS = su32(sA + s * L::STAGE), bS = su32(sB2 + bb * L::B2);
 #pragma unroll
         for (int mb = 0; mb < L::NB2; ++mb)
@@ -326,12 +322,39 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
           }
         mma_commit(&bar[B_EMPTY0 + s]);
         mma_commit(&bar[B_B2FREE0 + bb]);
-        return true;
       };
-      bool ok = c1(T);
-      for (int t = 0; ok && t < ntiles; ++t) {
-        if (t + 1 < ntiles && !c1(T + t + 1)) break;
-        ok = c2(T + t, t == 0);
+      auto ready = [&](int id, uint32_t parity) { return mbar_try(su32(&bar[id]), parity); };
+      int n1 = 0, n2 = 0;  // tiles of this segment whose C1 / C2 have been issued
+      long long last = clock64();
+      while (n2 < ntiles) {
+        bool progressed = false;
+        if (n1 < ntiles && n1 <= n2 + 1) {
+          const uint32_t Tg = T + n1;
+          if (ready(B_FULL0 + (Tg & 1), (Tg >> 1) & 1) && ready(B_D1EMPTY0 + (Tg & 1), ((Tg >> 1) + 1) & 1)) {
+            tc_fence_after();
+            c1(Tg);
+            ++n1;
+            progressed = true;
+          }
+        }
+        if (n2 < n1) {
+          const uint32_t Tg = T + n2;
+          if (ready(B_B2FULL0 + Tg % L::NB2BUF, (Tg / L::NB2BUF) & 1)) {
+            tc_fence_after();
+            c2(Tg, n2 == 0);
+            ++n2;
+            progressed = true;
+          }
+        }
+        if (progressed) {
+          last = clock64();
+        } else if (*abort_flag) {
+          break;
+        } else if (clock64() - last > kTimeoutCycles) {
+          *abort_flag = 1;
+          atomicOr(a.status, ST_TIMEOUT);
+          break;
+        }
       }
       mma_commit(&bar[B_D2FULL]);
     } else if (warp >= 4) {
@@ -497,6 +520,36 @@ cudaError_t launch_tc_t(const TcPlan& p, const TcArgs& a, cudaStream_t s) {
 
 }  // namespace
 
+// Clusters of `cl` CTAs that the device can hold at once for this kernel (0 if unknown).
+// Clusters must fit inside one GPC, so this can be below sms / cl; launching more
+// would run a second, mostly empty wave.
+template <int K, int NCH>
+int active_clusters(int cl) {
+  using L = TcLayout<K, NCH>;
+  auto kern = step_tc_kernel<K, NCH>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::alloc_bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(cl), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = L::alloc_bytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(cl);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
 bool tc_plan(int d, int k, int sms, TcPlan* p) {
   const int K = k <= 8 ? 8 : (k <= 16 ? 16 : 32);
   const int nch = d <= 128 ? 2 : 4;
@@ -508,11 +561,18 @@ bool tc_plan(int d, int k, int sms, TcPlan* p) {
   p->K = K;
   p->nch = nch;
   p->cluster = c2;
-  p->nclusters = sms / c2;
-  if (p->nclusters < 1) return false;
   size_t bytes;
-  if (nch == 2) bytes = K == 8 ? TcLayout<8, 2>::alloc_bytes : K == 16 ? TcLayout<16, 2>::alloc_bytes : TcLayout<32, 2>::alloc_bytes;
-  else bytes = K == 8 ? TcLayout<8, 4>::alloc_bytes : K == 16 ? TcLayout<16, 4>::alloc_bytes : TcLayout<32, 4>::alloc_bytes;
+  int active;
+  if (nch == 2) {
+    bytes = K == 8 ? TcLayout<8, 2>::alloc_bytes : K == 16 ? TcLayout<16, 2>::alloc_bytes : TcLayout<32, 2>::alloc_bytes;
+    active = K == 8 ? active_clusters<8, 2>(c2) : K == 16 ? active_clusters<16, 2>(c2) : active_clusters<32, 2>(c2);
+  } else {
+    bytes = K == 8 ? TcLayout<8, 4>::alloc_bytes : K == 16 ? TcLayout<16, 4>::alloc_bytes : TcLayout<32, 4>::alloc_bytes;
+    active = K == 8 ? active_clusters<8, 4>(c2) : K == 16 ? active_clusters<16, 4>(c2) : active_clusters<32, 4>(c2);
+  }
+  p->nclusters = sms / c2;
+  if (active > 0 && active < p->nclusters) p->nclusters = active;
+  if (p->nclusters < 1) return false;
   p->smem = bytes;
   return bytes <= 232448;
 }
