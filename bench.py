@@ -46,6 +46,9 @@ def _args():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage (tensor-core) run of the workload")
+    ap.add_argument("--workload", choices=["fp32", "lowprec"], default="fp32",
+                    help="fp32: the FP32 workload (default, with its BF16-storage run alongside); "
+                         "lowprec: the BF16-storage workload n=4e6, d=2048, k=32")
     ap.add_argument("--rows", type=int, default=None,
                     help="override n (same spectrum and partition count): a smaller case for profiler captures")
     return ap.parse_args()
@@ -113,13 +116,13 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _workload(rank: int, rows: int | None = None):
+def _workload(rank: int, rows: int | None = None, name: str = WORKLOAD):
     import synth
-    c = dict(synth.CONFIGS[WORKLOAD])
+    c = dict(synth.CONFIGS[name])
     if rows:
         c["n"] = int(rows)
-    A, sizes, Y0 = synth.make_config_data(WORKLOAD, n=c["n"])
-    return c, A, sizes, Y0, synth.config_schedule(WORKLOAD)
+    A, sizes, Y0 = synth.make_config_data(name, n=c["n"])
+    return c, A, sizes, Y0, synth.config_schedule(name)
 
 
 def _oracle_sample_gbps(parts, Y0, passes: int):
@@ -162,11 +165,72 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def _config(c, sched):
-    return {"workload": (f"LocalPower FP32: n={c['n']:,} d={c['d']} k={c['k']} m={c['m']}, p=8,4,2,1 x10 rounds "
-                         f"(T={len(sched)}, {sum(sched)} local steps) + Rayleigh-Ritz pass"),
-            "n": c["n"], "d": c["d"], "k": c["k"], "m": c["m"], "rounds": len(sched), "local_steps": sum(sched),
-            "l2": "inputs larger than L2 (A is 4.1 GB; L2 is 129 MB)"}
+def _config(c, sched, name: str = WORKLOAD):
+    if name == "lowprec":
+        text = (f"LocalPower BF16 storage: n={c['n']:,} d={c['d']} k={c['k']} m={c['m']}, p=4 x30 rounds + 3 "
+                f"FP32-accumulated p=1 refinement rounds ({sum(sched)} local steps) + Rayleigh-Ritz pass")
+        size = f"A is {c['n'] * c['d'] * 2 / 1e9:.1f} GB BF16"
+    else:
+        text = (f"LocalPower FP32: n={c['n']:,} d={c['d']} k={c['k']} m={c['m']}, p=8,4,2,1 x10 rounds "
+                f"(T={len(sched)}, {sum(sched)} local steps) + Rayleigh-Ritz pass")
+        size = f"A is {c['n'] * c['d'] * 4 / 1e9:.1f} GB FP32"
+    return {"workload": text, "n": c["n"], "d": c["d"], "k": c["k"], "m": c["m"], "rounds": len(sched),
+            "local_steps": sum(sched), "l2": f"inputs larger than L2 ({size}; L2 is 129 MB)"}
+
+
+def run_lowprec(args):
+    """The low-precision workload (BF16 storage) on the tensor-core path alone."""
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    import synth
+    from paper_2002_08014_gb300 import binding as B
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    c, A, sizes, Y0, sched = _workload(rank, args.rows, "lowprec")
+    _timed.y0 = Y0
+    k, d = c["k"], c["d"]
+    parts = synth.split_rows(A, sizes)
+    bits = [synth.f32_to_bf16_bits(p) for p in parts]
+    stream = torch.cuda.Stream(device=dev)
+    hbm_peak, _, peak_src = _peaks()
+    lpb = B.LocalPower(bits, dtype="bf16", device=local, stream=stream)
+    for _ in range(args.warmup):
+        lpb.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
+        lpb.result(k)
+    ms, stats, Z, sig, clk = _timed(torch, dist, world, dev, stream, lpb, k, sched, args.agg, args.steps,
+                                    Clocks(local))
+    s = _summary(world, args.steps, ms, stats, 2, c)
+    lpb.close()
+    gbs_k = s["launch_bytes"] / (s["step_ms"] / 1e3) / 1e9
+    line = {"metric": METRIC, "value": s["gbs"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": s["ms_per_solve"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": _config(c, sched, "lowprec"),
+            "solves_per_s": s["solves_per_s"], "latency_ms": s["latency_ms"], "clocks": clk,
+            "gpu_launches": s["launches"], "e2e": None,
+            "roofline": {"kernel": "step_tc_kernel (tcgen05, BF16 A, hi/lo BF16 Z and W)", "bound": "hbm",
+                         "achieved": gbs_k, "peak": hbm_peak, "unit": "GB/s", "frac": gbs_k / hbm_peak,
+                         "traffic": None, "launch_ms": s["step_ms"], "peak_source": f"{peak_src} HBM copy bandwidth"}}
+    line["orthonormality"] = float(np.abs(Z.T @ Z - np.eye(k)).max())
+    line["sigma_top3"] = [float(x) for x in sig[:3]]
+    if rank == 0 and not args.no_accuracy and c["n"] * d <= 2_200_000_000:
+        # truth of the decoded BF16 problem (the matrix the solver is given) and of the FP32 original;
+        # forming M in FP64 on the host is skipped above about the FP32 workload's size
+        dec = [oracle.decode_bf16(b) for b in bits]
+        Vb, _ = _truth(dec, c)
+        Vf, _ = _truth(parts, c)
+        line["accuracy"] = {"dist_to_eigh_topk_bf16_problem": oracle.subspace_dist(oracle.orth(Z), Vb),
+                            "dist_to_eigh_topk_fp32_problem": oracle.subspace_dist(oracle.orth(Z), Vf),
+                            "quantisation_shift": oracle.subspace_dist(Vb, Vf)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def _timed(torch, dist, world, dev, stream, lp, k, sched, agg, steps, clocks=None):
@@ -360,5 +424,7 @@ if __name__ == "__main__":
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "lowprec":
+        run_lowprec(a)
     else:
         run_ours(a)

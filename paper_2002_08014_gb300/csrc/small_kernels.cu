@@ -22,6 +22,29 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// FP64 1/sqrt(x) and 1/x by Newton-Raphson iteration from FP32 seeds
+// (y <- y (3 - x y^2) / 2 and y <- y (2 - x y)); each step doubles the number of
+// correct bits, so two steps take the FP32 seed (about 2^-22) past FP64
+// precision.  FP64 square roots and divisions are long instruction sequences on
+// this GPU; these are a few FMAs on the short k x k critical paths.  Arguments
+// outside the FP32 normal range take the plain sqrt / division.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  double y = static_cast<double>(rsqrtf(static_cast<float>(x)));
+  const double hx = 0.5 * x;
+  y = y * (1.5 - hx * y * y);
+  y = y * (1.5 - hx * y * y);
+  return y;
+}
+__device__ __forceinline__ double recip_nr(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+  double y = static_cast<double>(__frcp_rn(static_cast<float>(x)));
+  y = y * (2.0 - x * y);
+  y = y * (2.0 - x * y);
+  return y;
+}
+
 // ---------------------------------------------------------------- pack / unpack
 __global__ void pack_kernel(const double* __restrict__ src, float* __restrict__ dst, int batch, int d, int k, int K) {
   const int64_t total = int64_t(batch) * d * K;
@@ -59,47 +82,6 @@ __global__ void reduce_kernel(const float* __restrict__ P, const int* __restrict
 }
 
 // ---------------------------------------------------------------- k x k helpers (warp 0, FP64)
-// Cholesky G = L L^T in place into L (lower, k x k, stride K).  Returns false on breakdown
-// (non-positive or non-finite pivot); the pivot is then replaced by 1 so the caller can finish.
-__device__ bool warp_cholesky(const double* G, double* L, int k, int K) {
-  const int lane = threadIdx.x & 31;
-  bool ok = true;
-  for (int j = 0; j < k; ++j) {
-    if (lane == 0) {
-      double s = G[j * K + j];
-      for (int p = 0; p < j; ++p) s -= L[j * K + p] * L[j * K + p];
-      if (!(s > 0.0) || !isfinite(s)) {
-        ok = false;
-        s = 1.0;
-      }
-      L[j * K + j] = sqrt(s);
-    }
-    __syncwarp();
-    const double ljj = L[j * K + j];
-    for (int i = j + 1 + lane; i < k; i += 32) {
-      double s = G[i * K + j];
-      for (int p = 0; p < j; ++p) s -= L[i * K + p] * L[j * K + p];
-      L[i * K + j] = s / ljj;
-    }
-    __syncwarp();
-  }
-  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-}
-
-// X = L^{-1} (lower triangular), column c computed by lane c.
-__device__ void warp_lower_inverse(const double* L, double* X, int k, int K) {
-  const int c = threadIdx.x & 31;
-  if (c < k) {
-    X[c * K + c] = 1.0 / L[c * K + c];
-    for (int i = c + 1; i < k; ++i) {
-      double s = 0.0;
-      for (int p = c; p < i; ++p) s += L[i * K + p] * X[p * K + c];
-      X[i * K + c] = -s / L[i * K + i];
-    }
-  }
-  __syncwarp();
-}
-
 // One-sided (Hestenes) Jacobi on the k x k matrix C (stride K, in smem), accumulating the
 // rotations in V.  On return C's columns are mutually orthogonal: C_in V = C_out, so
 // C_in = U Sigma V^T with sigma_j = ||C_out[:, j]||, U[:, j] = C_out[:, j] / sigma_j.
@@ -124,11 +106,13 @@ __device__ bool warp_jacobi(double* C, double* V, int k, int K) {
         a = warp_sum(a);
         b = warp_sum(b);
         g = warp_sum(g);
-        if (fabs(g) > tol * sqrt(a * b) && fabs(g) > 1e-300) {
+        if (g * g > tol * tol * (a * b) && fabs(g) > 1e-300) {
           rotated = 1;
-          const double zeta = (b - a) / (2.0 * g);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t);
+          // zeta = (b - a) / 2g, t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2)
+          const double zeta = (b - a) * recip_nr(2.0 * g);
+          const double q2 = 1.0 + zeta * zeta;
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) * recip_nr(fabs(zeta) + q2 * rsqrt_nr(q2));
+          const double c = rsqrt_nr(1.0 + t * t);
           const double s = c * t;
           if (lane < k) {
             const double cp = C[lane * K + p], cq = C[lane * K + q];
@@ -155,50 +139,40 @@ __device__ bool warp_jacobi(double* C, double* V, int k, int K) {
 // The column space is Y's whatever the precision of L; the second pass restores
 // orthonormality lost to the FP32 Gram.  A pivot that is not positive and finite
 // sets ST_CHOL (the pivot is then taken as 1 so the kernel can finish).
-constexpr int kChunk = 128;
-
+// G = Y^T Y: thread (block (bi, bj) of 4 x 4 entries, row slice) accumulates
+// Y[r][4bi..4bi+3]^T Y[r][4bj..4bj+3] over its rows in FP32 registers (16 FMAs
+// per two 16-byte loads); the slices are added in FP64 through shared memory.
 template <int K>
-__device__ void gram_fp32(const float* __restrict__ Y, int d, float* chunk, double* G) {
-  constexpr int NP = K * K;
-  constexpr int RS = NP >= kT ? 1 : kT / NP;  // row slices
-  constexpr int PP = NP >= kT ? NP / kT : 1;  // pairs per thread
+__device__ void gram_fp32(const float* __restrict__ Y, int d, float* red, double* G) {
+  constexpr int NB = K / 4, NBB = NB * NB, S = kT / NBB;
   const int t = threadIdx.x;
-  float acc[PP];
+  const int blk = t % NBB, sl = t / NBB;
+  const int bi = blk / NB, bj = blk % NB;
+  float acc[4][4];
 #pragma unroll
-  for (int pp = 0; pp < PP; ++pp) acc[pp] = 0.f;
-  for (int r0 = 0; r0 < d; r0 += kChunk) {
-    const int nr = min(kChunk, d - r0);
-    __syncthreads();
-    for (int e = t; e < nr * K / 4; e += kT)
-      reinterpret_cast<float4*>(chunk)[e] = reinterpret_cast<const float4*>(Y + int64_t(r0) * K)[e];
-    __syncthreads();
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int pp = 0; pp < PP; ++pp) {
-      const int idx = t + kT * pp;
-      const int pair = idx % NP, slice = idx / NP;
-      const int a = pair / K, b = pair % K;
-      float s0 = 0.f, s1 = 0.f;
-      int r = slice;
-      for (; r + RS < nr; r += 2 * RS) {
-        s0 = fmaf(chunk[r * K + a], chunk[r * K + b], s0);
-        s1 = fmaf(chunk[(r + RS) * K + a], chunk[(r + RS) * K + b], s1);
-      }
-      if (r < nr) s0 = fmaf(chunk[r * K + a], chunk[r * K + b], s0);
-      acc[pp] += s0 + s1;
-    }
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int r = sl; r < d; r += S) {
+    const float4 u = *reinterpret_cast<const float4*>(Y + int64_t(r) * K + 4 * bi);
+    const float4 v = *reinterpret_cast<const float4*>(Y + int64_t(r) * K + 4 * bj);
+    const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(uu[a], vv[b], acc[a][b]);
   }
-  __syncthreads();
-  if (RS > 1) {
-    chunk[t] = acc[0];
-    __syncthreads();
-    if (t < NP) {
-      double s = 0.0;
-      for (int sl = 0; sl < RS; ++sl) s += chunk[sl * NP + t];
-      G[t] = s;
-    }
-  } else {
 #pragma unroll
-    for (int pp = 0; pp < PP; ++pp) G[t + kT * pp] = static_cast<double>(acc[pp]);
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) red[(sl * NBB + blk) * 16 + 4 * a + b] = acc[a][b];
+  __syncthreads();
+  for (int e = t; e < K * K; e += kT) {
+    const int i = e / K, j = e % K;
+    const int bb = (i / 4) * NB + j / 4, el = 4 * (i % 4) + j % 4;
+    double s = 0.0;
+    for (int q = 0; q < S; ++q) s += red[(q * NBB + bb) * 16 + el];
+    G[e] = s;
   }
   __syncthreads();
 }
@@ -215,8 +189,8 @@ __device__ bool warp_cholesky_rl(double* G, float* Lf, float* invd, int k) {
       ok = false;
       piv = 1.0;
     }
-    const double ljj = sqrt(piv);
-    const double inv = 1.0 / ljj;
+    const double inv = rsqrt_nr(piv);
+    const double ljj = piv * inv;
     // column j below the diagonal
     for (int i = j + 1 + lane; i < k; i += 32) G[i * K + j] *= inv;
     if (lane == 0) {
@@ -240,30 +214,44 @@ __device__ bool warp_cholesky_rl(double* G, float* Lf, float* invd, int k) {
   return ok;
 }
 
-// Z[r][:] = Y[r][:] L^{-T}: z_j = (y_j - sum_{p<j} z_p L[j][p]) / L[j][j], one thread per row.
+// Z[r][:] = Y[r][:] L^{-T}: z_j = (y_j - sum_{p<j} z_p L[j][p]) / L[j][j].  Each
+// thread solves four rows at once, column j outermost, so a row of L read from
+// shared memory serves four independent FMA chains.
 template <int K>
-__device__ void forward_rows(const float* Yin, float* Zout, const float* Lf_, const float* invd, int d, int k) {
-  // Read L through a volatile view so the compiler re-reads the broadcast
-  // shared values per row instead of holding all K(K+1)/2 of them in registers.
-  const volatile float* Lf = Lf_;
-  for (int r = threadIdx.x; r < d; r += kT) {
-    float y[K];
-    const float4* src = reinterpret_cast<const float4*>(Yin + int64_t(r) * K);
+__device__ void forward_rows(const float* Yin, float* Zout, const float* Lf, const float* invd, int d, int k) {
+  constexpr int RPT = 4;
+  for (int rb = 0; rb < d; rb += RPT * kT) {
+    asm volatile("" ::: "memory");  // keep the L reads inside this iteration
+    float y[RPT][K];
 #pragma unroll
-    for (int q = 0; q < K / 4; ++q) {
-      const float4 v = src[q];
-      y[4 * q] = v.x; y[4 * q + 1] = v.y; y[4 * q + 2] = v.z; y[4 * q + 3] = v.w;
+    for (int g = 0; g < RPT; ++g) {
+      const int r = rb + threadIdx.x + g * kT;
+#pragma unroll
+      for (int q = 0; q < K / 4; ++q) {
+        const float4 v = r < d ? reinterpret_cast<const float4*>(Yin + int64_t(r) * K)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        y[g][4 * q] = v.x; y[g][4 * q + 1] = v.y; y[g][4 * q + 2] = v.z; y[g][4 * q + 3] = v.w;
+      }
     }
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      float s = y[j];
+      const float inv = j < k ? invd[j] : 0.f;
 #pragma unroll
-      for (int p = 0; p < j; ++p) s = fmaf(-y[p], Lf[j * K + p], s);
-      y[j] = j < k ? s * invd[j] : 0.f;
+      for (int g = 0; g < RPT; ++g) {
+        float s = y[g][j];
+#pragma unroll
+        for (int p = 0; p < j; ++p) s = fmaf(-y[g][p], Lf[j * K + p], s);
+        y[g][j] = s * inv;
+      }
     }
-    float4* dst = reinterpret_cast<float4*>(Zout + int64_t(r) * K);
 #pragma unroll
-    for (int q = 0; q < K / 4; ++q) dst[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+    for (int g = 0; g < RPT; ++g) {
+      const int r = rb + threadIdx.x + g * kT;
+      if (r < d) {
+        float4* dst = reinterpret_cast<float4*>(Zout + int64_t(r) * K);
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) dst[q] = make_float4(y[g][4 * q], y[g][4 * q + 1], y[g][4 * q + 2], y[g][4 * q + 3]);
+      }
+    }
   }
 }
 
@@ -273,12 +261,12 @@ __global__ void __launch_bounds__(kT) cholqr2_kernel(const float* __restrict__ Y
   __shared__ __align__(16) double G[K * K];
   __shared__ __align__(16) float Lf[K * K];
   __shared__ float invd[K];
-  __shared__ __align__(16) float chunk[kChunk * K];
+  __shared__ __align__(16) float red[kT * 16];
   const float* Y = Yall + int64_t(blockIdx.x) * d * K;
   float* Z = Zall + int64_t(blockIdx.x) * d * K;
   for (int pass = 0; pass < 2; ++pass) {
     const float* src = pass == 0 ? Y : Z;
-    gram_fp32<K>(src, d, chunk, G);
+    gram_fp32<K>(src, d, red, G);
     if (threadIdx.x < 32) {
       const bool ok = warp_cholesky_rl<K>(G, Lf, invd, k);
       if (!ok && threadIdx.x == 0) atomicOr(status, ST_CHOL);
@@ -357,8 +345,9 @@ __global__ void __launch_bounds__(kT) align_kernel(const float* __restrict__ Zl,
     for (int j = 0; j < k; ++j) {
       double nrm = 0.0;
       if (t < k) nrm = C[t * K + j] * C[t * K + j];
-      nrm = sqrt(warp_sum(nrm));
-      if (t < k) C[t * K + j] = nrm > 1e-300 ? C[t * K + j] / nrm : 0.0;
+      nrm = warp_sum(nrm);  // squared norm
+      const double inv = nrm > 1e-300 ? rsqrt_nr(nrm) : 0.0;
+      if (t < k) C[t * K + j] *= inv;
       if (!(nrm > 1e-300) && t == 0) atomicOr(status, ST_JACOBI);
     }
     __syncwarp();
@@ -436,8 +425,8 @@ __global__ void __launch_bounds__(kT) ritz_kernel(const float* __restrict__ Z, c
     for (int j = 0; j < k; ++j) {
       double s = 0.0;
       if (t < k) s = H[t * K + j] * H[t * K + j];
-      s = sqrt(warp_sum(s));
-      if (t == 0) lam[j] = s;
+      s = warp_sum(s);
+      if (t == 0) lam[j] = s > 0.0 ? s * rsqrt_nr(s) : 0.0;
     }
     __syncwarp();
     if (t == 0) {
