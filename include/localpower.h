@@ -45,7 +45,11 @@ typedef enum lp_status {
 typedef enum lp_dtype {
     LP_F32 = 0,             /* IEEE binary32                                      */
     LP_BF16 = 1,            /* bfloat16 bit patterns (uint16)                     */
-    LP_FP8_E4M3 = 2         /* OCP FP8 E4M3 "FN" codes (uint8) x one FP32 scale per row */
+    LP_FP8_E4M3 = 2,        /* OCP FP8 E4M3 "FN" codes (uint8) x one FP32 scale per row */
+    LP_F32_BF16X2 = 3       /* IEEE binary32 input, stored on the device as two bfloat16
+                             * planes hi = RNE(a), lo = RNE(a - hi) (same 4 bytes per
+                             * element) and multiplied on the tensor cores.  The stored
+                             * matrix hi + lo differs from a by at most 2^-17 |a|. */
 } lp_dtype;
 
 /* The aligning family F of the unified update rule (App. B): F = {I} gives vanilla
@@ -63,6 +67,9 @@ typedef enum lp_ptr_space { LP_HOST = 0, LP_DEVICE = 1 } lp_ptr_space;
 #define LP_FLAG_RITZ   1u   /* finish with a Rayleigh-Ritz step: ordered basis + sigma */
 #define LP_FLAG_TIMING 2u   /* record CUDA events around every fused power-step launch */
 #define LP_FLAG_SIMT   4u   /* BF16 data: use the SIMT FP32 step kernel instead of the tensor-core one */
+#define LP_FLAG_TC_RESIDENT 8u  /* BF16 data: use the tensor-core step that keeps each tile in shared
+                                 * memory for both contractions (cluster-split d) instead of the
+                                 * streaming one; ignored for other dtypes */
 
 typedef struct lp_ctx lp_ctx;
 
@@ -73,7 +80,8 @@ typedef struct lp_stats {
     int32_t k;
     int64_t n, d;
     int32_t m;
-    int32_t path;              /* 0 = SIMT FP32 step kernel, 1 = tcgen05 tensor-core step (BF16) */
+    int32_t path;              /* step kernel: 0 = SIMT FP32, 1 = tcgen05 with the tile resident in
+                                * shared memory, 2 = tcgen05 streaming (second pass re-read from L2) */
     double a_bytes;            /* algorithmic bytes of A read by the step kernels     */
     double ms_solve;           /* solve wall time on the stream (events)              */
     double ms_step_kernels;    /* summed step-kernel time (LP_FLAG_TIMING only)       */
@@ -100,6 +108,7 @@ lp_status lp_create(lp_ctx** out, int device, size_t hbm_budget_bytes, void* cud
  *   d              columns, d >= 1.
  *   parts[m]       pointer to partition i, s_i x d row-major, elements of `dtype`.
  *   row_scales[m]  LP_FP8_E4M3 only: s_i FP32 scales (value = code * scale); else NULL.
+ *                  LP_F32_BF16X2 takes FP32 parts (like LP_F32) and splits them on the device.
  *   space          whether parts / row_scales are host or device pointers.
  * Replaces any previously loaded partitions.  The caller keeps its buffers.
  */
@@ -134,6 +143,41 @@ lp_status lp_solve(lp_ctx* ctx, int k, const int* p_schedule, int T, lp_aggregat
  * Returns LP_ERR_NUMERIC if a device-side check failed during the solve.
  */
 lp_status lp_result(lp_ctx* ctx, double* z_out, double* sigma_out, lp_stats* stats);
+
+/* Tuning of the streaming tensor-core step kernel (LP_BF16 and LP_F32_BF16X2
+ * data).  Zero in a field keeps the library's default for it.  These change
+ * speed only: every setting computes the same products in the same order. */
+typedef struct lp_tuning {
+    int32_t ring_units;      /* 32 KB shared-memory ring units (default: as many as fit, <= 8) */
+    int32_t lag_units;       /* first-pass units of tile t+1 issued before the second pass of
+                              * tile t starts (default 2 without a cluster, 4 with one)         */
+    int32_t prefetch_units;  /* first-pass units brought into L2 ahead of their load (default 0) */
+    int32_t cache_hints;     /* 1: first-pass loads mark lines evict_last, second-pass loads
+                              * evict_first (default 0: no hint)                                  */
+} lp_tuning;
+
+/*
+ * lp_set_tuning: set (tuning != NULL) or reset to defaults (NULL) the tuning
+ * used by later lp_solve / lp_power_step calls on this context.  Negative
+ * fields are LP_ERR_INVALID; a ring that does not fit shared memory is
+ * clamped to what fits.
+ */
+lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* tuning);
+
+/*
+ * lp_autotune: time the step-kernel candidates for rank k on the loaded
+ * partitions and keep the fastest for later solves on this context (it sets
+ * the context's tuning, and for LP_BF16 data whether the resident or the
+ * streaming tensor-core kernel runs).  Candidates: the streaming kernel with
+ * lag in {1, 2, 4} and cache hints off/on, and the resident kernel where it
+ * has a plan.  Each is timed over 3 launches after a warm-up launch, on the
+ * context's stream; the call synchronises.  Other dtypes have one candidate
+ * (the SIMT kernel) and return at once.
+ *   chosen      receives the winning tuning (may be NULL).
+ *   path        receives the winning lp_stats::path code (may be NULL).
+ *   best_ms     receives the winner's mean launch time in ms (may be NULL).
+ */
+lp_status lp_autotune(lp_ctx* ctx, int k, lp_tuning* chosen, int* path, double* best_ms);
 
 /* lp_destroy: free everything the context owns; NULL is a no-op. */
 void lp_destroy(lp_ctx* ctx);

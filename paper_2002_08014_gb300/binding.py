@@ -15,18 +15,19 @@ import numpy as np
 LP_OK, LP_ERR_INVALID, LP_ERR_STATE, LP_ERR_OOM, LP_ERR_CUDA, LP_ERR_NUMERIC, LP_ERR_TIMEOUT, LP_ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["LP_OK", "LP_ERR_INVALID", "LP_ERR_STATE", "LP_ERR_OOM", "LP_ERR_CUDA", "LP_ERR_NUMERIC",
                 "LP_ERR_TIMEOUT", "LP_ERR_UNSUPPORTED"]
-LP_F32, LP_BF16, LP_FP8_E4M3 = 0, 1, 2
+LP_F32, LP_BF16, LP_FP8_E4M3, LP_F32_BF16X2 = 0, 1, 2, 3
 LP_AGG_IDENTITY, LP_AGG_SIGN, LP_AGG_OPT = 0, 1, 2
 LP_HOST, LP_DEVICE = 0, 1
-LP_FLAG_RITZ, LP_FLAG_TIMING, LP_FLAG_SIMT = 1, 2, 4
+LP_FLAG_RITZ, LP_FLAG_TIMING, LP_FLAG_SIMT, LP_FLAG_TC_RESIDENT = 1, 2, 4, 8
 LP_MAX_K = 32
 
 AGG = {"identity": LP_AGG_IDENTITY, "sign": LP_AGG_SIGN, "opt": LP_AGG_OPT}
-DTYPE = {"f32": LP_F32, "bf16": LP_BF16, "e4m3": LP_FP8_E4M3}
+DTYPE = {"f32": LP_F32, "bf16": LP_BF16, "e4m3": LP_FP8_E4M3, "f32_bf16x2": LP_F32_BF16X2}
+PATHS = {0: "simt", 1: "tc_resident", 2: "tc_streaming"}
 
 # Every symbol the header declares, in declaration order.
 EXPORTS = ["lp_create", "lp_load_partitions", "lp_solve", "lp_result", "lp_destroy", "lp_last_error",
-           "lp_power_step", "lp_orth", "lp_align_aggregate", "lp_power_step_static"]
+           "lp_set_tuning", "lp_autotune", "lp_power_step", "lp_orth", "lp_align_aggregate", "lp_power_step_static"]
 
 
 class lp_stats(C.Structure):
@@ -37,6 +38,11 @@ class lp_stats(C.Structure):
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class lp_tuning(C.Structure):
+    _fields_ = [("ring_units", C.c_int32), ("lag_units", C.c_int32), ("prefetch_units", C.c_int32),
+                ("cache_hints", C.c_int32)]
 
 
 class LPError(RuntimeError):
@@ -78,6 +84,8 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
     L.lp_orth.argtypes = [P, I, I64, I, P, P, I]
     L.lp_align_aggregate.argtypes = [P, I, I64, I, I, I, P, P, P, P, P, I]
     L.lp_power_step_static.argtypes = [P, I, C.POINTER(I64), I64, I, P, P, P]
+    L.lp_set_tuning.argtypes = [P, C.POINTER(lp_tuning)]
+    L.lp_autotune.argtypes = [P, I, C.POINTER(lp_tuning), C.POINTER(I), C.POINTER(C.c_double)]
     for name in EXPORTS:
         if name not in ("lp_destroy", "lp_last_error"):
             getattr(L, name).restype = C.c_int
@@ -123,6 +131,29 @@ def lp_destroy(ctx) -> None:
     load().lp_destroy(ctx)
 
 
+def lp_set_tuning(ctx, ring_units: int = 0, lag_units: int = 0, prefetch_units: int = 0, cache_hints: int = 0,
+                  reset: bool = False) -> None:
+    """Tuning of the streaming tensor-core step (zeros keep the defaults; reset=True passes NULL)."""
+    L = load()
+    if reset:
+        _check(ctx, L.lp_set_tuning(ctx, None))
+        return
+    t = lp_tuning(ring_units, lag_units, prefetch_units, cache_hints)
+    _check(ctx, L.lp_set_tuning(ctx, C.byref(t)))
+
+
+def lp_autotune(ctx, k: int) -> dict:
+    """Time the step-kernel candidates for rank k and keep the fastest; returns the choice."""
+    L = load()
+    t = lp_tuning()
+    path = C.c_int(0)
+    ms = C.c_double(0.0)
+    _check(ctx, L.lp_autotune(ctx, int(k), C.byref(t), C.byref(path), C.byref(ms)))
+    return {"path": PATHS.get(path.value, path.value), "path_code": path.value, "ms_per_step": ms.value,
+            "ring_units": t.ring_units, "lag_units": t.lag_units, "prefetch_units": t.prefetch_units,
+            "cache_hints": t.cache_hints}
+
+
 def lp_last_error(ctx=None) -> str:
     return load().lp_last_error(ctx).decode(errors="replace")
 
@@ -133,7 +164,7 @@ def lp_load_partitions(ctx, parts, dtype: str = "f32", row_scales=None) -> None:
     arrays (E4M3 only)."""
     L = load()
     m = len(parts)
-    np_dt = {"f32": np.float32, "bf16": np.uint16, "e4m3": np.uint8}[dtype]
+    np_dt = {"f32": np.float32, "bf16": np.uint16, "e4m3": np.uint8, "f32_bf16x2": np.float32}[dtype]
     ptrs, keep, spaces = [], [], set()
     for p in parts:
         q, sp, k = _ptr(p, np_dt)

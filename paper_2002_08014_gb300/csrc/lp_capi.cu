@@ -56,7 +56,22 @@ struct lp_ctx {
   Segment* dSegsTc = nullptr;
   int* dSegPtrTc = nullptr;
   int* dSlotBeginTc = nullptr;
-  bool use_tc = false;  // path of the current solve / step
+
+  // streaming tensor-core step (BF16 plane or hi/lo planes): plans per padded k
+  // (index 0, 1, 2 for K = 8, 16, 32; state 0 = not planned, 1 = ready, -1 = none)
+  int planes = 0;  // 1 for LP_BF16, 2 for LP_F32_BF16X2, 0 otherwise
+  lp::TcsPlan tcs[3];
+  int tcs_state[3] = {0, 0, 0};
+  int tcs_G = 0;  // clusters the device segment table below was built for
+  int nslots_tcs = 0;
+  Segment* dSegsTcs = nullptr;
+  int* dSegPtrTcs = nullptr;
+  int* dSlotBeginTcs = nullptr;
+  const lp::TcsPlan* tcs_cur = nullptr;
+
+  int path = 0;  // step kernel of the current solve / step (lp_stats::path)
+  lp::TcsTuning tuning;
+  bool prefer_resident = false;  // set by lp_autotune for LP_BF16 data
 
   // solve state (capacity in K)
   int Kcap = 0;
@@ -126,15 +141,21 @@ void dfree(lp_ctx* c, T*& p, size_t bytes) {
   }
 }
 
+enum Path { PATH_SIMT = 0, PATH_TC = 1, PATH_TCS = 2 };
+
 int kcap_of(int k) { return k <= 8 ? 8 : (k <= 16 ? 16 : 32); }
-size_t elem_bytes(lp_dtype t) { return t == LP_F32 ? 4 : (t == LP_BF16 ? 2 : 1); }
+// Algorithmic bytes per element of A (both planes for LP_F32_BF16X2).
+size_t elem_bytes(lp_dtype t) { return (t == LP_F32 || t == LP_F32_BF16X2) ? 4 : (t == LP_BF16 ? 2 : 1); }
+// Bytes per stored element of one plane.
+size_t plane_bytes(lp_dtype t) { return t == LP_F32_BF16X2 ? 2 : elem_bytes(t); }
 
 struct StateSizes {
   size_t P, Yl, Y, G, stage;
 };
 StateSizes state_sizes(const lp_ctx* c, int K) {
   StateSizes s;
-  s.P = size_t(std::max(c->nslots, c->nslots_tc)) * c->d * K * 4;
+  // every step kernel's segment table has at most (workers <= SMs) + m - 1 segments
+  s.P = size_t(c->sms + c->m) * c->d * K * 4;
   s.Yl = size_t(c->m) * c->d * K * 4;
   s.Y = size_t(c->d) * K * 4;
   s.G = size_t(c->m) * K * K * 4;
@@ -188,9 +209,17 @@ void free_partitions(lp_ctx* c) {
   dfree(c, c->dSegsTc, (size_t(c->tc.nclusters) + c->m) * sizeof(Segment));
   dfree(c, c->dSegPtrTc, (size_t(c->tc.nclusters) + 1) * 4);
   dfree(c, c->dSlotBeginTc, (size_t(c->m) + 1) * 4);
+  dfree(c, c->dSegsTcs, (size_t(c->sms) + c->m) * sizeof(Segment));
+  dfree(c, c->dSegPtrTcs, (size_t(c->sms) + 1) * 4);
+  dfree(c, c->dSlotBeginTcs, (size_t(c->m) + 1) * 4);
   free_state(c);
   c->nslots_tc = 0;
   c->tc_ready = false;
+  c->nslots_tcs = 0;
+  c->tcs_G = 0;
+  c->tcs_state[0] = c->tcs_state[1] = c->tcs_state[2] = 0;
+  c->tcs_cur = nullptr;
+  c->planes = 0;
   c->m = 0;
   c->n = 0;
   c->dA_bytes = 0;
@@ -246,7 +275,9 @@ void build_segments(const lp_ctx* c, int G, std::vector<Segment>& segs, std::vec
   slot_begin[m] = nslots;
 }
 
-const int* slot_begin_of(const lp_ctx* c) { return c->use_tc ? c->dSlotBeginTc : c->dSlotBegin; }
+const int* slot_begin_of(const lp_ctx* c) {
+  return c->path == PATH_TCS ? c->dSlotBeginTcs : c->path == PATH_TC ? c->dSlotBeginTc : c->dSlotBegin;
+}
 
 lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool timing) {
   lp::StepArgs a;
@@ -269,9 +300,15 @@ lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool t
     }
     LP_CUDA(cudaEventRecord(c->step_ev[c->step_ev_used], c->stream));
   }
-  cudaError_t e = c->use_tc ? lp::launch_step_tc(c->tc, c->dSegsTc, c->dSegPtrTc, Z, z_stride, c->dP,
-                                                  static_cast<int>(c->d), c->dStatus, c->stream)
-                            : lp::launch_step_simt(a, c->dtype, K, c->stream);
+  cudaError_t e;
+  if (c->path == PATH_TCS)
+    e = lp::launch_step_tcs(*c->tcs_cur, c->dSegsTcs, c->dSegPtrTcs, Z, z_stride, c->dP, static_cast<int>(c->d),
+                            c->dStatus, c->stream);
+  else if (c->path == PATH_TC)
+    e = lp::launch_step_tc(c->tc, c->dSegsTc, c->dSegPtrTc, Z, z_stride, c->dP, static_cast<int>(c->d), c->dStatus,
+                           c->stream);
+  else
+    e = lp::launch_step_simt(a, c->dtype, K, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "fused power-step launch");
   if (timing) {
     LP_CUDA(cudaEventRecord(c->step_ev[c->step_ev_used + 1], c->stream));
@@ -354,7 +391,8 @@ lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, l
   c->err.clear();
   if (m < 1 || !rows || !parts) return fail(c, LP_ERR_INVALID, "need m >= 1 and non-NULL rows/parts");
   if (d < 1 || d > (1 << 20)) return fail(c, LP_ERR_INVALID, "d out of range");
-  if (dtype != LP_F32 && dtype != LP_BF16 && dtype != LP_FP8_E4M3) return fail(c, LP_ERR_INVALID, "unknown dtype");
+  if (dtype != LP_F32 && dtype != LP_BF16 && dtype != LP_FP8_E4M3 && dtype != LP_F32_BF16X2)
+    return fail(c, LP_ERR_INVALID, "unknown dtype");
   if (space != LP_HOST && space != LP_DEVICE) return fail(c, LP_ERR_INVALID, "unknown pointer space");
   if (dtype == LP_FP8_E4M3 && !row_scales) return fail(c, LP_ERR_INVALID, "FP8 partitions need row_scales");
   int64_t n = 0;
@@ -369,13 +407,21 @@ lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, l
   LP_CUDA(cudaStreamSynchronize(c->stream));
   free_partitions(c);
 
-  const size_t eb = elem_bytes(dtype);
+  const bool split = dtype == LP_F32_BF16X2;
+  if (split) {
+    lp::TcsPlan probe;
+    if (!lp::tcs_plan(static_cast<int>(d), 8, 2, c->sms, lp::TcsTuning{}, &probe))
+      return fail(c, LP_ERR_UNSUPPORTED, "split-plane storage has no tensor-core kernel for d=" + std::to_string(d));
+  }
+  const size_t eb = plane_bytes(dtype);  // bytes per stored element of one plane
+  const int nplanes = split ? 2 : 1;
   const int64_t per16 = 16 / static_cast<int64_t>(eb);
   c->m = m;
   c->d = d;
   c->ld = (d + per16 - 1) / per16 * per16;
   c->n = n;
   c->dtype = dtype;
+  c->planes = dtype == LP_BF16 ? 1 : (split ? 2 : 0);
   c->rows.assign(rows, rows + m);
   c->row_off.resize(m);
   int64_t o = 0;
@@ -409,7 +455,7 @@ lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, l
     w[i] = static_cast<float>(double(rows[i]) / double(n));
   }
 
-  c->dA_bytes = size_t(n) * size_t(c->ld) * eb;
+  c->dA_bytes = size_t(n) * size_t(c->ld) * eb * nplanes;
   lp_status st;
   if ((st = dalloc(c, &c->dA, c->dA_bytes)) ||
       (dtype == LP_FP8_E4M3 && (st = dalloc(c, &c->dScales, size_t(n) * 4))) ||
@@ -438,8 +484,44 @@ lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, l
     }
   }
   const cudaMemcpyKind kind = space == LP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  if (c->ld != d) LP_CUDA(cudaMemsetAsync(c->dA, 0, c->dA_bytes, c->stream));
-  for (int i = 0; i < m; ++i) {
+  if (split) {
+    // FP32 -> hi / lo planes on the device; host data go through a bounded FP32 staging buffer.
+    uint16_t* hi = static_cast<uint16_t*>(c->dA);
+    uint16_t* lo = hi + size_t(n) * c->ld;
+    float* stage = nullptr;
+    const int64_t chunk_rows = std::max<int64_t>(1, (int64_t(1) << 24) / d);  // 64 MB of FP32
+    size_t stage_bytes = 0;
+    if (space == LP_HOST) {
+      stage_bytes = size_t(std::min(chunk_rows, *std::max_element(c->rows.begin(), c->rows.end()))) * d * 4;
+      if ((st = dalloc(c, &stage, stage_bytes))) {
+        std::string msg = c->err;
+        free_partitions(c);
+        c->err = msg;
+        return st;
+      }
+    }
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < m && e == cudaSuccess; ++i) {
+      const float* src = static_cast<const float*>(parts[i]);
+      for (int64_t r0 = 0; r0 < rows[i] && e == cudaSuccess; r0 += chunk_rows) {
+        const int64_t nr = std::min(chunk_rows, rows[i] - r0);
+        const size_t off = size_t(c->row_off[i] + r0) * c->ld;
+        const float* from = src + size_t(r0) * d;
+        if (space == LP_HOST) {
+          e = cudaMemcpyAsync(stage, from, size_t(nr) * d * 4, cudaMemcpyHostToDevice, c->stream);
+          from = stage;
+        }
+        if (e == cudaSuccess) e = lp::launch_split_planes(from, d, nr, static_cast<int>(d), hi + off, lo + off, c->ld,
+                                                          c->stream);
+      }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dfree(c, stage, stage_bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "split-plane load");
+  } else if (c->ld != d) {
+    LP_CUDA(cudaMemsetAsync(c->dA, 0, c->dA_bytes, c->stream));
+  }
+  for (int i = 0; i < m && !split; ++i) {
     char* dst = static_cast<char*>(c->dA) + size_t(c->row_off[i]) * c->ld * eb;
     LP_CUDA(cudaMemcpy2DAsync(dst, size_t(c->ld) * eb, parts[i], size_t(d) * eb, size_t(d) * eb, size_t(rows[i]), kind,
                               c->stream));
@@ -463,26 +545,183 @@ static lp_status validate_k(lp_ctx* c, int k) {
   if (k > smin)
     return fail(c, LP_ERR_INVALID, "k exceeds the smallest partition's row count (its local Y_i would be rank deficient)");
   const int K = kcap_of(k);
-  if (!c->tc_ready && lp::step_simt_smem(static_cast<int>(c->d), c->ld, c->dtype, K, nullptr) == 0)
+  if (c->planes == 0 && lp::step_simt_smem(static_cast<int>(c->d), c->ld, c->dtype, K, nullptr) == 0)
     return fail(c, LP_ERR_UNSUPPORTED, "no step kernel for d=" + std::to_string(c->d) + ", k=" + std::to_string(k));
   return LP_OK;
 }
 
-// Picks the step kernel: tensor cores for BF16 partitions unless LP_FLAG_SIMT asks
-// otherwise (or the shape has no tensor-core plan), else the SIMT FP32 kernel.
+// Plans the streaming tensor-core step for k (once per padded k) and makes the
+// device segment table match its cluster count.  LP_ERR_UNSUPPORTED when the
+// shape has no streaming kernel.
+static lp_status ensure_tcs(lp_ctx* c, int k) {
+  const int K = kcap_of(k);
+  const int idx = K == 8 ? 0 : (K == 16 ? 1 : 2);
+  if (c->tcs_state[idx] == 0) {
+    lp::TcsPlan& p = c->tcs[idx];
+    c->tcs_state[idx] = -1;
+    if (!lp::tcs_plan(static_cast<int>(c->d), K, c->planes, c->sms, c->tuning, &p))
+      return fail(c, LP_ERR_UNSUPPORTED, "no streaming tensor-core plan for d=" + std::to_string(c->d));
+    const uint16_t* hi = static_cast<const uint16_t*>(c->dA);
+    const uint16_t* lo = c->planes == 2 ? hi + size_t(c->n) * c->ld : nullptr;
+    LP_CUDA(lp::tcs_encode_maps(hi, lo, c->n, static_cast<int>(c->d), c->ld, &p));
+    c->tcs_state[idx] = 1;
+  }
+  if (c->tcs_state[idx] < 0)
+    return fail(c, LP_ERR_UNSUPPORTED, "no streaming tensor-core plan for d=" + std::to_string(c->d));
+  lp::TcsPlan& p = c->tcs[idx];
+  // Whole 128-row tiles per cluster: no more clusters than tiles.
+  const int G = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(p.nclusters, (c->n + 127) / 128)));
+  p.nclusters = G;
+  if (G != c->tcs_G) {
+    std::vector<Segment> segs;
+    std::vector<int> seg_ptr, slot_begin;
+    build_segments(c, G, segs, seg_ptr, slot_begin);
+    lp_status st;
+    if (!c->dSegsTcs &&
+        ((st = dalloc(c, &c->dSegsTcs, (size_t(c->sms) + c->m) * sizeof(Segment))) ||
+         (st = dalloc(c, &c->dSegPtrTcs, (size_t(c->sms) + 1) * 4)) ||
+         (st = dalloc(c, &c->dSlotBeginTcs, (size_t(c->m) + 1) * 4))))
+      return st;
+    LP_CUDA(cudaMemcpyAsync(c->dSegsTcs, segs.data(), segs.size() * sizeof(Segment), cudaMemcpyHostToDevice,
+                            c->stream));
+    LP_CUDA(cudaMemcpyAsync(c->dSegPtrTcs, seg_ptr.data(), seg_ptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    LP_CUDA(cudaMemcpyAsync(c->dSlotBeginTcs, slot_begin.data(), slot_begin.size() * 4, cudaMemcpyHostToDevice,
+                            c->stream));
+    // pageable sources: make sure the copies have read them before the vectors go
+    LP_CUDA(cudaStreamSynchronize(c->stream));
+    c->nslots_tcs = static_cast<int>(segs.size());
+    c->tcs_G = G;
+  }
+  c->tcs_cur = &p;
+  return LP_OK;
+}
+
+// Picks the step kernel.  BF16 and split-plane data run on the tensor cores:
+// the streaming kernel unless LP_FLAG_TC_RESIDENT asks for the resident one
+// (BF16) or the shape has no streaming plan; LP_FLAG_SIMT (BF16 only) and the
+// other dtypes use the SIMT FP32 kernel.
 static lp_status select_path(lp_ctx* c, int k, unsigned flags) {
-  c->use_tc = false;
-  if (c->tc_ready && !(flags & LP_FLAG_SIMT)) {
-    lp::TcPlan p;
-    if (lp::tc_plan(static_cast<int>(c->d), k, c->sms, &p) && p.cluster == c->tc.cluster && p.nch == c->tc.nch) {
-      c->tc.K = p.K;
-      c->tc.smem = p.smem;
-      c->use_tc = true;
+  c->path = PATH_SIMT;
+  if (c->planes > 0 && !(flags & LP_FLAG_SIMT)) {
+    const bool resident = ((flags & LP_FLAG_TC_RESIDENT) || c->prefer_resident) && c->dtype == LP_BF16;
+    if (!resident) {
+      const lp_status st = ensure_tcs(c, k);
+      if (st == LP_OK) c->path = PATH_TCS;
+      else if (st != LP_ERR_UNSUPPORTED) return st;
+      c->err.clear();
+    }
+    if (c->path == PATH_SIMT && c->dtype == LP_BF16 && c->tc_ready) {
+      lp::TcPlan p;
+      if (lp::tc_plan(static_cast<int>(c->d), k, c->sms, &p) && p.cluster == c->tc.cluster && p.nch == c->tc.nch) {
+        c->tc.K = p.K;
+        c->tc.smem = p.smem;
+        c->path = PATH_TC;
+      }
     }
   }
-  if (!c->use_tc && lp::step_simt_smem(static_cast<int>(c->d), c->ld, c->dtype, kcap_of(k), nullptr) == 0)
-    return fail(c, LP_ERR_UNSUPPORTED,
-                "no step kernel for d=" + std::to_string(c->d) + ", k=" + std::to_string(k) + " on this path");
+  if (c->path == PATH_SIMT) {
+    if (c->dtype == LP_F32_BF16X2)
+      return fail(c, LP_ERR_UNSUPPORTED,
+                  "split-plane data run only on the streaming tensor-core kernel, which has no plan for d=" +
+                      std::to_string(c->d) + ", k=" + std::to_string(k));
+    if (lp::step_simt_smem(static_cast<int>(c->d), c->ld, c->dtype, kcap_of(k), nullptr) == 0)
+      return fail(c, LP_ERR_UNSUPPORTED,
+                  "no step kernel for d=" + std::to_string(c->d) + ", k=" + std::to_string(k) + " on this path");
+  }
+  return LP_OK;
+}
+
+lp_status lp_set_tuning(lp_ctx* c, const lp_tuning* t) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  lp::TcsTuning nt;
+  if (t) {
+    if (t->ring_units < 0 || t->lag_units < 0 || t->prefetch_units < 0 || t->cache_hints < 0)
+      return fail(c, LP_ERR_INVALID, "tuning fields must be >= 0");
+    nt.ring_units = t->ring_units;
+    nt.lag_units = t->lag_units;
+    nt.prefetch_units = t->prefetch_units;
+    nt.cache_hints = t->cache_hints;
+  }
+  c->tuning = nt;
+  c->prefer_resident = false;
+  // plans are rebuilt on the next solve; the segment table is kept (same cluster count or rebuilt then)
+  c->tcs_state[0] = c->tcs_state[1] = c->tcs_state[2] = 0;
+  c->tcs_cur = nullptr;
+  return LP_OK;
+}
+
+lp_status lp_autotune(lp_ctx* c, int k, lp_tuning* chosen, int* path_out, double* best_ms) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  lp_status st = validate_k(c, k);
+  if (st) return st;
+  LP_CUDA(cudaSetDevice(c->device));
+  const int K = kcap_of(k);
+  if ((st = ensure_state(c, K))) return st;
+  struct Cand {
+    lp::TcsTuning t;
+    bool resident;
+  };
+  std::vector<Cand> cands;
+  if (c->planes > 0) {
+    for (int lag : {1, 2, 4})
+      for (int hint : {0, 1}) {
+        Cand cd;
+        cd.t.lag_units = lag;
+        cd.t.cache_hints = hint;
+        cd.resident = false;
+        cands.push_back(cd);
+      }
+    if (c->dtype == LP_BF16 && c->tc_ready) cands.push_back(Cand{lp::TcsTuning{}, true});
+  }
+  const lp::TcsTuning saved = c->tuning;
+  const bool saved_res = c->prefer_resident;
+  double best = -1.0;
+  Cand win{saved, saved_res};
+  int win_path = PATH_SIMT;
+  if (!cands.empty()) {
+    LP_CUDA(cudaMemsetAsync(c->dZ, 0, size_t(c->d) * K * 4, c->stream));
+    for (const Cand& cd : cands) {
+      c->tuning = cd.t;
+      c->prefer_resident = cd.resident;
+      c->tcs_state[0] = c->tcs_state[1] = c->tcs_state[2] = 0;
+      if ((st = select_path(c, k, 0))) {
+        if (st == LP_ERR_UNSUPPORTED) continue;
+        break;
+      }
+      if ((st = launch_step(c, K, c->dZ, 0, false))) break;
+      LP_CUDA(cudaEventRecord(c->ev0, c->stream));
+      for (int r = 0; r < 3 && !st; ++r) st = launch_step(c, K, c->dZ, 0, false);
+      if (st) break;
+      LP_CUDA(cudaEventRecord(c->ev1, c->stream));
+      LP_CUDA(cudaEventSynchronize(c->ev1));
+      float ms = 0.f;
+      LP_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+      const double per = ms / 3.0;
+      if (best < 0 || per < best) {
+        best = per;
+        win = cd;
+        win_path = c->path;
+      }
+    }
+  } else {
+    if ((st = select_path(c, k, 0))) return st;
+    win_path = c->path;
+  }
+  c->tuning = win.t;
+  c->prefer_resident = win.resident;
+  c->tcs_state[0] = c->tcs_state[1] = c->tcs_state[2] = 0;
+  c->solved = false;  // the timing launches overwrote the solve buffers
+  if (st) return st;
+  if (chosen) {
+    chosen->ring_units = win.t.ring_units;
+    chosen->lag_units = win.t.lag_units;
+    chosen->prefetch_units = win.t.prefetch_units;
+    chosen->cache_hints = win.t.cache_hints;
+  }
+  if (path_out) *path_out = win_path;
+  if (best_ms) *best_ms = best;
   return LP_OK;
 }
 
@@ -570,7 +809,7 @@ lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator
   c->stats.n = c->n;
   c->stats.d = c->d;
   c->stats.m = m;
-  c->stats.path = c->use_tc ? 1 : 0;
+  c->stats.path = c->path;
   c->solved = true;
   return LP_OK;
 }

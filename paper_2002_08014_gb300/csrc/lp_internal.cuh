@@ -60,6 +60,36 @@ cudaError_t tc_encode_map(void* A, int64_t n, int d, int64_t ld, TcPlan* p);
 cudaError_t launch_step_tc(const TcPlan& p, const Segment* segs, const int* seg_ptr, const float* Z, int64_t z_stride,
                            float* P, int d, int* status, cudaStream_t s);
 
+// ---- fused local power step (tcgen05, streaming; BF16 plane or hi/lo planes) --
+struct TcsPlan {
+  int K = 0;           // padded k (8, 16, 32); MMA N = 2K
+  int planes = 0;      // 1: BF16 A; 2: hi + lo BF16 planes of FP32 A
+  int ncd = 0;         // 64-column chunks of each CTA's column slice (even)
+  int cluster = 0;     // CTAs per cluster splitting d
+  int nclusters = 0;   // clusters in the grid (one CTA per SM)
+  int ring = 0;        // 32 KB ring units
+  int lag = 0;         // first-pass units of tile t+1 issued before tile t's second pass
+  int prefetch = 0;    // first-pass units prefetched into L2 ahead of their load
+  int hints = 0;       // L2 eviction hints on the two passes
+  uint32_t off_B1 = 0, off_B2 = 0, off_W = 0, off_Wrecv = 0, off_bar = 0, tmem_cols = 0;
+  size_t smem = 0;     // dynamic shared memory per CTA
+  alignas(64) unsigned char tmap[2][128];  // CUtensorMaps of the planes
+};
+// Tuning of the streaming kernel (lp_tuning without the C names); zeros are defaults.
+struct TcsTuning {
+  int ring_units = 0, lag_units = 0, prefetch_units = 0, cache_hints = 0;
+};
+// Fills the geometry for (d, k, planes).  False when the shape has no streaming kernel.
+bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan* p);
+// Encodes the tensor maps of the planes (plane1 may be NULL for one plane).
+cudaError_t tcs_encode_maps(const void* plane0, const void* plane1, int64_t n, int d, int64_t ld, TcsPlan* p);
+cudaError_t launch_step_tcs(const TcsPlan& p, const Segment* segs, const int* seg_ptr, const float* Z,
+                            int64_t z_stride, float* P, int d, int* status, cudaStream_t s);
+// FP32 rows (pitch src_ld) -> hi = RNE_bf16(a), lo = RNE_bf16(a - hi) planes (pitch ld,
+// columns d..ld-1 zero).
+cudaError_t launch_split_planes(const float* src, int64_t src_ld, int64_t rows, int d, uint16_t* hi, uint16_t* lo,
+                                int64_t ld, cudaStream_t s);
+
 // Message returned by lp_last_error(NULL) (failures of calls without a context).
 void set_no_context_error(const char* msg);
 inline void set_no_context_error(const std::string& msg) { set_no_context_error(msg.c_str()); }

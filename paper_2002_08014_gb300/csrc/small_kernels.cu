@@ -7,7 +7,10 @@
 // Precision: the d-sized work (Gram, solves, averaging) is FP32; the k x k
 // factorisations (Cholesky, triangular inverse, Jacobi SVD / eigen) are FP64,
 // as are the sign-fix inner products that decide D_i.
+#include <algorithm>
 #include <cfloat>
+
+#include <cuda_bf16.h>
 
 #include "lp_internal.cuh"
 
@@ -46,6 +49,22 @@ __device__ __forceinline__ double recip_nr(double x) {
 }
 
 // ---------------------------------------------------------------- pack / unpack
+// FP32 rows -> two BF16 planes: hi = RNE(a), lo = RNE(a - hi).  a - hi is exact
+// in FP32, so hi + lo matches a to within half an ulp of lo (<= 2^-17 |a|).
+__global__ void split_planes_kernel(const float* __restrict__ src, int64_t src_ld, int64_t rows, int d,
+                                    uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, int64_t ld) {
+  const int64_t total = rows * ld;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = e / ld;
+    const int c = static_cast<int>(e - r * ld);
+    const float a = c < d ? src[r * src_ld + c] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(a);
+    const __nv_bfloat16 l = __float2bfloat16_rn(a - __bfloat162float(h));
+    hi[e] = __bfloat16_as_ushort(h);
+    lo[e] = __bfloat16_as_ushort(l);
+  }
+}
+
 __global__ void pack_kernel(const double* __restrict__ src, float* __restrict__ dst, int batch, int d, int k, int K) {
   const int64_t total = int64_t(batch) * d * K;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
@@ -454,6 +473,15 @@ __global__ void __launch_bounds__(kT) ritz_kernel(const float* __restrict__ Z, c
 }
 
 }  // namespace
+
+cudaError_t launch_split_planes(const float* src, int64_t src_ld, int64_t rows, int d, uint16_t* hi, uint16_t* lo,
+                                int64_t ld, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  const int64_t total = rows * ld;
+  const int64_t blocks = std::min<int64_t>((total + kT - 1) / kT, 4096);
+  split_planes_kernel<<<static_cast<unsigned>(blocks), kT, 0, s>>>(src, src_ld, rows, d, hi, lo, ld);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pack(const double* src, float* dst, int batch, int d, int k, int K, cudaStream_t s) {
   const int64_t total = int64_t(batch) * d * K;

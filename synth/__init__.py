@@ -14,6 +14,7 @@ from .spiked import (  # noqa: F401
 )
 from .lowprec import (  # noqa: F401
     f32_to_bf16_bits,
+    f32_to_bf16x2_planes,
     f32_to_e4m3_rowscaled,
     E4M3_MAX,
 )

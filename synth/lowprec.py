@@ -5,6 +5,8 @@ one FP32 scale per row).  They are input preparation, not part of LocalPower;
 the oracle decodes the stored bytes with its own decoder and never re-encodes.
 
 * BF16: the top 16 bits of the FP32 pattern after round-to-nearest-even.
+* BF16x2 planes of FP32 data: hi = BF16(a), lo = BF16(a - hi), both RNE; a - hi
+  is exact in FP32, so the stored matrix hi + lo is within 2^-17 |a| of a.
 * FP8-E4M3 (the OCP "FN" variant: bias 7, no infinities, max 448):
   scale_r = max_j |a_rj| / 448 in FP32 (1 for an all-zero row), then
   q_rj = E4M3(a_rj / scale_r) with round-to-nearest-even and saturation to
@@ -27,6 +29,15 @@ def f32_to_bf16_bits(x: np.ndarray) -> np.ndarray:
     if nan.any():
         r = np.where(nan, (u >> np.uint32(16)) | np.uint32(0x40), r)
     return r.astype(np.uint16)
+
+
+def f32_to_bf16x2_planes(x: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """FP32 array -> (hi, lo) uint16 BF16 bit patterns with hi = BF16(x), lo = BF16(x - hi)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    hi = f32_to_bf16_bits(x)
+    hi_val = (hi.astype(np.uint32) << np.uint32(16)).view(np.float32)
+    lo = f32_to_bf16_bits((x - hi_val).astype(np.float32))
+    return hi, lo
 
 
 def _e4m3_positive_table() -> np.ndarray:
