@@ -46,9 +46,15 @@ def _args():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage (tensor-core) run of the workload")
-    ap.add_argument("--workload", choices=["fp32", "lowprec"], default="fp32",
-                    help="fp32: the FP32 workload (default, with its BF16-storage run alongside); "
-                         "lowprec: the BF16-storage workload n=4e6, d=2048, k=32")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--shape", default="1024x16", help="kernels: d x k of the step-kernel comparison")
+    ap.add_argument("--workload", choices=["fp32", "lowprec", "plain", "serving", "kernels"], default="fp32",
+                    help="fp32: the FP32 workload (default, with its BF16-storage and split-plane runs alongside); "
+                         "lowprec: the reduced-precision workload n=4e6, d=2048, k=32 (BF16, then FP8-E4M3); "
+                         "plain: the small plain configuration n=4000, d=100, k=5 (latency-bound); "
+                         "serving: a Poisson stream of BF16 truncated-SVD requests through the request server; "
+                         "kernels: every step kernel on one shape (--shape, --rows), one-step solves, for profiling")
     ap.add_argument("--rows", type=int, default=None,
                     help="override n (same spectrum and partition count): a smaller case for profiler captures")
     return ap.parse_args()
@@ -165,7 +171,17 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+KERNELS = {0: "step_simt2_kernel (SIMT FP32 fused A_i^T (A_i Z_i))",
+           1: "step_tc_kernel (tcgen05, tile resident in shared memory, cluster-split d)",
+           2: "step_tcs_kernel (tcgen05 streaming, second pass re-read from L2)"}
+
+
 def _config(c, sched, name: str = WORKLOAD):
+    if name == "plain":
+        text = (f"LocalPower plain: n={c['n']:,} d={c['d']} k={c['k']} m={c['m']}, p=4 x20 rounds, sign-fixing "
+                f"(FP32 A)")
+        return {"workload": text, "n": c["n"], "d": c["d"], "k": c["k"], "m": c["m"], "rounds": len(sched),
+                "local_steps": sum(sched), "l2": "inputs fit in L2 (1.6 MB); latency-bound configuration"}
     if name == "lowprec":
         text = (f"LocalPower BF16 storage: n={c['n']:,} d={c['d']} k={c['k']} m={c['m']}, p=4 x30 rounds + 3 "
                 f"FP32-accumulated p=1 refinement rounds ({sum(sched)} local steps) + Rayleigh-Ritz pass")
@@ -179,7 +195,8 @@ def _config(c, sched, name: str = WORKLOAD):
 
 
 def run_lowprec(args):
-    """The low-precision workload (BF16 storage) on the tensor-core path alone."""
+    """The reduced-precision workload: BF16 storage on the tensor cores (kernel
+    chosen by the autotuner), then the same matrix in FP8-E4M3 with row scales."""
     import torch
     import torch.distributed as dist
 
@@ -200,6 +217,7 @@ def run_lowprec(args):
     stream = torch.cuda.Stream(device=dev)
     hbm_peak, _, peak_src = _peaks()
     lpb = B.LocalPower(bits, dtype="bf16", device=local, stream=stream)
+    choice = B.lp_autotune(lpb.ctx, k)
     for _ in range(args.warmup):
         lpb.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
         lpb.result(k)
@@ -212,25 +230,238 @@ def run_lowprec(args):
             "warmup": args.warmup, "ms_per_step": s["ms_per_solve"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": _config(c, sched, "lowprec"),
             "solves_per_s": s["solves_per_s"], "latency_ms": s["latency_ms"], "clocks": clk,
-            "gpu_launches": s["launches"], "e2e": None,
-            "roofline": {"kernel": "step_tc_kernel (tcgen05, BF16 A, hi/lo BF16 Z and W)", "bound": "hbm",
+            "gpu_launches": s["launches"], "e2e": None, "autotune": choice,
+            "roofline": {"kernel": KERNELS[s["path"]], "bound": "hbm",
                          "achieved": gbs_k, "peak": hbm_peak, "unit": "GB/s", "frac": gbs_k / hbm_peak,
                          "traffic": None, "launch_ms": s["step_ms"], "peak_source": f"{peak_src} HBM copy bandwidth"}}
     line["orthonormality"] = float(np.abs(Z.T @ Z - np.eye(k)).max())
     line["sigma_top3"] = [float(x) for x in sig[:3]]
-    if rank == 0 and not args.no_accuracy and c["n"] * d <= 2_200_000_000:
-        # truth of the decoded BF16 problem (the matrix the solver is given) and of the FP32 original;
-        # forming M in FP64 on the host is skipped above about the FP32 workload's size
-        dec = [oracle.decode_bf16(b) for b in bits]
-        Vb, _ = _truth(dec, c)
+
+    # the same matrix as FP8-E4M3 codes with one FP32 scale per row (SIMT kernel)
+    fp8 = None
+    try:
+        codes, scales = zip(*[synth.f32_to_e4m3_rowscaled(p) for p in parts])
+        lp8 = B.LocalPower(list(codes), dtype="e4m3", row_scales=list(scales), device=local, stream=stream)
+        lp8.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
+        lp8.result(k)
+        ms8, st8, Z8, sig8, clk8 = _timed(torch, dist, world, dev, stream, lp8, k, sched, args.agg, 1, Clocks(local))
+        s8 = _summary(world, 1, ms8, st8, 1, c)
+        lp8.close()
+        fp8 = {"dtype": "e4m3 codes x FP32 row scales, FP32 accumulation", "step_kernel": KERNELS[s8["path"]],
+               "gbs": s8["gbs"], "solves_per_s": s8["solves_per_s"], "ms_per_solve": s8["ms_per_solve"],
+               "step_launch_ms": s8["step_ms"], "clocks": clk8,
+               "note": "FP8 runs on the SIMT kernel: the tensor-core kernels take BF16 operands only"}
+    except Exception as e:  # reported, not hidden
+        fp8 = {"error": str(e)[:300]}
+    line["fp8_path"] = fp8
+
+    if rank == 0 and not args.no_accuracy:
+        # FP64 truth of the decoded BF16 problem (the matrix the solver is given) and of the FP32 original
+        t0 = time.perf_counter()
+        Vb, _ = _truth(bits, c, oracle.decode_bf16)
         Vf, _ = _truth(parts, c)
         line["accuracy"] = {"dist_to_eigh_topk_bf16_problem": oracle.subspace_dist(oracle.orth(Z), Vb),
                             "dist_to_eigh_topk_fp32_problem": oracle.subspace_dist(oracle.orth(Z), Vf),
-                            "quantisation_shift": oracle.subspace_dist(Vb, Vf)}
+                            "quantisation_shift": oracle.subspace_dist(Vb, Vf),
+                            "host_fp64_seconds": time.perf_counter() - t0}
+        if fp8 and "error" not in fp8:
+            line["fp8_path"]["dist_to_eigh_topk_fp32_problem"] = oracle.subspace_dist(oracle.orth(Z8), Vf)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_plain(args):
+    """The small plain configuration (FP32, n=4000, d=100, k=5, m=4): latency-bound,
+    reported as solves/s and per-solve latency over many solves."""
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    import synth
+    from paper_2002_08014_gb300 import binding as B
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    c, A, sizes, Y0, sched = _workload(rank, None, "plain")
+    _timed.y0 = Y0
+    k = c["k"]
+    parts = synth.split_rows(A, sizes)
+    stream = torch.cuda.Stream(device=dev)
+    lp = B.LocalPower(parts, device=local, stream=stream)
+    solves = max(args.steps, 50)
+    for _ in range(max(args.warmup, 3)):
+        lp.submit(k, sched, "sign", Y0, ritz=True, timing=True)
+        lp.result(k)
+    ms, stats, Z, sig, clk = _timed(torch, dist, world, dev, stream, lp, k, sched, "sign", solves, Clocks(local))
+    s = _summary(world, solves, ms, stats, 4, c)
+    lp.close()
+    ref = oracle.localpower(parts, k, sched, "sign", Y0)
+    line = {"metric": METRIC, "value": s["gbs"], "unit": "GB/s", "n_gpus": world, "steps": solves,
+            "warmup": max(args.warmup, 3), "ms_per_step": s["ms_per_solve"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(c, sched, "plain"), "solves_per_s": s["solves_per_s"], "latency_ms": s["latency_ms"],
+            "clocks": clk, "gpu_launches": s["launches"], "e2e": None,
+            "launches_per_solve": s["launches"] / solves, "step_kernel": KERNELS[s["path"]],
+            "dist_to_oracle": oracle.subspace_dist(oracle.orth(Z), ref["Z"])}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _serving_requests(n_req: int, rate: float, seed: int):
+    """Request shapes (log-uniform n, d, m; k uniform in {4, 8, 16, 32}) and Poisson arrival times."""
+    rng = np.random.default_rng(seed)
+    lu = lambda lo, hi, size: np.exp(rng.uniform(np.log(lo), np.log(hi), size))
+    n = np.round(lu(2_000, 200_000, n_req)).astype(int)
+    d = np.round(lu(64, 1024, n_req)).astype(int)
+    m = np.round(lu(4, 32, n_req)).astype(int)
+    k = rng.choice([4, 8, 16, 32], n_req)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    offs = rng.integers(0, 1, n_req)  # filled by the caller once the pool size is known
+    return [dict(n=int(n[i]), d=int(d[i]), m=int(m[i]), k=int(k[i]), t=float(arrivals[i]), off=int(offs[i]),
+                 seed=seed * 100_000 + i) for i in range(n_req)]
+
+
+def run_serving(args):
+    """Continuous batching: a Poisson stream of truncated-SVD requests of mixed
+    shapes through the request server (each BF16, p = 4 x 30 rounds + 3
+    refinement rounds + Rayleigh-Ritz), admitted against an HBM budget.  Rows
+    come from a device-resident pool of spiked BF16 rows (lambda_j = 0.85^j); a
+    request names a row range and its first d columns (row pitch 1024)."""
+    import torch
+
+    import oracle
+    import synth
+    from paper_2002_08014_gb300 import binding as B
+
+    rank, world, local = _dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    seed = synth.configs.SEED_BASE + 5
+    reqs = _serving_requests(args.requests, args.rate, seed)
+    pool_rows, pool_d = 1_000_000, 1024
+    lam = 0.85 ** np.arange(1, pool_d + 1)
+    pool = synth.spiked_rows(pool_rows, pool_d, lam, 0.0, seed, out_dtype=np.float32, threads=os.cpu_count())
+    pool_bits = synth.f32_to_bf16_bits(pool)
+    del pool
+    dev_pool = torch.from_numpy(pool_bits.view(np.int16)).cuda(local)
+    orng = np.random.default_rng(seed + 1)
+    for r in reqs:
+        r["off"] = int(orng.integers(0, pool_rows - r["n"]))
+    sched = [4] * 30
+    budget = 120 << 30
+    lat, done_t, a_bytes = {}, {}, 0.0
+    clocks = Clocks(local)
+    with B.Server(device=local, hbm_budget_bytes=budget, max_active=64) as srv:
+        # warm-up: a few requests of the same kind, not timed
+        for r in reqs[:4]:
+            sizes = synth.partition_sizes(r["n"], r["m"])
+            offs = r["off"] + np.cumsum([0] + sizes[:-1])
+            parts = [dev_pool[o:o + s_] for o, s_ in zip(offs, sizes)]
+            rid = srv.submit(parts, r["k"], sched, "sign", synth.gaussian_start(r["d"], r["k"], r["seed"]),
+                             dtype="bf16", refine_rounds=3, row_pitch=pool_d, d=r["d"])
+            while rid not in srv.progress():
+                time.sleep(0.0005)
+            srv.result(rid)
+        torch.cuda.synchronize()
+        clocks.start()
+        t0 = time.perf_counter()
+        nxt, ids = 0, {}
+        peak = {"active": 0, "queued": 0}
+        while len(done_t) < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt]["t"] <= now:
+                r = reqs[nxt]
+                sizes = synth.partition_sizes(r["n"], r["m"])
+                offs = r["off"] + np.cumsum([0] + sizes[:-1])
+                parts = [dev_pool[o:o + s_] for o, s_ in zip(offs, sizes)]
+                y0 = synth.gaussian_start(r["d"], r["k"], r["seed"])
+                ids[srv.submit(parts, r["k"], sched, "sign", y0, dtype="bf16", refine_rounds=3, row_pitch=pool_d,
+                               d=r["d"])] = nxt
+                nxt += 1
+            fin = srv.progress()
+            tnow = time.perf_counter() - t0
+            for rid in fin:
+                i = ids[rid]
+                done_t[i] = tnow
+                Z, sig, st = srv.result(rid)
+                a_bytes += st["a_bytes"]
+                reqs[i]["Z"] = Z
+            info = srv.query()
+            peak["active"] = max(peak["active"], info["active"])
+            peak["queued"] = max(peak["queued"], info["queued"])
+            if not fin:
+                time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+        hbm_peak = srv.query()["hbm_peak"]
+    clk = clocks.stop()
+    lats = np.array([(done_t[i] - reqs[i]["t"]) * 1e3 for i in range(len(reqs))])
+    span = max(done_t.values()) - reqs[0]["t"]
+    # accuracy of a sample against the FP64 eigendecomposition of each request's decoded matrix
+    acc = []
+    for i in np.linspace(0, len(reqs) - 1, 8).astype(int):
+        r = reqs[i]
+        rows = oracle.decode_bf16(pool_bits[r["off"]:r["off"] + r["n"], :r["d"]])
+        w, V = np.linalg.eigh(rows.T @ rows / r["n"])
+        acc.append(oracle.subspace_dist(oracle.orth(r["Z"]), V[:, ::-1][:, :r["k"]]))
+    line = {"metric": METRIC, "value": a_bytes / span / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": len(reqs),
+            "warmup": 4, "ms_per_step": span * 1e3 / len(reqs), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"LocalPower serving: {len(reqs)} truncated-SVD requests, Poisson arrivals at "
+                                   f"{args.rate:g} req/s, n log-uniform [2e3, 2e5], d [64, 1024], m [4, 32], "
+                                   f"k in {{4, 8, 16, 32}}, BF16, p=4 x30 rounds + 3 refinement rounds + Ritz, "
+                                   f"admission budget 120 GB",
+                       "requests": len(reqs), "rate_per_s": args.rate, "budget_bytes": budget, "max_active": 64,
+                       "l2": "requests' A from a 2 GB device pool (larger than L2)"},
+            "solves_per_s": len(reqs) / span, "latency_ms": {"p50": float(np.percentile(lats, 50)),
+                                                             "p99": float(np.percentile(lats, 99)),
+                                                             "max": float(lats.max()), "samples": len(lats)},
+            "offered_solves_per_s": args.rate, "wall_s": wall, "peak_active": peak["active"],
+            "peak_queued": peak["queued"], "hbm_peak_bytes": int(hbm_peak), "clocks": clk, "e2e": None,
+            "accuracy_sample": {"dist_to_eigh_topk": [float(x) for x in acc], "max": float(max(acc))}}
+    print(json.dumps(line))
+
+
+def run_kernels(args):
+    """Each step kernel on one shape: one-step solves (a single fused-step launch
+    each) per kernel, in a fixed order, for profiler captures and quick scans:
+    SIMT FP32, streaming tcgen05 BF16, resident tcgen05 BF16, streaming tcgen05
+    on hi/lo planes of the FP32 data."""
+    import synth
+    from paper_2002_08014_gb300 import binding as B
+
+    d, k = (int(x) for x in args.shape.lower().split("x"))
+    n = int(args.rows or (1 << 31) // (d * 4))
+    m = 64
+    lam = 10.0 * 0.9 ** np.arange(1, min(32, d) + 1)
+    A = synth.spiked_rows(n, d, lam, np.sqrt(0.1), synth.configs.SEED_BASE + 9, threads=os.cpu_count())
+    parts = synth.split_rows(A, synth.partition_sizes(n, m))
+    Y0 = synth.gaussian_start(d, k, 1)
+    runs = [("f32", parts, 0), ("bf16", None, 0), ("bf16", None, B.LP_FLAG_TC_RESIDENT), ("f32_bf16x2", parts, 0)]
+    bits = [synth.f32_to_bf16_bits(p) for p in parts]
+    out = {}
+    for dtype, data, flags in runs:
+        eb = 2 if dtype == "bf16" else 4
+        try:
+            with B.LocalPower(data if data is not None else bits, dtype=dtype) as lp:
+                ms = []
+                for _ in range(max(args.steps, 2)):
+                    B.lp_solve(lp.ctx, k, [1], "sign", Y0, 0, B.LP_FLAG_TIMING | B.LP_FLAG_NO_GRAPH | flags)
+                    _, _, st = lp.result(k)
+                    ms.append(st["ms_step_kernels"])
+            best = min(ms[1:])
+            out[f"{dtype}{'_resident' if flags else ''}"] = {
+                "kernel": KERNELS[st["path"]], "launch_ms": best, "gbs": n * d * eb / (best / 1e3) / 1e9}
+        except Exception as e:
+            out[f"{dtype}{'_resident' if flags else ''}"] = {"error": str(e)[:200]}
+    print(json.dumps({"workload": "kernels", "n": n, "d": d, "k": k, "m": m, "results": out}))
 
 
 def _timed(torch, dist, world, dev, stream, lp, k, sched, agg, steps, clocks=None):
@@ -292,11 +523,12 @@ def _summary(world, steps, ms, stats, elem_bytes, c):
             "bytes_solve": bytes_solve}
 
 
-def _truth(parts, c):
-    """Top-k eigenvectors / eigenvalues of M = A^T A / n (FP64, on the host)."""
+def _truth(parts, c, decode=None):
+    """Top-k eigenvectors / eigenvalues of M = A^T A / n (FP64, on the host);
+    `decode` maps a stored partition to its FP64 values, a few at a time."""
     M = np.zeros((c["d"], c["d"]))
     for i in range(0, len(parts), 8):
-        blk = np.concatenate(parts[i:i + 8]).astype(np.float64)
+        blk = np.concatenate([decode(p) if decode else p for p in parts[i:i + 8]]).astype(np.float64)
         M += blk.T @ blk
     lam, V = np.linalg.eigh(M / c["n"])
     return V[:, ::-1][:, :c["k"]], lam[::-1][:c["k"]]
@@ -368,7 +600,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(c, sched),
             "solves_per_s": f32["solves_per_s"], "latency_ms": f32["latency_ms"], "clocks": clk,
             "gpu_launches": f32["launches"], "e2e": e2e,
-            "roofline": {"kernel": "step_simt_kernel (fused A_i^T (A_i Z_i), FP32)", "bound": "alu",
+            "roofline": {"kernel": KERNELS[f32["path"]], "bound": "alu",
                          "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
                          "traffic": None, "launch_ms": f32["step_ms"],
                          "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz"},
@@ -381,6 +613,7 @@ def run_ours(args):
     if not args.no_bf16:
         bits = [synth.f32_to_bf16_bits(p) for p in parts]
         lpb = B.LocalPower(bits, dtype="bf16", device=local, stream=stream)
+        choice = B.lp_autotune(lpb.ctx, k)
         for _ in range(args.warmup):
             lpb.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
             lpb.result(k)
@@ -390,13 +623,35 @@ def run_ours(args):
         lpb.close()
         gbs_b = b16["launch_bytes"] / (b16["step_ms"] / 1e3) / 1e9
         line["precision_path"] = {
-            "dtype": "bf16 storage, FP32 accumulation (hi/lo BF16 operands)", "step_kernel":
-            "step_tc_kernel (tcgen05)" if b16["path"] == 1 else "step_simt_kernel", "gbs": b16["gbs"],
+            "dtype": "bf16 storage, FP32 accumulation (hi/lo BF16 operands)", "step_kernel": KERNELS[b16["path"]],
+            "autotune": choice, "gbs": b16["gbs"],
             "solves_per_s": b16["solves_per_s"], "ms_per_solve": b16["ms_per_solve"],
             "latency_ms": b16["latency_ms"], "clocks": clkb, "gpu_launches": b16["launches"],
             "speedup_solves_vs_fp32": b16["solves_per_s"] / f32["solves_per_s"],
             "roofline": {"bound": "hbm", "achieved": gbs_b, "peak": hbm_peak, "unit": "GB/s",
                          "frac": gbs_b / hbm_peak, "traffic": None, "launch_ms": b16["step_ms"],
+                         "peak_source": f"{peak_src} HBM copy bandwidth"}}
+
+    # ---------------- the FP32 data stored as hi + lo BF16 planes (same bytes, tensor cores)
+    Zs = None
+    if not args.no_bf16:
+        lps = B.LocalPower(parts, dtype="f32_bf16x2", device=local, stream=stream)
+        choice_s = B.lp_autotune(lps.ctx, k)
+        for _ in range(args.warmup):
+            lps.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
+            lps.result(k)
+        mss, statss, Zs, sigs, clks = _timed(torch, dist, world, dev, stream, lps, k, sched, args.agg, args.steps,
+                                             Clocks(local))
+        sp = _summary(world, args.steps, mss, statss, 4, c)
+        lps.close()
+        gbs_s = sp["launch_bytes"] / (sp["step_ms"] / 1e3) / 1e9
+        line["split_plane_path"] = {
+            "dtype": "FP32 data as hi + lo BF16 planes (4 bytes per element), FP32 accumulation",
+            "step_kernel": KERNELS[sp["path"]], "autotune": choice_s, "gbs": sp["gbs"],
+            "solves_per_s": sp["solves_per_s"], "ms_per_solve": sp["ms_per_solve"], "latency_ms": sp["latency_ms"],
+            "clocks": clks, "speedup_solves_vs_fp32": sp["solves_per_s"] / f32["solves_per_s"],
+            "roofline": {"bound": "hbm", "achieved": gbs_s, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": gbs_s / hbm_peak, "traffic": None, "launch_ms": sp["step_ms"],
                          "peak_source": f"{peak_src} HBM copy bandwidth"}}
 
     if rank == 0 and not args.no_accuracy:
@@ -409,6 +664,10 @@ def run_ours(args):
             line["precision_path"]["accuracy"] = {
                 "dist_to_eigh_topk_of_fp32_problem": oracle.subspace_dist(oracle.orth(Zb), V),
                 "dist_to_fp32_path_output": oracle.subspace_dist(oracle.orth(Zb), oracle.orth(Z))}
+        if Zs is not None:
+            line["split_plane_path"]["accuracy"] = {
+                "dist_to_eigh_topk_of_fp32_problem": oracle.subspace_dist(oracle.orth(Zs), V),
+                "dist_to_fp32_path_output": oracle.subspace_dist(oracle.orth(Zs), oracle.orth(Z))}
     if rank == 0 and not args.no_cpu_baseline:
         gbs, dt = _oracle_sample_gbps(parts, Y0, 3)
         line["cpu_baseline"] = {"value": gbs, "unit": "GB/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -426,5 +685,11 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "lowprec":
         run_lowprec(a)
+    elif a.workload == "plain":
+        run_plain(a)
+    elif a.workload == "serving":
+        run_serving(a)
+    elif a.workload == "kernels":
+        run_kernels(a)
     else:
         run_ours(a)

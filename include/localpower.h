@@ -67,6 +67,8 @@ typedef enum lp_ptr_space { LP_HOST = 0, LP_DEVICE = 1 } lp_ptr_space;
 #define LP_FLAG_RITZ   1u   /* finish with a Rayleigh-Ritz step: ordered basis + sigma */
 #define LP_FLAG_TIMING 2u   /* record CUDA events around every fused power-step launch */
 #define LP_FLAG_SIMT   4u   /* BF16 data: use the SIMT FP32 step kernel instead of the tensor-core one */
+#define LP_FLAG_NO_GRAPH 16u     /* launch the solve's kernels one by one instead of replaying the
+                                 * CUDA graph captured for this (k, schedule, aggregator, flags)  */
 #define LP_FLAG_TC_RESIDENT 8u  /* BF16 data: use the tensor-core step that keeps each tile in shared
                                  * memory for both contractions (cluster-split d) instead of the
                                  * streaming one; ignored for other dtypes */
@@ -186,6 +188,83 @@ void lp_destroy(lp_ctx* ctx);
  * until the next call on the context.  With ctx == NULL: the last failure of a
  * call that has no context (lp_create, lp_power_step_static) on this thread. */
 const char* lp_last_error(const lp_ctx* ctx);
+
+/* ----------------------------------------------------------------------------
+ * Request server: continuous batching of independent truncated-SVD solves on
+ * one GPU.  The paper has no counterpart; it serves many LocalPower problems
+ * at once.  Each admitted request gets its own context and stream, so its
+ * partitions A_i and iterates Z_i stay on the device across its rounds while
+ * the rounds of other requests run beside it; requests that arrive while
+ * others run are admitted as soon as the HBM budget and the active-request
+ * limit allow, in arrival order.  One thread drives a server at a time.
+ * ------------------------------------------------------------------------- */
+typedef struct lp_server lp_server;
+
+typedef struct lp_request {
+    /* the data, as for lp_load_partitions, plus a source row pitch */
+    int m;
+    const int64_t* rows;            /* m row counts s_i                                 */
+    int64_t d;
+    int64_t row_pitch;              /* elements between source rows (0 = d)            */
+    lp_dtype dtype;
+    const void* const* parts;       /* m pointers; must stay valid until completion    */
+    const float* const* row_scales; /* LP_FP8_E4M3 only, else NULL                      */
+    lp_ptr_space space;
+    /* the solve, as for lp_solve */
+    int k;
+    const int* p_schedule;
+    int T;
+    lp_aggregator agg;
+    const double* y0;               /* d x k row-major, host                           */
+    int refine_rounds;
+    unsigned flags;
+} lp_request;
+
+typedef struct lp_server_info {
+    int64_t queued, active, completed;    /* requests by state (completed: not yet fetched) */
+    uint64_t hbm_in_use, hbm_peak, hbm_budget;
+} lp_server_info;
+
+/*
+ * lp_server_create: a server on `device` that admits requests while the sum of
+ * their device-memory estimates stays within hbm_budget_bytes (0 = no bound)
+ * and at most max_active (>= 1) are on the device.
+ */
+lp_status lp_server_create(lp_server** out, int device, size_t hbm_budget_bytes, int max_active);
+
+/*
+ * lp_server_submit: queue a request; *id receives its id (> 0).  The small
+ * arrays (rows, p_schedule, y0, the pointer arrays) are copied; the partition
+ * buffers are read when the request is admitted and must not change until it
+ * completes.  LP_ERR_INVALID for malformed requests (the checks of
+ * lp_load_partitions / lp_solve), LP_ERR_OOM when the request alone exceeds the
+ * budget.
+ */
+lp_status lp_server_submit(lp_server* s, const lp_request* req, int64_t* id);
+
+/*
+ * lp_server_progress: retire requests whose solve finished (their device memory
+ * is released), admit queued requests, and write up to `cap` ids of requests
+ * that completed since the last call to done_ids (*n_done of them).  Admission
+ * copies the partitions to the device and enqueues the whole solve on the
+ * request's stream; nothing else waits for the GPU.
+ */
+lp_status lp_server_progress(lp_server* s, int64_t* done_ids, int cap, int* n_done);
+
+/*
+ * lp_server_result: results of a completed request (as lp_result), then the
+ * request is forgotten.  Returns the request's own status (its load or solve
+ * failure, if any); LP_ERR_STATE if the id is unknown or not complete.
+ */
+lp_status lp_server_result(lp_server* s, int64_t id, double* z_out, double* sigma_out, lp_stats* stats);
+
+lp_status lp_server_query(lp_server* s, lp_server_info* info);
+
+/* lp_server_error: text of the last failure on the server ("" if none). */
+const char* lp_server_error(const lp_server* s);
+
+/* lp_server_destroy: wait for active requests, free everything; NULL is a no-op. */
+void lp_server_destroy(lp_server* s);
 
 /* ----------------------------------------------------------------------------
  * Single-kernel entry points, for checking one step of the method at a time.

@@ -18,7 +18,7 @@ STATUS_NAMES = ["LP_OK", "LP_ERR_INVALID", "LP_ERR_STATE", "LP_ERR_OOM", "LP_ERR
 LP_F32, LP_BF16, LP_FP8_E4M3, LP_F32_BF16X2 = 0, 1, 2, 3
 LP_AGG_IDENTITY, LP_AGG_SIGN, LP_AGG_OPT = 0, 1, 2
 LP_HOST, LP_DEVICE = 0, 1
-LP_FLAG_RITZ, LP_FLAG_TIMING, LP_FLAG_SIMT, LP_FLAG_TC_RESIDENT = 1, 2, 4, 8
+LP_FLAG_RITZ, LP_FLAG_TIMING, LP_FLAG_SIMT, LP_FLAG_TC_RESIDENT, LP_FLAG_NO_GRAPH = 1, 2, 4, 8, 16
 LP_MAX_K = 32
 
 AGG = {"identity": LP_AGG_IDENTITY, "sign": LP_AGG_SIGN, "opt": LP_AGG_OPT}
@@ -27,7 +27,9 @@ PATHS = {0: "simt", 1: "tc_resident", 2: "tc_streaming"}
 
 # Every symbol the header declares, in declaration order.
 EXPORTS = ["lp_create", "lp_load_partitions", "lp_solve", "lp_result", "lp_destroy", "lp_last_error",
-           "lp_set_tuning", "lp_autotune", "lp_power_step", "lp_orth", "lp_align_aggregate", "lp_power_step_static"]
+           "lp_set_tuning", "lp_autotune", "lp_server_create", "lp_server_submit", "lp_server_progress",
+           "lp_server_result", "lp_server_query", "lp_server_error", "lp_server_destroy", "lp_power_step", "lp_orth",
+           "lp_align_aggregate", "lp_power_step_static"]
 
 
 class lp_stats(C.Structure):
@@ -43,6 +45,18 @@ class lp_stats(C.Structure):
 class lp_tuning(C.Structure):
     _fields_ = [("ring_units", C.c_int32), ("lag_units", C.c_int32), ("prefetch_units", C.c_int32),
                 ("cache_hints", C.c_int32)]
+
+
+class lp_request(C.Structure):
+    _fields_ = [("m", C.c_int), ("rows", C.POINTER(C.c_int64)), ("d", C.c_int64), ("row_pitch", C.c_int64),
+                ("dtype", C.c_int), ("parts", C.POINTER(C.c_void_p)), ("row_scales", C.POINTER(C.c_void_p)),
+                ("space", C.c_int), ("k", C.c_int), ("p_schedule", C.POINTER(C.c_int)), ("T", C.c_int),
+                ("agg", C.c_int), ("y0", C.POINTER(C.c_double)), ("refine_rounds", C.c_int), ("flags", C.c_uint)]
+
+
+class lp_server_info(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("active", C.c_int64), ("completed", C.c_int64),
+                ("hbm_in_use", C.c_uint64), ("hbm_peak", C.c_uint64), ("hbm_budget", C.c_uint64)]
 
 
 class LPError(RuntimeError):
@@ -86,8 +100,17 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
     L.lp_power_step_static.argtypes = [P, I, C.POINTER(I64), I64, I, P, P, P]
     L.lp_set_tuning.argtypes = [P, C.POINTER(lp_tuning)]
     L.lp_autotune.argtypes = [P, I, C.POINTER(lp_tuning), C.POINTER(I), C.POINTER(C.c_double)]
+    L.lp_server_create.argtypes = [C.POINTER(P), I, C.c_size_t, I]
+    L.lp_server_submit.argtypes = [P, C.POINTER(lp_request), C.POINTER(I64)]
+    L.lp_server_progress.argtypes = [P, C.POINTER(I64), I, C.POINTER(I)]
+    L.lp_server_result.argtypes = [P, I64, P, P, C.POINTER(lp_stats)]
+    L.lp_server_query.argtypes = [P, C.POINTER(lp_server_info)]
+    L.lp_server_error.argtypes = [P]
+    L.lp_server_error.restype = C.c_char_p
+    L.lp_server_destroy.argtypes = [P]
+    L.lp_server_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("lp_destroy", "lp_last_error"):
+        if name not in ("lp_destroy", "lp_last_error", "lp_server_error", "lp_server_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -323,3 +346,92 @@ class LocalPower:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------- request server
+
+class Server:
+    """lp_server_*: continuous batching of independent solves.  Keeps each
+    request's buffers alive until its result is fetched."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_active: int = 16):
+        L = load()
+        self.h = C.c_void_p()
+        st = L.lp_server_create(C.byref(self.h), device, hbm_budget_bytes, max_active)
+        if st != LP_OK:
+            raise LPError(st, "lp_server_create failed")
+        self._keep = {}
+        self._shape = {}
+
+    def _check(self, st):
+        if st != LP_OK:
+            raise LPError(st, load().lp_server_error(self.h).decode(errors="replace"))
+
+    def submit(self, parts, k: int, p_schedule, agg: str, y0, dtype: str = "f32", row_scales=None,
+               refine_rounds: int = 0, flags: int = LP_FLAG_RITZ, row_pitch: int = 0, d: int | None = None) -> int:
+        """parts: host arrays or CUDA tensors (s_i x pitch); d defaults to the parts' width."""
+        np_dt = {"f32": np.float32, "bf16": np.uint16, "e4m3": np.uint8, "f32_bf16x2": np.float32}[dtype]
+        m = len(parts)
+        keep, ptrs, spaces = [], [], set()
+        for p in parts:
+            q, sp, kk = _ptr(p, np_dt)
+            ptrs.append(q.value)
+            keep.append(kk)
+            spaces.add(sp)
+        if len(spaces) != 1:
+            raise ValueError("partitions must all be host or all device")
+        dd = int(d if d is not None else parts[0].shape[1])
+        rows = (C.c_int64 * m)(*[int(p.shape[0]) for p in parts])
+        parr = (C.c_void_p * m)(*ptrs)
+        sarr = None
+        if row_scales is not None:
+            sl = []
+            for sc in row_scales:
+                q, _, kk = _ptr(sc, np.float32)
+                sl.append(q.value)
+                keep.append(kk)
+            sarr = (C.c_void_p * m)(*sl)
+        sched = np.ascontiguousarray(np.asarray(p_schedule, dtype=np.int32))
+        y0c = np.ascontiguousarray(y0, dtype=np.float64)
+        req = lp_request(m, rows, dd, int(row_pitch), DTYPE[dtype], parr, sarr, spaces.pop(), int(k),
+                         sched.ctypes.data_as(C.POINTER(C.c_int)), len(sched), AGG[agg],
+                         y0c.ctypes.data_as(C.POINTER(C.c_double)), int(refine_rounds), int(flags))
+        rid = C.c_int64(0)
+        self._check(load().lp_server_submit(self.h, C.byref(req), C.byref(rid)))
+        self._keep[rid.value] = (keep, rows, parr, sarr, sched, y0c)
+        self._shape[rid.value] = (dd, int(k))
+        return rid.value
+
+    def progress(self, cap: int = 256) -> list[int]:
+        ids = (C.c_int64 * cap)()
+        n = C.c_int(0)
+        self._check(load().lp_server_progress(self.h, ids, cap, C.byref(n)))
+        return [ids[i] for i in range(n.value)]
+
+    def result(self, rid: int):
+        d, k = self._shape.get(rid, (1, 1))   # unknown ids: the library reports LP_ERR_STATE
+        Z = np.empty((d, k), dtype=np.float64)
+        sig = np.empty(k, dtype=np.float64)
+        st = lp_stats()
+        code = load().lp_server_result(self.h, rid, Z.ctypes.data, sig.ctypes.data, C.byref(st))
+        self._keep.pop(rid, None)
+        self._shape.pop(rid, None)
+        self._check(code)
+        return Z, sig, st.as_dict()
+
+    def query(self) -> dict:
+        info = lp_server_info()
+        self._check(load().lp_server_query(self.h, C.byref(info)))
+        return {f: getattr(info, f) for f, _ in info._fields_}
+
+    def close(self):
+        if self.h:
+            load().lp_server_destroy(self.h)
+            self.h = C.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -19,7 +19,8 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB_NAME = "liblocalpower.so"
 LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 
-SOURCES = ["lp_capi.cu", "step_simt.cu", "step_tc.cu", "step_tcs.cu", "small_kernels.cu", "step_static.cu"]
+SOURCES = ["lp_capi.cu", "lp_server.cu", "step_simt.cu", "step_tc.cu", "step_tcs.cu", "small_kernels.cu",
+           "step_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", INCLUDE, "-I", CSRC]

@@ -73,6 +73,13 @@ struct lp_ctx {
   lp::TcsTuning tuning;
   bool prefer_resident = false;  // set by lp_autotune for LP_BF16 data
 
+  // CUDA graph of the last solve's launch sequence, replayed while its key matches
+  uint64_t gen = 1;  // bumped whenever buffers, plans or tuning change
+  std::vector<int64_t> graph_key;
+  cudaGraphExec_t graph_exec = nullptr;
+  lp_stats graph_stats{};
+  int graph_step_ev_used = 0;
+
   // solve state (capacity in K)
   int Kcap = 0;
   float *dP = nullptr, *dYl = nullptr, *dZl = nullptr, *dY = nullptr, *dZ = nullptr, *dG = nullptr, *dMZ = nullptr;
@@ -149,6 +156,14 @@ size_t elem_bytes(lp_dtype t) { return (t == LP_F32 || t == LP_F32_BF16X2) ? 4 :
 // Bytes per stored element of one plane.
 size_t plane_bytes(lp_dtype t) { return t == LP_F32_BF16X2 ? 2 : elem_bytes(t); }
 
+// Forget the captured solve graph (buffers, plans or tuning changed).
+void drop_graph(lp_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+  c->graph_key.clear();
+  c->gen++;
+}
+
 struct StateSizes {
   size_t P, Yl, Y, G, stage;
 };
@@ -182,6 +197,7 @@ void free_state(lp_ctx* c) {
 
 lp_status ensure_state(lp_ctx* c, int K) {
   if (c->Kcap >= K) return LP_OK;
+  drop_graph(c);
   free_state(c);
   StateSizes s = state_sizes(c, K);
   lp_status st;
@@ -199,6 +215,7 @@ lp_status ensure_state(lp_ctx* c, int K) {
 }
 
 void free_partitions(lp_ctx* c) {
+  drop_graph(c);
   dfree(c, c->dA, c->dA_bytes);
   dfree(c, c->dScales, size_t(c->n) * 4);
   dfree(c, c->dSegs, (size_t(c->grid) + c->m) * sizeof(Segment));
@@ -298,7 +315,7 @@ lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool t
       LP_CUDA(cudaEventCreate(&e));
       c->step_ev.push_back(e);
     }
-    LP_CUDA(cudaEventRecord(c->step_ev[c->step_ev_used], c->stream));
+    LP_CUDA(cudaEventRecordWithFlags(c->step_ev[c->step_ev_used], c->stream, cudaEventRecordExternal));
   }
   cudaError_t e;
   if (c->path == PATH_TCS)
@@ -311,7 +328,7 @@ lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool t
     e = lp::launch_step_simt(a, c->dtype, K, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "fused power-step launch");
   if (timing) {
-    LP_CUDA(cudaEventRecord(c->step_ev[c->step_ev_used + 1], c->stream));
+    LP_CUDA(cudaEventRecordWithFlags(c->step_ev[c->step_ev_used + 1], c->stream, cudaEventRecordExternal));
     c->step_ev_used += 2;
   }
   c->stats.step_launches++;
@@ -376,6 +393,7 @@ void lp_destroy(lp_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   free_partitions(c);
   dfree(c, c->dStatus, 16);
+  drop_graph(c);
   for (cudaEvent_t e : c->step_ev) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -387,8 +405,16 @@ const char* lp_last_error(const lp_ctx* c) { return c ? c->err.c_str() : g_creat
 
 lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, lp_dtype dtype,
                              const void* const* parts, const float* const* row_scales, lp_ptr_space space) {
+  return lp::load_pitched(c, m, rows, d, d, dtype, parts, row_scales, space);
+}
+
+}  // extern "C"
+
+lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int64_t pitch, lp_dtype dtype,
+                           const void* const* parts, const float* const* row_scales, lp_ptr_space space) {
   if (!c) return LP_ERR_INVALID;
   c->err.clear();
+  if (pitch < d) return fail(c, LP_ERR_INVALID, "row pitch below d");
   if (m < 1 || !rows || !parts) return fail(c, LP_ERR_INVALID, "need m >= 1 and non-NULL rows/parts");
   if (d < 1 || d > (1 << 20)) return fail(c, LP_ERR_INVALID, "d out of range");
   if (dtype != LP_F32 && dtype != LP_BF16 && dtype != LP_FP8_E4M3 && dtype != LP_F32_BF16X2)
@@ -506,13 +532,16 @@ lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, l
       for (int64_t r0 = 0; r0 < rows[i] && e == cudaSuccess; r0 += chunk_rows) {
         const int64_t nr = std::min(chunk_rows, rows[i] - r0);
         const size_t off = size_t(c->row_off[i] + r0) * c->ld;
-        const float* from = src + size_t(r0) * d;
+        const float* from = src + size_t(r0) * pitch;
+        int64_t from_ld = pitch;
         if (space == LP_HOST) {
-          e = cudaMemcpyAsync(stage, from, size_t(nr) * d * 4, cudaMemcpyHostToDevice, c->stream);
+          e = cudaMemcpy2DAsync(stage, size_t(d) * 4, from, size_t(pitch) * 4, size_t(d) * 4, size_t(nr),
+                                cudaMemcpyHostToDevice, c->stream);
           from = stage;
+          from_ld = d;
         }
-        if (e == cudaSuccess) e = lp::launch_split_planes(from, d, nr, static_cast<int>(d), hi + off, lo + off, c->ld,
-                                                          c->stream);
+        if (e == cudaSuccess)
+          e = lp::launch_split_planes(from, from_ld, nr, static_cast<int>(d), hi + off, lo + off, c->ld, c->stream);
       }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -523,7 +552,7 @@ lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, l
   }
   for (int i = 0; i < m && !split; ++i) {
     char* dst = static_cast<char*>(c->dA) + size_t(c->row_off[i]) * c->ld * eb;
-    LP_CUDA(cudaMemcpy2DAsync(dst, size_t(c->ld) * eb, parts[i], size_t(d) * eb, size_t(d) * eb, size_t(rows[i]), kind,
+    LP_CUDA(cudaMemcpy2DAsync(dst, size_t(c->ld) * eb, parts[i], size_t(pitch) * eb, size_t(d) * eb, size_t(rows[i]), kind,
                               c->stream));
     if (dtype == LP_FP8_E4M3)
       LP_CUDA(cudaMemcpyAsync(c->dScales + c->row_off[i], row_scales[i], size_t(rows[i]) * 4, kind, c->stream));
@@ -536,6 +565,46 @@ lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, l
   LP_CUDA(cudaStreamSynchronize(c->stream));
   return LP_OK;
 }
+
+size_t lp::estimate_bytes(int sms, int m, const int64_t* rows, int64_t d, int64_t pitch_unused, lp_dtype dtype,
+                          int k, lp_ptr_space space) {
+  (void)pitch_unused;
+  auto r256 = [](size_t b) -> size_t { return ((b ? b : 16) + 255) / 256 * 256; };
+  int64_t n = 0, smax = 0;
+  for (int i = 0; i < m; ++i) {
+    n += rows[i];
+    smax = std::max(smax, rows[i]);
+  }
+  const size_t eb = plane_bytes(dtype);
+  const int planes = dtype == LP_F32_BF16X2 ? 2 : 1;
+  const int64_t per16 = 16 / static_cast<int64_t>(eb);
+  const size_t ld = size_t((d + per16 - 1) / per16 * per16);
+  const size_t K = size_t(kcap_of(k)), D = size_t(d), M = size_t(m);
+  size_t tot = r256(size_t(n) * ld * eb * planes);
+  if (dtype == LP_FP8_E4M3) tot += r256(size_t(n) * 4);
+  // segment tables of the three step kernels, weights
+  tot += 3 * (r256((size_t(sms) + M) * sizeof(Segment)) + r256((size_t(sms) + 1) * 4) + r256((M + 1) * 4)) +
+         2 * r256(M * 4);
+  // solve state
+  tot += r256((size_t(sms) + M) * D * K * 4) + 2 * r256(M * D * K * 4) + 3 * r256(D * K * 4) + r256(M * K * K * 4) +
+         r256(D * LP_MAX_K * 8) + r256(LP_MAX_K * 8) + r256(M * D * K * 8) + r256(16);
+  if (dtype == LP_F32_BF16X2 && space == LP_HOST) {
+    const int64_t chunk_rows = std::max<int64_t>(1, (int64_t(1) << 24) / d);
+    tot += r256(size_t(std::min(chunk_rows, smax)) * D * 4);  // load staging
+  }
+  return tot + (tot >> 6) + (1u << 20);  // slack for rounding
+}
+
+int lp::solve_state(lp_ctx* c) {
+  if (!c || !c->solved) return -1;
+  const cudaError_t e = cudaEventQuery(c->ev1);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  (void)cudaGetLastError();
+  return -1;
+}
+
+extern "C" {
 
 static lp_status validate_k(lp_ctx* c, int k) {
   if (c->m == 0) return fail(c, LP_ERR_STATE, "no partitions loaded");
@@ -631,6 +700,65 @@ static lp_status select_path(lp_ctx* c, int k, unsigned flags) {
   return LP_OK;
 }
 
+// The launch sequence of one solve (Alg. 1 in rounds, then Ritz or unpack), on
+// the context's stream; lp_solve runs it eagerly or captures it into a graph.
+static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, int refine_rounds,
+                            bool timing, const double* dy0) {
+  const int d = static_cast<int>(c->d);
+  const int m = c->m;
+  const int K = kcap_of(k);
+  lp_status st;
+  LP_CUDA(cudaMemsetAsync(c->dStatus, 0, 4, c->stream));
+  if ((st = check_launch(c, lp::launch_pack(dy0, c->dY, 1, d, k, K, c->stream), "pack"))) return st;
+  if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream), "orth"))) return st;
+
+  const int rounds = T + refine_rounds;
+  const int64_t zs = int64_t(d) * K;
+  for (int t = 0; t < rounds; ++t) {
+    const int p = t < T ? p_schedule[t] : 1;
+    for (int j = 0; j < p; ++j) {
+      if (j > 0 && (st = check_launch(c, lp::launch_cholqr2(c->dYl, c->dZl, m, d, k, K, c->dStatus, c->stream),
+                                      "local orth")))
+        return st;
+      if ((st = launch_step(c, K, j == 0 ? c->dZ : c->dZl, j == 0 ? 0 : zs, timing))) return st;
+      if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream),
+                             "reduce")))
+        return st;
+      c->stats.local_steps++;
+    }
+    const bool align = p > 1 && agg != LP_AGG_IDENTITY;
+    if (align) {
+      // The last basis each partition multiplied this round is Z_i (orth of its previous Y_i).
+      if ((st = check_launch(c, lp::launch_align(c->dZl, zs, c->dZl + zs * c->base, m, d, k, K, c->base, agg, c->dG,
+                                                 c->dStatus, c->stream),
+                             "align")))
+        return st;
+    }
+    if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, align ? c->dG : nullptr, agg == LP_AGG_SIGN ? 1 : 0,
+                                                   m, d, K, c->dY, c->stream),
+                           "aggregate")))
+      return st;
+    if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream), "orth")))
+      return st;
+    c->stats.rounds++;
+  }
+  if (c->ritz) {
+    if ((st = launch_step(c, K, c->dZ, 0, timing))) return st;
+    if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream), "reduce")))
+      return st;
+    if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, nullptr, 0, m, d, K, c->dMZ, c->stream),
+                           "aggregate")))
+      return st;
+    if ((st = check_launch(c, lp::launch_ritz(c->dZ, c->dMZ, d, k, K, double(c->n), c->dZout, c->dSigma, c->dStatus,
+                                              c->stream),
+                           "ritz")))
+      return st;
+  } else {
+    if ((st = check_launch(c, lp::launch_unpack(c->dZ, c->dZout, 1, d, k, K, c->stream), "unpack"))) return st;
+  }
+  return LP_OK;
+}
+
 lp_status lp_set_tuning(lp_ctx* c, const lp_tuning* t) {
   if (!c) return LP_ERR_INVALID;
   c->err.clear();
@@ -645,6 +773,7 @@ lp_status lp_set_tuning(lp_ctx* c, const lp_tuning* t) {
   }
   c->tuning = nt;
   c->prefer_resident = false;
+  drop_graph(c);
   // plans are rebuilt on the next solve; the segment table is kept (same cluster count or rebuilt then)
   c->tcs_state[0] = c->tcs_state[1] = c->tcs_state[2] = 0;
   c->tcs_cur = nullptr;
@@ -711,6 +840,7 @@ lp_status lp_autotune(lp_ctx* c, int k, lp_tuning* chosen, int* path_out, double
   }
   c->tuning = win.t;
   c->prefer_resident = win.resident;
+  drop_graph(c);
   c->tcs_state[0] = c->tcs_state[1] = c->tcs_state[2] = 0;
   c->solved = false;  // the timing launches overwrote the solve buffers
   if (st) return st;
@@ -744,71 +874,58 @@ lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator
   if ((st = select_path(c, k, flags))) return st;
   if ((st = ensure_state(c, K))) return st;
 
-  const int d = static_cast<int>(c->d);
-  const int m = c->m;
   const bool timing = (flags & LP_FLAG_TIMING) != 0;
   c->solved = false;
   c->k = k;
   c->ritz = (flags & LP_FLAG_RITZ) != 0;
-  std::memset(&c->stats, 0, sizeof(c->stats));
-  c->step_ev_used = 0;
 
-  LP_CUDA(cudaMemsetAsync(c->dStatus, 0, 4, c->stream));
   LP_CUDA(cudaEventRecord(c->ev0, c->stream));
   const double* dy0;
-  if ((st = stage_in(c, y0, size_t(d) * k, LP_HOST, &dy0))) return st;
-  if ((st = check_launch(c, lp::launch_pack(dy0, c->dY, 1, d, k, K, c->stream), "pack"))) return st;
-  if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream), "orth"))) return st;
-
-  const int rounds = T + refine_rounds;
-  const int64_t zs = int64_t(d) * K;
-  for (int t = 0; t < rounds; ++t) {
-    const int p = t < T ? p_schedule[t] : 1;
-    for (int j = 0; j < p; ++j) {
-      if (j > 0 && (st = check_launch(c, lp::launch_cholqr2(c->dYl, c->dZl, m, d, k, K, c->dStatus, c->stream),
-                                      "local orth")))
-        return st;
-      if ((st = launch_step(c, K, j == 0 ? c->dZ : c->dZl, j == 0 ? 0 : zs, timing))) return st;
-      if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream),
-                             "reduce")))
-        return st;
-      c->stats.local_steps++;
-    }
-    const bool align = p > 1 && agg != LP_AGG_IDENTITY;
-    if (align) {
-      // The last basis each partition multiplied this round is Z_i (orth of its previous Y_i).
-      if ((st = check_launch(c, lp::launch_align(c->dZl, zs, c->dZl + zs * c->base, m, d, k, K, c->base, agg, c->dG,
-                                                 c->dStatus, c->stream),
-                             "align")))
-        return st;
-    }
-    if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, align ? c->dG : nullptr, agg == LP_AGG_SIGN ? 1 : 0,
-                                                   m, d, K, c->dY, c->stream),
-                           "aggregate")))
-      return st;
-    if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream), "orth")))
-      return st;
-    c->stats.rounds++;
-  }
-  if (c->ritz) {
-    if ((st = launch_step(c, K, c->dZ, 0, timing))) return st;
-    if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream), "reduce")))
-      return st;
-    if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, nullptr, 0, m, d, K, c->dMZ, c->stream),
-                           "aggregate")))
-      return st;
-    if ((st = check_launch(c, lp::launch_ritz(c->dZ, c->dMZ, d, k, K, double(c->n), c->dZout, c->dSigma, c->dStatus,
-                                              c->stream),
-                           "ritz")))
-      return st;
+  if ((st = stage_in(c, y0, size_t(c->d) * k, LP_HOST, &dy0))) return st;
+  // The launch sequence depends only on these; a matching key replays the captured graph.
+  std::vector<int64_t> key = {int64_t(c->gen), k, T, int64_t(agg), refine_rounds, int64_t(flags), c->path};
+  key.insert(key.end(), p_schedule, p_schedule + T);
+  const bool use_graph = (flags & LP_FLAG_NO_GRAPH) == 0;
+  if (use_graph && c->graph_exec && key == c->graph_key) {
+    LP_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
+    c->stats = c->graph_stats;
+    c->step_ev_used = c->graph_step_ev_used;
   } else {
-    if ((st = check_launch(c, lp::launch_unpack(c->dZ, c->dZout, 1, d, k, K, c->stream), "unpack"))) return st;
+    if (use_graph) {
+      drop_graph(c);
+      key[0] = int64_t(c->gen);
+      LP_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+    }
+    std::memset(&c->stats, 0, sizeof(c->stats));
+    c->step_ev_used = 0;
+    st = solve_body(c, k, p_schedule, T, agg, refine_rounds, timing, dy0);
+    if (use_graph) {
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+      if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "capturing the solve");
+      const cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess) {
+        c->graph_exec = nullptr;
+        return cuda_fail(c, ei, "instantiating the solve graph");
+      }
+      c->graph_key = key;
+      c->graph_stats = c->stats;
+      c->graph_step_ev_used = c->step_ev_used;
+      LP_CUDA(cudaGraphLaunch(c->graph_exec, c->stream));
+    } else if (st) {
+      return st;
+    }
   }
   LP_CUDA(cudaEventRecord(c->ev1, c->stream));
   c->stats.k = k;
   c->stats.n = c->n;
   c->stats.d = c->d;
-  c->stats.m = m;
+  c->stats.m = c->m;
   c->stats.path = c->path;
   c->solved = true;
   return LP_OK;

@@ -90,6 +90,16 @@ cudaError_t launch_step_tcs(const TcsPlan& p, const Segment* segs, const int* se
 cudaError_t launch_split_planes(const float* src, int64_t src_ld, int64_t rows, int d, uint16_t* hi, uint16_t* lo,
                                 int64_t ld, cudaStream_t s);
 
+// ---- context internals used by the request server ---------------------------
+// lp_load_partitions with a row pitch (elements) for the partitions' source rows.
+lp_status load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int64_t pitch, lp_dtype dtype,
+                       const void* const* parts, const float* const* row_scales, lp_ptr_space space);
+// Device bytes a context needs to load these partitions and solve at rank k.
+size_t estimate_bytes(int sms, int m, const int64_t* rows, int64_t d, int64_t pitch, lp_dtype dtype, int k,
+                      lp_ptr_space space);
+// 1: the last lp_solve finished on the device; 0: still running; -1: no solve or a CUDA error.
+int solve_state(lp_ctx* c);
+
 // Message returned by lp_last_error(NULL) (failures of calls without a context).
 void set_no_context_error(const char* msg);
 inline void set_no_context_error(const std::string& msg) { set_no_context_error(msg.c_str()); }

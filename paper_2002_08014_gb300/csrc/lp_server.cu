@@ -1,0 +1,268 @@
+// Request server: continuous batching of independent LocalPower solves.
+//
+// A request is one truncated-SVD problem (its partitions and its schedule).
+// Requests wait in arrival order; lp_server_progress admits the head of the
+// queue while the sum of the admitted requests' device-memory estimates stays
+// within the budget and fewer than max_active are on the device.  An admitted
+// request gets its own context (own stream, own device buffers): its partitions
+// are copied in and its whole solve is enqueued at once, so A_i and the
+// iterates stay resident across its rounds and the GPU interleaves its kernels
+// with those of every other admitted request.  Completion is detected with the
+// event the solve records last; the results move to host memory and the
+// context is destroyed, which returns its budget share to the queue.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <deque>
+#include <new>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "lp_internal.cuh"
+
+namespace {
+
+struct Request {
+  int64_t id = 0;
+  // copies of the request's small arrays
+  int m = 0;
+  int64_t d = 0, pitch = 0;
+  lp_dtype dtype = LP_F32;
+  lp_ptr_space space = LP_HOST;
+  std::vector<int64_t> rows;
+  std::vector<const void*> parts;
+  std::vector<const float*> scales;
+  int k = 0, refine = 0, T = 0;
+  lp_aggregator agg = LP_AGG_SIGN;
+  unsigned flags = 0;
+  std::vector<int> sched;
+  std::vector<double> y0;
+  size_t est = 0;
+  // device side while active
+  lp_ctx* ctx = nullptr;
+  // results
+  bool done = false;
+  lp_status status = LP_OK;
+  std::string err;
+  std::vector<double> z, sigma;
+  lp_stats stats{};
+};
+
+}  // namespace
+
+struct lp_server {
+  int device = 0;
+  int sms = 0;
+  size_t budget = 0;
+  int max_active = 1;
+  size_t in_use = 0, peak = 0;
+  int64_t next_id = 1;
+  std::deque<Request*> queue;
+  std::vector<Request*> active;
+  std::vector<int64_t> finished;  // completed since the last progress call
+  std::unordered_map<int64_t, std::unique_ptr<Request>> all;
+  std::string err;
+};
+
+namespace {
+
+lp_status sfail(lp_server* s, lp_status st, const std::string& msg) {
+  s->err = msg;
+  return st;
+}
+
+void finish(lp_server* s, Request* r, lp_status st, const std::string& msg) {
+  r->status = st;
+  r->err = msg;
+  r->done = true;
+  s->finished.push_back(r->id);
+}
+
+void release(lp_server* s, Request* r) {
+  if (r->ctx) {
+    lp_destroy(r->ctx);
+    r->ctx = nullptr;
+    s->in_use -= r->est;
+  }
+}
+
+// Copies the partitions in and enqueues the solve; failures complete the request.
+void admit(lp_server* s, Request* r) {
+  lp_ctx* c = nullptr;
+  lp_status st = lp_create(&c, s->device, r->est, nullptr);
+  if (st) {
+    finish(s, r, st, lp_last_error(nullptr));
+    return;
+  }
+  r->ctx = c;
+  s->in_use += r->est;
+  s->peak = std::max(s->peak, s->in_use);
+  st = lp::load_pitched(c, r->m, r->rows.data(), r->d, r->pitch, r->dtype, r->parts.data(),
+                        r->dtype == LP_FP8_E4M3 ? r->scales.data() : nullptr, r->space);
+  if (!st)
+    st = lp_solve(c, r->k, r->sched.empty() ? nullptr : r->sched.data(), r->T, r->agg, r->y0.data(), r->refine,
+                  r->flags);
+  if (st) {
+    const std::string msg = lp_last_error(c);
+    release(s, r);
+    finish(s, r, st, msg);
+    return;
+  }
+  s->active.push_back(r);
+}
+
+}  // namespace
+
+extern "C" {
+
+lp_status lp_server_create(lp_server** out, int device, size_t hbm_budget_bytes, int max_active) {
+  if (!out) return LP_ERR_INVALID;
+  *out = nullptr;
+  if (max_active < 1) return LP_ERR_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    (void)cudaGetLastError();
+    return ndev == 0 ? LP_ERR_CUDA : LP_ERR_INVALID;
+  }
+  lp_server* s = new (std::nothrow) lp_server();
+  if (!s) return LP_ERR_OOM;
+  s->device = device;
+  s->budget = hbm_budget_bytes;
+  s->max_active = max_active;
+  if (cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    delete s;
+    return LP_ERR_CUDA;
+  }
+  *out = s;
+  return LP_OK;
+}
+
+lp_status lp_server_submit(lp_server* s, const lp_request* q, int64_t* id) {
+  if (!s) return LP_ERR_INVALID;
+  s->err.clear();
+  if (!q || !id) return sfail(s, LP_ERR_INVALID, "request and id must be non-NULL");
+  *id = 0;
+  if (q->m < 1 || !q->rows || !q->parts || q->d < 1 || q->k < 1 || q->k > LP_MAX_K || q->k > q->d || !q->y0 ||
+      q->T < 0 || q->refine_rounds < 0 || q->T + q->refine_rounds < 1 || (q->T > 0 && !q->p_schedule))
+    return sfail(s, LP_ERR_INVALID, "malformed request");
+  if (q->row_pitch != 0 && q->row_pitch < q->d) return sfail(s, LP_ERR_INVALID, "row_pitch below d");
+  if (q->dtype == LP_FP8_E4M3 && !q->row_scales) return sfail(s, LP_ERR_INVALID, "FP8 request needs row_scales");
+  for (int i = 0; i < q->m; ++i) {
+    if (q->rows[i] < q->k) return sfail(s, LP_ERR_INVALID, "k exceeds a partition's row count");
+    if (!q->parts[i]) return sfail(s, LP_ERR_INVALID, "NULL partition pointer");
+  }
+  for (int t = 0; t < q->T; ++t)
+    if (q->p_schedule[t] < 1) return sfail(s, LP_ERR_INVALID, "p_schedule entries must be >= 1");
+  auto r = std::make_unique<Request>();
+  r->m = q->m;
+  r->d = q->d;
+  r->pitch = q->row_pitch ? q->row_pitch : q->d;
+  r->dtype = q->dtype;
+  r->space = q->space;
+  r->rows.assign(q->rows, q->rows + q->m);
+  r->parts.assign(q->parts, q->parts + q->m);
+  if (q->dtype == LP_FP8_E4M3) r->scales.assign(q->row_scales, q->row_scales + q->m);
+  r->k = q->k;
+  r->T = q->T;
+  r->refine = q->refine_rounds;
+  r->agg = q->agg;
+  r->flags = q->flags;
+  if (q->T > 0) r->sched.assign(q->p_schedule, q->p_schedule + q->T);
+  r->y0.assign(q->y0, q->y0 + size_t(q->d) * q->k);
+  r->est = lp::estimate_bytes(s->sms, r->m, r->rows.data(), r->d, r->pitch, r->dtype, r->k, r->space);
+  if (s->budget && r->est > s->budget)
+    return sfail(s, LP_ERR_OOM, "request needs about " + std::to_string(r->est) + " bytes, over the server budget");
+  r->id = s->next_id++;
+  *id = r->id;
+  s->queue.push_back(r.get());
+  s->all.emplace(r->id, std::move(r));
+  return LP_OK;
+}
+
+lp_status lp_server_progress(lp_server* s, int64_t* done_ids, int cap, int* n_done) {
+  if (!s) return LP_ERR_INVALID;
+  s->err.clear();
+  if (n_done) *n_done = 0;
+  if (cudaSetDevice(s->device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return sfail(s, LP_ERR_CUDA, "cudaSetDevice failed");
+  }
+  // retire
+  for (size_t i = 0; i < s->active.size();) {
+    Request* r = s->active[i];
+    const int state = lp::solve_state(r->ctx);
+    if (state == 0) {
+      ++i;
+      continue;
+    }
+    r->z.assign(size_t(r->d) * r->k, 0.0);
+    r->sigma.assign(size_t(r->k), 0.0);
+    const lp_status st = lp_result(r->ctx, r->z.data(), r->sigma.data(), &r->stats);
+    const std::string msg = st ? lp_last_error(r->ctx) : "";
+    release(s, r);
+    finish(s, r, st, msg);
+    s->active[i] = s->active.back();
+    s->active.pop_back();
+  }
+  // admit in arrival order
+  while (!s->queue.empty() && static_cast<int>(s->active.size()) < s->max_active) {
+    Request* r = s->queue.front();
+    if (s->budget && s->in_use + r->est > s->budget) break;
+    s->queue.pop_front();
+    admit(s, r);
+  }
+  // report
+  int n = 0;
+  while (n < cap && !s->finished.empty()) {
+    if (done_ids) done_ids[n] = s->finished.front();
+    s->finished.erase(s->finished.begin());
+    ++n;
+  }
+  if (n_done) *n_done = n;
+  return LP_OK;
+}
+
+lp_status lp_server_result(lp_server* s, int64_t id, double* z_out, double* sigma_out, lp_stats* stats) {
+  if (!s) return LP_ERR_INVALID;
+  s->err.clear();
+  auto it = s->all.find(id);
+  if (it == s->all.end() || !it->second->done) return sfail(s, LP_ERR_STATE, "request unknown or not complete");
+  Request* r = it->second.get();
+  const lp_status st = r->status;
+  s->err = r->err;
+  if (!st) {
+    if (z_out) std::copy(r->z.begin(), r->z.end(), z_out);
+    if (sigma_out) std::copy(r->sigma.begin(), r->sigma.end(), sigma_out);
+  }
+  if (stats) *stats = r->stats;
+  s->finished.erase(std::remove(s->finished.begin(), s->finished.end(), id), s->finished.end());
+  s->all.erase(it);
+  return st;
+}
+
+lp_status lp_server_query(lp_server* s, lp_server_info* info) {
+  if (!s || !info) return LP_ERR_INVALID;
+  int64_t completed = 0;
+  for (const auto& kv : s->all) completed += kv.second->done ? 1 : 0;
+  info->queued = static_cast<int64_t>(s->queue.size());
+  info->active = static_cast<int64_t>(s->active.size());
+  info->completed = completed;
+  info->hbm_in_use = s->in_use;
+  info->hbm_peak = s->peak;
+  info->hbm_budget = s->budget;
+  return LP_OK;
+}
+
+const char* lp_server_error(const lp_server* s) { return s ? s->err.c_str() : ""; }
+
+void lp_server_destroy(lp_server* s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  for (Request* r : s->active) release(s, r);  // lp_destroy synchronises the request's stream
+  delete s;
+}
+
+}  // extern "C"

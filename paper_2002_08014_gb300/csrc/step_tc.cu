@@ -55,15 +55,18 @@ struct TcLayout {
   static constexpr int B2 = 2 * N * 128;
   static constexpr int NB2BUF = K == 32 ? 1 : 2;  // W operand buffers (one at K = 32 to fit shared memory)
   static constexpr int NB2 = NCH / 2;
-  static constexpr int KS = K + 4;                  // W row stride in floats: 16-byte rows, odd in 16-byte units
-  static constexpr int WBYTES = kBM * KS * 4;
+  // Cluster sum of the row products: all-gather (one shared-memory trip) for
+  // K <= 16 and clusters of up to 4 CTAs, else reduce-scatter + broadcast.
+  static constexpr bool AG = K <= 16;
+  static constexpr int WBYTES = kBM * K * 4;                    // one 128 x K FP32 block (wpos layout)
+  static constexpr int RECV = AG ? 2 * 3 * WBYTES : WBYTES;      // AG: 2 parities x 3 peers
   static constexpr int off_A = 0;
   static constexpr int off_B1 = off_A + 2 * STAGE;
   static constexpr int off_B2 = off_B1 + B1;
-  static constexpr int off_W = off_B2 + NB2BUF * B2;   // partial W rows, then the cluster sum in place
-  static constexpr int off_Wrecv = off_W + WBYTES;      // partials received for the rows this CTA owns
-  static constexpr int off_bar = off_Wrecv + WBYTES;
-  static constexpr int kBars = 16;
+  static constexpr int off_W = off_B2 + NB2BUF * B2;   // this CTA's partial rows (RS: then the owned sums)
+  static constexpr int off_Wrecv = off_W + WBYTES;      // peers' partials
+  static constexpr int off_bar = off_Wrecv + RECV;
+  static constexpr int kBars = 18;
   static constexpr int bytes = off_bar + kBars * 8 + 16;
   static constexpr int alloc_bytes = bytes + 1024;  // room to align the base to 1024
   static constexpr uint32_t tmem_used = 2 * N + NB2 * N;
@@ -72,7 +75,7 @@ struct TcLayout {
 };
 
 enum BarId { B_FULL0 = 0, B_EMPTY0 = 2, B_D1FULL0 = 4, B_D1EMPTY0 = 6, B_B2FULL0 = 8, B_B2FREE0 = 10, B_D2FULL = 12,
-             B_REDFULL = 13, B_WFULL = 14, B_DONE = 15 };
+             B_REDFULL = 13, B_WFULL = 14, B_DONE = 15, B_RED1 = 16, B_EPI = 17 };
 
 template <int K, int NCH>
 __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcArgs a) {
@@ -108,6 +111,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
     }
     mbar_init(&bar[B_D2FULL], 1);
     mbar_init(&bar[B_REDFULL], 1);  // local expect_tx + bytes of the peers' partial rows
+    mbar_init(&bar[B_RED1], 1);     // all-gather, odd tiles
+    mbar_init(&bar[B_EPI], 128);    // barrier of the four epilogue warps (bounded waits)
     mbar_init(&bar[B_WFULL], 1);    // local expect_tx + bytes of the owners' summed rows
     mbar_init(&bar[B_DONE], 1);
     *abort_flag = 0;
@@ -144,6 +149,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
 
   const int sb = a.seg_ptr[cluster_id], se = a.seg_ptr[cluster_id + 1];
   uint32_t T = 0;  // tiles processed so far (identical in every CTA of the cluster)
+  uint32_t epi_phase = 0;  // uses of the epilogue barrier so far (epilogue threads)
   for (int si = sb; si < se; ++si) {
     const Segment sg = a.segs[si];
     const int ntiles = static_cast<int>((sg.row1 - sg.row0 + kBM - 1) / kBM);
@@ -245,6 +251,12 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
       const int r = (warp - 4) * 32 + lane;
       const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
       bool ok = true;
+      // Barrier of the 128 epilogue threads on an mbarrier with a bounded wait
+      // (a named barrier could hang if some threads left the loop on an abort).
+      auto epi_sync = [&]() -> bool {
+        mbar_arrive(&bar[B_EPI]);
+        return wait(B_EPI, (epi_phase++) & 1, false);
+      };
       for (int t = 0; ok && t < ntiles; ++t) {
         const uint32_t Tg = T + t, b = Tg & 1;
         if (!(ok = wait(B_D1FULL0 + b, (Tg >> 1) & 1, false))) break;
@@ -269,24 +281,67 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
 #pragma unroll
           for (int j = 0; j < K; ++j) w[j] = 0.f;
         }
-        if (CL > 1) {
-          // Cluster sum of W.  Owner o holds rows [o*RPC, (o+1)*RPC).  Every CTA
-          // writes its partial rows to sW and one thread ships each owner its
-          // rows (bulk DSMEM copies, counted in bytes on the owner's barrier);
-          // owners add the partials in source-rank order, in place in sW, and
-          // ship the sums back the same way.  Peers' data land only in rows
-          // whose earlier contents were already consumed (see the waits).
-          const uint32_t rows_bytes = static_cast<uint32_t>(RPC * L::KS * 4);
-          float* wr = sW + r * L::KS;
+        if (CL > 1 && L::AG && CL <= 4) {
+          // All-gather: every CTA ships its 128 partial rows to each peer (bulk
+          // copies counted in bytes on the peer's barrier for this tile's
+          // parity) and then sums all CL partials of its own rows in source-rank
+          // order.  A peer can refill a parity's slots only after this CTA has
+          // sent its next tile, i.e. after it finished reading them.
+          const uint32_t par = Tg & 1;
+          const int rb = par ? B_RED1 : B_REDFULL;
+          const uint32_t blk = static_cast<uint32_t>(L::WBYTES);
+          if (!(ok = epi_sync())) break;  // the previous tile's bulk copies have read sW (r == 0 waited)
 #pragma unroll
-          for (int j = 0; j < K; j += 4) *reinterpret_cast<float4*>(wr + j) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+          for (int j = 0; j < K; j += 4)
+            *reinterpret_cast<float4*>(sW + wpos<K>(r, j)) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
           fence_async_smem();
-          epi_bar();
+          if (!(ok = epi_sync())) break;
+          if (r == 0) {
+            mbar_expect_tx(&bar[rb], (CL - 1) * blk);
+            for (uint32_t o = 0; o < CL; ++o)
+              if (o != crank) {
+                const uint32_t slot = par * 3 + (crank < o ? crank : crank - 1);  // this CTA's slot at peer o
+                bulk_s2s_cluster(mapa(su32(sWrecv + slot * kBM * K), o), su32(sW), blk, mapa(su32(&bar[rb]), o));
+              }
+            bulk_commit();
+            bulk_wait_read0();
+          }
+          if (!(ok = wait(rb, (Tg >> 1) & 1, true))) break;
+          float acc[K];
+#pragma unroll
+          for (int j = 0; j < K; ++j) acc[j] = 0.f;
+          for (uint32_t src = 0; src < CL; ++src) {
+            const float* pb = src == crank ? sW : sWrecv + (par * 3 + (src < crank ? src : src - 1)) * kBM * K;
+#pragma unroll
+            for (int j = 0; j < K; j += 4) {
+              const float4 v = *reinterpret_cast<const float4*>(pb + wpos<K>(r, j));
+              acc[j] += v.x;
+              acc[j + 1] += v.y;
+              acc[j + 2] += v.z;
+              acc[j + 3] += v.w;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < K; ++j) w[j] = acc[j];
+        } else if (CL > 1) {
+          // Reduce-scatter + broadcast.  Owner o holds rows [o*RPC, (o+1)*RPC).
+          // Every CTA writes its partial rows to sW and one thread ships each
+          // owner its rows (bulk copies counted in bytes on the owner's
+          // barrier); owners add the partials in source-rank order, in place,
+          // and ship the sums back the same way.  Peers' data land only in rows
+          // whose earlier contents were already consumed (see the waits).
+          const uint32_t rows_bytes = static_cast<uint32_t>(RPC * K * 4);
+          if (!(ok = epi_sync())) break;  // the previous tile's bulk copies have read sW (r == 0 waited)
+#pragma unroll
+          for (int j = 0; j < K; j += 4)
+            *reinterpret_cast<float4*>(sW + wpos<K>(r, j)) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+          fence_async_smem();
+          if (!(ok = epi_sync())) break;
           if (r == 0) {
             mbar_expect_tx(&bar[B_REDFULL], (CL - 1) * rows_bytes);
             for (uint32_t o = 0; o < CL; ++o)
               if (o != crank)
-                bulk_s2s_cluster(mapa(su32(sWrecv + crank * RPC * L::KS), o), su32(sW + o * RPC * L::KS), rows_bytes,
+                bulk_s2s_cluster(mapa(su32(sWrecv + crank * RPC * K), o), su32(sW + o * RPC * K), rows_bytes,
                                  mapa(su32(&bar[B_REDFULL]), o));
             bulk_commit();
             bulk_wait_read0();
@@ -295,27 +350,31 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
           const int per = RPC * K / kBM;  // values per epilogue thread (K / CL)
           for (int e = 0; e < per; ++e) {
             const int idx = r * per + e, rl = idx / K, col = idx % K;
-            float s = 0.f;
-            for (uint32_t src = 0; src < CL; ++src)
-              s += src == crank ? sW[(crank * RPC + rl) * L::KS + col] : sWrecv[(src * RPC + rl) * L::KS + col];
-            sW[(crank * RPC + rl) * L::KS + col] = s;
+            const int own = wpos<K>(static_cast<int>(crank) * RPC + rl, col);
+            const int rel = own - static_cast<int>(crank) * RPC * K;  // offset inside one owner's row block
+            float sum = 0.f;
+            for (uint32_t src = 0; src < CL; ++src) sum += src == crank ? sW[own] : sWrecv[src * RPC * K + rel];
+            sW[own] = sum;
           }
           fence_async_smem();
-          epi_bar();
+          if (!(ok = epi_sync())) break;
           if (r == 0) {
             mbar_expect_tx(&bar[B_WFULL], (CL - 1) * rows_bytes);
             for (uint32_t dsti = 0; dsti < CL; ++dsti)
               if (dsti != crank)
-                bulk_s2s_cluster(mapa(su32(sW + crank * RPC * L::KS), dsti), su32(sW + crank * RPC * L::KS),
-                                 rows_bytes, mapa(su32(&bar[B_WFULL]), dsti));
+                bulk_s2s_cluster(mapa(su32(sW + crank * RPC * K), dsti), su32(sW + crank * RPC * K), rows_bytes,
+                                 mapa(su32(&bar[B_WFULL]), dsti));
             bulk_commit();
             bulk_wait_read0();
           }
           if (!(ok = wait(B_WFULL, Tg & 1, true))) break;
 #pragma unroll
           for (int j = 0; j < K; j += 4) {
-            const float4 v = *reinterpret_cast<const float4*>(wr + j);
-            w[j] = v.x; w[j + 1] = v.y; w[j + 2] = v.z; w[j + 3] = v.w;
+            const float4 v = *reinterpret_cast<const float4*>(sW + wpos<K>(r, j));
+            w[j] = v.x;
+            w[j + 1] = v.y;
+            w[j + 2] = v.z;
+            w[j + 3] = v.w;
           }
         }
         // [W_hi | W_lo]^T into B2: row n = output column, k-index = tile row r

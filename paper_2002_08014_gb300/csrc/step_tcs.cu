@@ -38,7 +38,7 @@ constexpr int kMaxRing = 8;
 constexpr int kSmemLimit = 232448;
 
 enum TcsBar { S_D1FULL0 = 0, S_D1EMPTY0 = 2, S_B2FULL0 = 4, S_B2FREE0 = 6, S_D2FULL = 8, S_REDFULL = 9,
-              S_WFULL = 10, S_DONE = 11, S_RING0 = 12 };  // ring: FULL[s] = S_RING0 + s, EMPTY[s] = S_RING0 + ring + s
+              S_WFULL = 10, S_DONE = 11, S_EPI = 12, S_RING0 = 13 };  // ring: FULL[s] = S_RING0 + s, EMPTY[s] = S_RING0 + ring + s
 
 struct TcsArgs {
   const Segment* segs;
@@ -56,15 +56,6 @@ struct TcsArgs {
   uint32_t off_B1, off_B2, off_W, off_Wrecv, off_bar, tmem_cols;
 };
 
-// Position (in floats) of the 4-float group holding column j of row r in a
-// row-major 128 x K FP32 buffer; groups are XOR-permuted so that a warp's
-// float4 row writes touch distinct banks.
-template <int K>
-__device__ __forceinline__ int wpos(int r, int j) {
-  constexpr int rows_per_128b = 32 / K;
-  constexpr int groups = K / 4;
-  return r * K + ((((j >> 2) ^ ((r / rows_per_128b) % groups))) << 2) + (j & 3);
-}
 
 // Walks the load/consume order of one segment: first pass of tile t (units
 // 0..U-1) interleaved with the second pass of tile t-1, `lag` units behind.
@@ -118,6 +109,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(&bar[S_REDFULL], 1);
     mbar_init(&bar[S_WFULL], 1);
     mbar_init(&bar[S_DONE], 1);
+    mbar_init(&bar[S_EPI], 128);  // barrier of the four epilogue warps (bounded waits)
     for (int s = 0; s < R; ++s) {
       mbar_init(&bar[S_RING0 + s], 1);
       mbar_init(&bar[S_RING0 + R + s], 1);
@@ -159,6 +151,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int sb = a.seg_ptr[cluster_id], se = a.seg_ptr[cluster_id + 1];
   uint32_t T = 0;  // tiles before this segment (same in every CTA of the cluster)
+  uint32_t epi_phase = 0;  // uses of the epilogue barrier so far (epilogue threads)
   uint32_t G = 0;  // ring units before this segment
   for (int si = sb; si < se; ++si) {
     const Segment sg = a.segs[si];
@@ -274,6 +267,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int r = (warp - 4) * 32 + lane;
       const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
       bool ok = true;
+      // Barrier of the 128 epilogue threads on an mbarrier with a bounded wait
+      // (a named barrier could hang if some threads left the loop on an abort).
+      auto epi_sync = [&]() -> bool {
+        mbar_arrive(&bar[S_EPI]);
+        return wait(S_EPI, (epi_phase++) & 1, false);
+      };
       for (int t = 0; ok && t < ntiles; ++t) {
         const uint32_t Tg = T + t, buf = Tg & 1;
         if (!(ok = wait(S_D1FULL0 + buf, (Tg >> 1) & 1, false))) break;
@@ -306,11 +305,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           // back the same way.  A buffer is rewritten only after the waits show
           // its previous contents were consumed.
           const uint32_t rows_bytes = static_cast<uint32_t>(RPC * K * 4);
+          if (!(ok = epi_sync())) break;  // the previous tile's bulk copies have read sW (r == 0 waited)
 #pragma unroll
           for (int j = 0; j < K; j += 4)
             *reinterpret_cast<float4*>(sW + wpos<K>(r, j)) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
           fence_async_smem();
-          epi_bar();
+          if (!(ok = epi_sync())) break;
           if (r == 0) {
             mbar_expect_tx(&bar[S_REDFULL], (CL - 1) * rows_bytes);
             for (uint32_t o = 0; o < CL; ++o)
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             sW[own] = sum;
           }
           fence_async_smem();
-          epi_bar();
+          if (!(ok = epi_sync())) break;
           if (r == 0) {
             mbar_expect_tx(&bar[S_WFULL], (CL - 1) * rows_bytes);
             for (uint32_t dst = 0; dst < CL; ++dst)
@@ -491,7 +491,7 @@ bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan*
   const uint32_t B2 = 2u * (2u * N * 128);
   const uint32_t W = cl > 1 ? 128u * K * 4 : 0u;
   const int fixed_no_bars = static_cast<int>(B1 + B2 + 2 * W);
-  int ring = (kSmemLimit - 1024 - fixed_no_bars - (12 + 2 * kMaxRing) * 8 - 16) / kUnitBytes;
+  int ring = (kSmemLimit - 1024 - fixed_no_bars - (S_RING0 + 2 * kMaxRing) * 8 - 16) / kUnitBytes;
   if (ring > kMaxRing) ring = kMaxRing;
   if (ring_cap > 0 && ring > ring_cap) ring = ring_cap;
   if (ring < 2) return false;
@@ -510,7 +510,7 @@ bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan*
   p->off_W = p->off_B2 + B2;
   p->off_Wrecv = p->off_W + W;
   p->off_bar = p->off_Wrecv + W;
-  p->smem = p->off_bar + (12 + 2 * ring) * 8 + 16 + 1024;
+  p->smem = p->off_bar + (S_RING0 + 2 * ring) * 8 + 16 + 1024;
   const uint32_t used = static_cast<uint32_t>(2 * N + (ncd / 2) * N);
   uint32_t cols = 32;
   while (cols < used) cols *= 2;

@@ -77,8 +77,6 @@ __device__ __forceinline__ void bulk_s2s_cluster(uint32_t dst, uint32_t src, uin
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// Named barrier of the four epilogue warps.
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -145,6 +143,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Position (in floats) of the 4-float group holding column j of row r in a
+// row-major 128 x K FP32 buffer; groups are XOR-permuted so that a warp's
+// float4 row writes touch distinct banks.
+template <int K>
+__device__ __forceinline__ int wpos(int r, int j) {
+  constexpr int rows_per_128b = 32 / K;
+  constexpr int groups = K / 4;
+  return r * K + ((((j >> 2) ^ ((r / rows_per_128b) % groups))) << 2) + (j & 3);
 }
 
 // Shared-memory matrix descriptor, SWIZZLE_128B, tcgen05 format (version field = 1).

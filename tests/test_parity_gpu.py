@@ -402,3 +402,30 @@ def test_autotune_picks_a_working_kernel(gpu_lib, dtype):
         assert choice["path_code"] in (TC_RESIDENT, TC_STREAM) and choice["ms_per_step"] > 0
     ref = O.localpower(exact, 12, [3, 1], "opt", Y0)
     assert O.subspace_dist(Z, ref["Z"]) < (1e-6 if dtype == "f32" else TC_SOLVE_TOL)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_graph_replay_matches_eager_launches(gpu_lib, dtype):
+    """The solve's captured CUDA graph replays exactly the eager launch sequence;
+    a changed schedule or aggregator is captured anew."""
+    sizes = [700, 900, 650]
+    stored, exact, _ = _parts(sizes, 160, 51, dtype)
+    Y0 = synth.gaussian_start(160, 8, 52)
+    with B.LocalPower(stored, dtype=dtype) as lp:
+        runs = []
+        for sched, agg in [([3, 2, 1], "sign"), ([3, 2, 1], "sign"), ([2, 2], "opt"), ([3, 2, 1], "sign")]:
+            for flags in (B.LP_FLAG_RITZ | B.LP_FLAG_NO_GRAPH, B.LP_FLAG_RITZ, B.LP_FLAG_RITZ | B.LP_FLAG_TIMING):
+                B.lp_solve(lp.ctx, 8, sched, agg, Y0, 1, flags)
+                Z, sig, st = lp.result(8)
+                if flags & B.LP_FLAG_TIMING:   # step events recorded inside the graph
+                    assert st["ms_step_kernels"] > 0
+                runs.append((sched, agg, Z, sig, st))
+    for i in range(0, len(runs), 3):
+        eager, first, replay = runs[i:i + 3]
+        for other in (first, replay):
+            assert np.array_equal(eager[2], other[2]) and np.array_equal(eager[3], other[3])
+            assert other[4]["kernel_launches"] == eager[4]["kernel_launches"]
+            assert other[4]["local_steps"] == eager[4]["local_steps"]
+    for sched, agg, Z, _, _ in runs[:3] + runs[6:9]:
+        ref = O.localpower(exact, 8, list(sched) + [1], agg, Y0)
+        assert O.subspace_dist(Z, ref["Z"]) < (1e-6 if dtype == "f32" else TC_SOLVE_TOL)
