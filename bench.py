@@ -49,12 +49,15 @@ def _args():
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--shape", default="1024x16", help="kernels: d x k of the step-kernel comparison")
-    ap.add_argument("--workload", choices=["fp32", "lowprec", "plain", "serving", "kernels"], default="fp32",
+    ap.add_argument("--instances", type=int, default=256, help="batching: number of instances")
+    ap.add_argument("--workload", choices=["fp32", "lowprec", "plain", "serving", "kernels", "batching"],
+                    default="fp32",
                     help="fp32: the FP32 workload (default, with its BF16-storage and split-plane runs alongside); "
                          "lowprec: the reduced-precision workload n=4e6, d=2048, k=32 (BF16, then FP8-E4M3); "
                          "plain: the small plain configuration n=4000, d=100, k=5 (latency-bound); "
                          "serving: a Poisson stream of BF16 truncated-SVD requests through the request server; "
-                         "kernels: every step kernel on one shape (--shape, --rows), one-step solves, for profiling")
+                         "kernels: every step kernel on one shape (--shape, --rows), one-step solves, for profiling; "
+                         "batching: independent BF16 instances of mixed shapes solved by one graph launch")
     ap.add_argument("--rows", type=int, default=None,
                     help="override n (same spectrum and partition count): a smaller case for profiler captures")
     return ap.parse_args()
@@ -314,12 +317,17 @@ def run_plain(args):
         dist.destroy_process_group()
 
 
+SERVING_WIDTHS = [64, 90, 128, 181, 256, 362, 512, 724, 1024]   # log-spaced pool widths
+
+
 def _serving_requests(n_req: int, rate: float, seed: int):
-    """Request shapes (log-uniform n, d, m; k uniform in {4, 8, 16, 32}) and Poisson arrival times."""
+    """Request shapes (log-uniform n, m; d log-uniform rounded to the nearest
+    pool width; k uniform in {4, 8, 16, 32}) and Poisson arrival times."""
     rng = np.random.default_rng(seed)
     lu = lambda lo, hi, size: np.exp(rng.uniform(np.log(lo), np.log(hi), size))
     n = np.round(lu(2_000, 200_000, n_req)).astype(int)
-    d = np.round(lu(64, 1024, n_req)).astype(int)
+    w = np.log(np.array(SERVING_WIDTHS, dtype=float))
+    d = np.array([SERVING_WIDTHS[int(np.argmin(np.abs(w - np.log(x))))] for x in lu(64, 1024, n_req)])
     m = np.round(lu(4, 32, n_req)).astype(int)
     k = rng.choice([4, 8, 16, 32], n_req)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
@@ -328,12 +336,130 @@ def _serving_requests(n_req: int, rate: float, seed: int):
                  seed=seed * 100_000 + i) for i in range(n_req)]
 
 
+def _width_pools(torch, local, seed, pool_rows):
+    """Device pools of spiked BF16 rows, one per width in SERVING_WIDTHS, each with
+    its own Haar rotation and lambda_j = 0.85^j (j <= width); host copies too."""
+    import synth
+    bits, dev = {}, {}
+    for wi, w in enumerate(SERVING_WIDTHS):
+        lam = 0.85 ** np.arange(1, w + 1)
+        rows = synth.spiked_rows(pool_rows, w, lam, 0.0, seed + 10 + wi, out_dtype=np.float32,
+                                 threads=os.cpu_count())
+        bits[w] = synth.f32_to_bf16_bits(rows)
+        dev[w] = torch.from_numpy(bits[w].view(np.int16)).cuda(local)
+        del rows
+    return bits, dev
+
+
+def run_batching(args):
+    """Batching: independent instances (n log-uniform [2e3, 2e5], d log-uniform
+    [64, 1024] rounded to the pool widths, m [4, 32], k in {4, 8, 16, 32}; BF16;
+    p = 4, T = 30) loaded once into a batch, step kernels chosen per instance by
+    the autotuner, and every solve run by one CUDA graph launch.  Beside it: the
+    same instances solved one after another (each its own replayed graph)."""
+    import torch
+
+    import oracle
+    import synth
+    from paper_2002_08014_gb300 import binding as B
+
+    rank, world, local = _dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    seed = synth.configs.SEED_BASE + 4
+    inst = _serving_requests(args.instances, 1.0, seed)
+    pool_rows = 400_000
+    bits, dev = _width_pools(torch, local, seed, pool_rows)
+    orng = np.random.default_rng(seed + 1)
+    sched = [4] * 30
+    a_bytes = 0.0
+    with B.Batch(device=local) as bt:
+        for r in inst:
+            r["off"] = int(orng.integers(0, pool_rows - r["n"]))
+            sizes = synth.partition_sizes(r["n"], r["m"])
+            offs = r["off"] + np.cumsum([0] + sizes[:-1])
+            parts = [dev[r["d"]][o:o + s_] for o, s_ in zip(offs, sizes)]
+            bt.add(parts, r["k"], sched, "sign", synth.gaussian_start(r["d"], r["k"], r["seed"]), dtype="bf16")
+        t_tune = time.perf_counter()
+        bt.autotune()
+        t_tune = time.perf_counter() - t_tune
+        t_cap = time.perf_counter()
+        bt.solve()                      # captures and instantiates the graph, then runs it
+        for i in range(len(inst)):
+            bt.result(i)
+        t_cap = time.perf_counter() - t_cap
+        for _ in range(max(args.warmup - 1, 1)):
+            bt.solve()
+            bt.result(0)
+        clocks = Clocks(local)
+        torch.cuda.synchronize()
+        clocks.start()
+        ms = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            bt.solve()
+            bt.result(0)               # waits for the whole batch
+            ms.append((time.perf_counter() - t0) * 1e3)
+        clk = clocks.stop()
+        outs = [bt.result(i) for i in range(len(inst))]
+        a_bytes = sum(o[2]["a_bytes"] for o in outs)
+        launches = sum(o[2]["kernel_launches"] for o in outs)
+        paths = {}
+        for o in outs:
+            paths[KERNELS[o[2]["path"]]] = paths.get(KERNELS[o[2]["path"]], 0) + 1
+    # the same instances one after another, each with its own context and replayed graph
+    seq_ms = None
+    try:
+        t0 = time.perf_counter()
+        for r in inst:
+            sizes = synth.partition_sizes(r["n"], r["m"])
+            offs = r["off"] + np.cumsum([0] + sizes[:-1])
+            parts = [dev[r["d"]][o:o + s_] for o, s_ in zip(offs, sizes)]
+            with B.LocalPower(parts, dtype="bf16") as lp:
+                lp.solve(r["k"], sched, "sign", synth.gaussian_start(r["d"], r["k"], r["seed"]))
+        seq_ms = (time.perf_counter() - t0) * 1e3
+    except Exception as e:
+        seq_ms = f"error: {str(e)[:200]}"
+    acc, acc_o = [], []
+    cheap = [i for i, r in enumerate(inst) if r["n"] * r["d"] * r["k"] <= 3e8]
+    for i in [cheap[j] for j in np.linspace(0, len(cheap) - 1, min(6, len(cheap))).astype(int)]:
+        r = inst[i]
+        rows = oracle.decode_bf16(bits[r["d"]][r["off"]:r["off"] + r["n"]])
+        w, V = np.linalg.eigh(rows.T @ rows / r["n"])
+        acc.append(oracle.subspace_dist(oracle.orth(outs[i][0]), V[:, ::-1][:, :r["k"]]))
+        ref = oracle.localpower(synth.split_rows(rows, synth.partition_sizes(r["n"], r["m"])), r["k"], sched, "sign",
+                                synth.gaussian_start(r["d"], r["k"], r["seed"]))
+        acc_o.append(oracle.subspace_dist(oracle.orth(outs[i][0]), ref["Z"]))
+    best = min(ms)
+    line = {"metric": METRIC, "value": a_bytes / (best / 1e3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup - 1, 1) + 1, "ms_per_step": float(np.mean(ms)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"LocalPower batching: {len(inst)} independent BF16 instances, n log-uniform "
+                                   f"[2e3, 2e5], d log-uniform [64, 1024] rounded to 9 widths, m [4, 32], k in "
+                                   f"{{4, 8, 16, 32}}, p=4 x30 rounds, one graph launch per step",
+                       "instances": len(inst), "a_bytes_per_step": a_bytes,
+                       "l2": "instances' A from 2.7 GB of device pools (larger than L2)"},
+            "solves_per_s": len(inst) / (best / 1e3), "latency_ms": {"p50": float(np.percentile(ms, 50)),
+                                                                    "p99": float(np.percentile(ms, 99)),
+                                                                    "samples": len(ms)},
+            "kernel_launches_per_step": launches, "step_kernels_chosen": paths,
+            "autotune_s": t_tune, "first_solve_with_capture_s": t_cap,
+            "sequential_ms": seq_ms,
+            "speedup_vs_sequential": (seq_ms / best) if isinstance(seq_ms, float) else None,
+            "clocks": clk, "e2e": None,
+            "accuracy_sample": {"dist_to_oracle": [float(x) for x in acc_o], "max_dist_to_oracle": float(max(acc_o)),
+                                "dist_to_eigh_topk": [float(x) for x in acc]}}
+    print(json.dumps(line))
+
+
 def run_serving(args):
     """Continuous batching: a Poisson stream of truncated-SVD requests of mixed
     shapes through the request server (each BF16, p = 4 x 30 rounds + 3
     refinement rounds + Rayleigh-Ritz), admitted against an HBM budget.  Rows
-    come from a device-resident pool of spiked BF16 rows (lambda_j = 0.85^j); a
-    request names a row range and its first d columns (row pitch 1024)."""
+    come from device-resident pools of spiked BF16 rows, one per width d, each
+    with its own Haar rotation and lambda_j = 0.85^j (j <= d); a request names a
+    row range of the pool of its width."""
     import torch
 
     import oracle
@@ -346,12 +472,8 @@ def run_serving(args):
     torch.cuda.set_device(local)
     seed = synth.configs.SEED_BASE + 5
     reqs = _serving_requests(args.requests, args.rate, seed)
-    pool_rows, pool_d = 1_000_000, 1024
-    lam = 0.85 ** np.arange(1, pool_d + 1)
-    pool = synth.spiked_rows(pool_rows, pool_d, lam, 0.0, seed, out_dtype=np.float32, threads=os.cpu_count())
-    pool_bits = synth.f32_to_bf16_bits(pool)
-    del pool
-    dev_pool = torch.from_numpy(pool_bits.view(np.int16)).cuda(local)
+    pool_rows = 400_000
+    pool_bits, dev_pool = _width_pools(torch, local, seed, pool_rows)
     orng = np.random.default_rng(seed + 1)
     for r in reqs:
         r["off"] = int(orng.integers(0, pool_rows - r["n"]))
@@ -364,9 +486,9 @@ def run_serving(args):
         for r in reqs[:4]:
             sizes = synth.partition_sizes(r["n"], r["m"])
             offs = r["off"] + np.cumsum([0] + sizes[:-1])
-            parts = [dev_pool[o:o + s_] for o, s_ in zip(offs, sizes)]
+            parts = [dev_pool[r["d"]][o:o + s_] for o, s_ in zip(offs, sizes)]
             rid = srv.submit(parts, r["k"], sched, "sign", synth.gaussian_start(r["d"], r["k"], r["seed"]),
-                             dtype="bf16", refine_rounds=3, row_pitch=pool_d, d=r["d"])
+                             dtype="bf16", refine_rounds=3)
             while rid not in srv.progress():
                 time.sleep(0.0005)
             srv.result(rid)
@@ -381,10 +503,9 @@ def run_serving(args):
                 r = reqs[nxt]
                 sizes = synth.partition_sizes(r["n"], r["m"])
                 offs = r["off"] + np.cumsum([0] + sizes[:-1])
-                parts = [dev_pool[o:o + s_] for o, s_ in zip(offs, sizes)]
+                parts = [dev_pool[r["d"]][o:o + s_] for o, s_ in zip(offs, sizes)]
                 y0 = synth.gaussian_start(r["d"], r["k"], r["seed"])
-                ids[srv.submit(parts, r["k"], sched, "sign", y0, dtype="bf16", refine_rounds=3, row_pitch=pool_d,
-                               d=r["d"])] = nxt
+                ids[srv.submit(parts, r["k"], sched, "sign", y0, dtype="bf16", refine_rounds=3)] = nxt
                 nxt += 1
             fin = srv.progress()
             tnow = time.perf_counter() - t0
@@ -404,28 +525,36 @@ def run_serving(args):
     clk = clocks.stop()
     lats = np.array([(done_t[i] - reqs[i]["t"]) * 1e3 for i in range(len(reqs))])
     span = max(done_t.values()) - reqs[0]["t"]
-    # accuracy of a sample against the FP64 eigendecomposition of each request's decoded matrix
-    acc = []
-    for i in np.linspace(0, len(reqs) - 1, 8).astype(int):
+    # a sample of requests against the FP64 oracle run on the same decoded data and schedule
+    # (parity) and against the eigendecomposition of the request's matrix (convergence of the
+    # schedule on that matrix's sample spectrum)
+    acc, acc_o = [], []
+    cheap = [i for i, r in enumerate(reqs) if r["n"] * r["d"] * r["k"] <= 3e8]
+    for i in [cheap[j] for j in np.linspace(0, len(cheap) - 1, min(8, len(cheap))).astype(int)]:
         r = reqs[i]
-        rows = oracle.decode_bf16(pool_bits[r["off"]:r["off"] + r["n"], :r["d"]])
+        rows = oracle.decode_bf16(pool_bits[r["d"]][r["off"]:r["off"] + r["n"]])
         w, V = np.linalg.eigh(rows.T @ rows / r["n"])
         acc.append(oracle.subspace_dist(oracle.orth(r["Z"]), V[:, ::-1][:, :r["k"]]))
+        ref = oracle.localpower(synth.split_rows(rows, synth.partition_sizes(r["n"], r["m"])), r["k"],
+                                sched + [1, 1, 1], "sign", synth.gaussian_start(r["d"], r["k"], r["seed"]))
+        acc_o.append(oracle.subspace_dist(oracle.orth(r["Z"]), ref["Z"]))
     line = {"metric": METRIC, "value": a_bytes / span / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": len(reqs),
             "warmup": 4, "ms_per_step": span * 1e3 / len(reqs), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"LocalPower serving: {len(reqs)} truncated-SVD requests, Poisson arrivals at "
-                                   f"{args.rate:g} req/s, n log-uniform [2e3, 2e5], d [64, 1024], m [4, 32], "
+                                   f"{args.rate:g} req/s, n log-uniform [2e3, 2e5], d log-uniform [64, 1024] "
+                                   f"rounded to 9 pool widths, m [4, 32], "
                                    f"k in {{4, 8, 16, 32}}, BF16, p=4 x30 rounds + 3 refinement rounds + Ritz, "
                                    f"admission budget 120 GB",
                        "requests": len(reqs), "rate_per_s": args.rate, "budget_bytes": budget, "max_active": 64,
-                       "l2": "requests' A from a 2 GB device pool (larger than L2)"},
+                       "l2": "requests' A from 2.7 GB of device pools (larger than L2)"},
             "solves_per_s": len(reqs) / span, "latency_ms": {"p50": float(np.percentile(lats, 50)),
                                                              "p99": float(np.percentile(lats, 99)),
                                                              "max": float(lats.max()), "samples": len(lats)},
             "offered_solves_per_s": args.rate, "wall_s": wall, "peak_active": peak["active"],
             "peak_queued": peak["queued"], "hbm_peak_bytes": int(hbm_peak), "clocks": clk, "e2e": None,
-            "accuracy_sample": {"dist_to_eigh_topk": [float(x) for x in acc], "max": float(max(acc))}}
+            "accuracy_sample": {"dist_to_oracle": [float(x) for x in acc_o], "max_dist_to_oracle": float(max(acc_o)),
+                                "dist_to_eigh_topk": [float(x) for x in acc]}}
     print(json.dumps(line))
 
 
@@ -691,5 +820,7 @@ if __name__ == "__main__":
         run_serving(a)
     elif a.workload == "kernels":
         run_kernels(a)
+    elif a.workload == "batching":
+        run_batching(a)
     else:
         run_ours(a)

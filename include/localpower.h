@@ -267,6 +267,45 @@ const char* lp_server_error(const lp_server* s);
 void lp_server_destroy(lp_server* s);
 
 /* ----------------------------------------------------------------------------
+ * Batch runner: many independent instances (the same lp_request description,
+ * each its own shapes, schedule and dtype) loaded once and solved together by
+ * one CUDA graph launch.  The paper has no counterpart.  The graph holds every
+ * instance's whole solve as an independent branch; it is captured on the first
+ * lp_batch_solve and replayed by later ones until instances are added or
+ * re-tuned.  One thread drives a batch at a time.
+ * ------------------------------------------------------------------------- */
+typedef struct lp_batch lp_batch;
+
+/* lp_batch_create: an empty batch on `device`; instances are admitted while
+ * the sum of their device-memory estimates stays within hbm_budget_bytes
+ * (0 = no bound). */
+lp_status lp_batch_create(lp_batch** out, int device, size_t hbm_budget_bytes);
+
+/* lp_batch_add: load one instance (its partitions are copied to the device now;
+ * the caller's buffers may be reused after the call); *index receives its
+ * position.  LP_ERR_INVALID for malformed requests, LP_ERR_OOM over budget. */
+lp_status lp_batch_add(lp_batch* b, const lp_request* req, int* index);
+
+/* lp_batch_autotune: lp_autotune for every instance (the step kernel and its
+ * tuning chosen by timing, per instance). */
+lp_status lp_batch_autotune(lp_batch* b);
+
+/* lp_batch_solve: every instance's solve, asynchronously, as one graph launch. */
+lp_status lp_batch_solve(lp_batch* b);
+
+/* lp_batch_result: waits for the batch, then lp_result of instance `index`. */
+lp_status lp_batch_result(lp_batch* b, int index, double* z_out, double* sigma_out, lp_stats* stats);
+
+/* lp_batch_size: number of instances (0 for NULL). */
+int lp_batch_size(const lp_batch* b);
+
+/* lp_batch_error: text of the last failure on the batch ("" if none). */
+const char* lp_batch_error(const lp_batch* b);
+
+/* lp_batch_destroy: wait for the batch and free everything; NULL is a no-op. */
+void lp_batch_destroy(lp_batch* b);
+
+/* ----------------------------------------------------------------------------
  * Single-kernel entry points, for checking one step of the method at a time.
  * They run on the context's stream and synchronise before returning.
  * ------------------------------------------------------------------------- */

@@ -28,8 +28,9 @@ PATHS = {0: "simt", 1: "tc_resident", 2: "tc_streaming"}
 # Every symbol the header declares, in declaration order.
 EXPORTS = ["lp_create", "lp_load_partitions", "lp_solve", "lp_result", "lp_destroy", "lp_last_error",
            "lp_set_tuning", "lp_autotune", "lp_server_create", "lp_server_submit", "lp_server_progress",
-           "lp_server_result", "lp_server_query", "lp_server_error", "lp_server_destroy", "lp_power_step", "lp_orth",
-           "lp_align_aggregate", "lp_power_step_static"]
+           "lp_server_result", "lp_server_query", "lp_server_error", "lp_server_destroy", "lp_batch_create",
+           "lp_batch_add", "lp_batch_autotune", "lp_batch_solve", "lp_batch_result", "lp_batch_size", "lp_batch_error",
+           "lp_batch_destroy", "lp_power_step", "lp_orth", "lp_align_aggregate", "lp_power_step_static"]
 
 
 class lp_stats(C.Structure):
@@ -109,8 +110,19 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
     L.lp_server_error.restype = C.c_char_p
     L.lp_server_destroy.argtypes = [P]
     L.lp_server_destroy.restype = None
+    L.lp_batch_create.argtypes = [C.POINTER(P), I, C.c_size_t]
+    L.lp_batch_add.argtypes = [P, C.POINTER(lp_request), C.POINTER(I)]
+    L.lp_batch_autotune.argtypes = [P]
+    L.lp_batch_solve.argtypes = [P]
+    L.lp_batch_result.argtypes = [P, I, P, P, C.POINTER(lp_stats)]
+    L.lp_batch_size.argtypes = [P]
+    L.lp_batch_error.argtypes = [P]
+    L.lp_batch_error.restype = C.c_char_p
+    L.lp_batch_destroy.argtypes = [P]
+    L.lp_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("lp_destroy", "lp_last_error", "lp_server_error", "lp_server_destroy"):
+        if name not in ("lp_destroy", "lp_last_error", "lp_server_error", "lp_server_destroy", "lp_batch_error",
+                        "lp_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -370,35 +382,11 @@ class Server:
     def submit(self, parts, k: int, p_schedule, agg: str, y0, dtype: str = "f32", row_scales=None,
                refine_rounds: int = 0, flags: int = LP_FLAG_RITZ, row_pitch: int = 0, d: int | None = None) -> int:
         """parts: host arrays or CUDA tensors (s_i x pitch); d defaults to the parts' width."""
-        np_dt = {"f32": np.float32, "bf16": np.uint16, "e4m3": np.uint8, "f32_bf16x2": np.float32}[dtype]
-        m = len(parts)
-        keep, ptrs, spaces = [], [], set()
-        for p in parts:
-            q, sp, kk = _ptr(p, np_dt)
-            ptrs.append(q.value)
-            keep.append(kk)
-            spaces.add(sp)
-        if len(spaces) != 1:
-            raise ValueError("partitions must all be host or all device")
-        dd = int(d if d is not None else parts[0].shape[1])
-        rows = (C.c_int64 * m)(*[int(p.shape[0]) for p in parts])
-        parr = (C.c_void_p * m)(*ptrs)
-        sarr = None
-        if row_scales is not None:
-            sl = []
-            for sc in row_scales:
-                q, _, kk = _ptr(sc, np.float32)
-                sl.append(q.value)
-                keep.append(kk)
-            sarr = (C.c_void_p * m)(*sl)
-        sched = np.ascontiguousarray(np.asarray(p_schedule, dtype=np.int32))
-        y0c = np.ascontiguousarray(y0, dtype=np.float64)
-        req = lp_request(m, rows, dd, int(row_pitch), DTYPE[dtype], parr, sarr, spaces.pop(), int(k),
-                         sched.ctypes.data_as(C.POINTER(C.c_int)), len(sched), AGG[agg],
-                         y0c.ctypes.data_as(C.POINTER(C.c_double)), int(refine_rounds), int(flags))
+        req, keep, dd = _make_request(parts, k, p_schedule, agg, y0, dtype, row_scales, refine_rounds, flags,
+                                      row_pitch, d)
         rid = C.c_int64(0)
         self._check(load().lp_server_submit(self.h, C.byref(req), C.byref(rid)))
-        self._keep[rid.value] = (keep, rows, parr, sarr, sched, y0c)
+        self._keep[rid.value] = keep
         self._shape[rid.value] = (dd, int(k))
         return rid.value
 
@@ -429,6 +417,90 @@ class Server:
             load().lp_server_destroy(self.h)
             self.h = C.c_void_p()
             self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _make_request(parts, k, p_schedule, agg, y0, dtype, row_scales, refine_rounds, flags, row_pitch, d):
+    """An lp_request for the server or the batch runner, and the objects that must outlive it."""
+    np_dt = {"f32": np.float32, "bf16": np.uint16, "e4m3": np.uint8, "f32_bf16x2": np.float32}[dtype]
+    m = len(parts)
+    keep, ptrs, spaces = [], [], set()
+    for p in parts:
+        q, sp, kk = _ptr(p, np_dt)
+        ptrs.append(q.value)
+        keep.append(kk)
+        spaces.add(sp)
+    if len(spaces) != 1:
+        raise ValueError("partitions must all be host or all device")
+    dd = int(d if d is not None else parts[0].shape[1])
+    rows = (C.c_int64 * m)(*[int(p.shape[0]) for p in parts])
+    parr = (C.c_void_p * m)(*ptrs)
+    sarr = None
+    if row_scales is not None:
+        sl = []
+        for sc in row_scales:
+            q, _, kk = _ptr(sc, np.float32)
+            sl.append(q.value)
+            keep.append(kk)
+        sarr = (C.c_void_p * m)(*sl)
+    sched = np.ascontiguousarray(np.asarray(p_schedule, dtype=np.int32))
+    y0c = np.ascontiguousarray(y0, dtype=np.float64)
+    req = lp_request(m, rows, dd, int(row_pitch), DTYPE[dtype], parr, sarr, spaces.pop(), int(k),
+                     sched.ctypes.data_as(C.POINTER(C.c_int)), len(sched), AGG[agg],
+                     y0c.ctypes.data_as(C.POINTER(C.c_double)), int(refine_rounds), int(flags))
+    keep += [rows, parr, sarr, sched, y0c]
+    return req, keep, dd
+
+
+class Batch:
+    """lp_batch_*: independent instances solved by one graph launch."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.h = C.c_void_p()
+        st = load().lp_batch_create(C.byref(self.h), device, hbm_budget_bytes)
+        if st != LP_OK:
+            raise LPError(st, "lp_batch_create failed")
+        self._shape = []
+
+    def _check(self, st):
+        if st != LP_OK:
+            raise LPError(st, load().lp_batch_error(self.h).decode(errors="replace"))
+
+    def add(self, parts, k: int, p_schedule, agg: str, y0, dtype: str = "f32", row_scales=None,
+            refine_rounds: int = 0, flags: int = LP_FLAG_RITZ, row_pitch: int = 0, d: int | None = None) -> int:
+        req, keep, dd = _make_request(parts, k, p_schedule, agg, y0, dtype, row_scales, refine_rounds, flags,
+                                      row_pitch, d)
+        idx = C.c_int(0)
+        self._check(load().lp_batch_add(self.h, C.byref(req), C.byref(idx)))
+        self._shape.append((dd, int(k)))
+        return idx.value
+
+    def autotune(self):
+        self._check(load().lp_batch_autotune(self.h))
+
+    def solve(self):
+        self._check(load().lp_batch_solve(self.h))
+
+    def result(self, i: int):
+        d, k = self._shape[i]
+        Z = np.empty((d, k), dtype=np.float64)
+        sig = np.empty(k, dtype=np.float64)
+        st = lp_stats()
+        self._check(load().lp_batch_result(self.h, i, Z.ctypes.data, sig.ctypes.data, C.byref(st)))
+        return Z, sig, st.as_dict()
+
+    def __len__(self):
+        return int(load().lp_batch_size(self.h))
+
+    def close(self):
+        if self.h:
+            load().lp_batch_destroy(self.h)
+            self.h = C.c_void_p()
 
     def __enter__(self):
         return self

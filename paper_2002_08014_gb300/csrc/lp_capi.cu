@@ -292,6 +292,16 @@ void build_segments(const lp_ctx* c, int G, std::vector<Segment>& segs, std::vec
   slot_begin[m] = nslots;
 }
 
+// Event record that also works inside a stream capture: there a plain record is
+// only a dependency edge, so timing events become external event-record nodes.
+cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t q = cudaStreamIsCapturing(s, &cs);
+  if (q != cudaSuccess) return q;
+  return cudaEventRecordWithFlags(e, s, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                             : cudaEventRecordDefault);
+}
+
 const int* slot_begin_of(const lp_ctx* c) {
   return c->path == PATH_TCS ? c->dSlotBeginTcs : c->path == PATH_TC ? c->dSlotBeginTc : c->dSlotBegin;
 }
@@ -315,7 +325,7 @@ lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool t
       LP_CUDA(cudaEventCreate(&e));
       c->step_ev.push_back(e);
     }
-    LP_CUDA(cudaEventRecordWithFlags(c->step_ev[c->step_ev_used], c->stream, cudaEventRecordExternal));
+    LP_CUDA(record_event(c->step_ev[c->step_ev_used], c->stream));
   }
   cudaError_t e;
   if (c->path == PATH_TCS)
@@ -328,7 +338,7 @@ lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool t
     e = lp::launch_step_simt(a, c->dtype, K, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "fused power-step launch");
   if (timing) {
-    LP_CUDA(cudaEventRecordWithFlags(c->step_ev[c->step_ev_used + 1], c->stream, cudaEventRecordExternal));
+    LP_CUDA(record_event(c->step_ev[c->step_ev_used + 1], c->stream));
     c->step_ev_used += 2;
   }
   c->stats.step_launches++;
@@ -749,10 +759,13 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
     if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, nullptr, 0, m, d, K, c->dMZ, c->stream),
                            "aggregate")))
       return st;
-    if ((st = check_launch(c, lp::launch_ritz(c->dZ, c->dMZ, d, k, K, double(c->n), c->dZout, c->dSigma, c->dStatus,
-                                              c->stream),
+    // the partials buffer is free again after the reduction: it holds the Ritz scratch
+    if (lp::ritz_scratch_bytes(d, K) > state_sizes(c, K).P) return fail(c, LP_ERR_INVALID, "Ritz scratch too small");
+    if ((st = check_launch(c, lp::launch_ritz(c->dZ, c->dMZ, d, k, K, double(c->n), c->dZout, c->dSigma,
+                                              reinterpret_cast<double*>(c->dP), c->dStatus, c->stream),
                            "ritz")))
       return st;
+    c->stats.kernel_launches += 2;  // launch_ritz runs three kernels
   } else {
     if ((st = check_launch(c, lp::launch_unpack(c->dZ, c->dZout, 1, d, k, K, c->stream), "unpack"))) return st;
   }
@@ -855,8 +868,10 @@ lp_status lp_autotune(lp_ctx* c, int k, lp_tuning* chosen, int* path_out, double
   return LP_OK;
 }
 
-lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, const double* y0,
-                   int refine_rounds, unsigned flags) {
+// Checks, kernel choice and device state of a solve; uploads y0 to the staging
+// buffer (pageable host memory: never inside a captured graph).
+static lp_status solve_prepare(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, const double* y0,
+                               int refine_rounds, unsigned flags, bool record_start, const double** dy0) {
   if (!c) return LP_ERR_INVALID;
   c->err.clear();
   lp_status st = validate_k(c, k);
@@ -873,15 +888,28 @@ lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator
   const int K = kcap_of(k);
   if ((st = select_path(c, k, flags))) return st;
   if ((st = ensure_state(c, K))) return st;
-
-  const bool timing = (flags & LP_FLAG_TIMING) != 0;
   c->solved = false;
   c->k = k;
   c->ritz = (flags & LP_FLAG_RITZ) != 0;
+  if (record_start) LP_CUDA(cudaEventRecord(c->ev0, c->stream));
+  return stage_in(c, y0, size_t(c->d) * k, LP_HOST, dy0);
+}
 
-  LP_CUDA(cudaEventRecord(c->ev0, c->stream));
-  const double* dy0;
-  if ((st = stage_in(c, y0, size_t(c->d) * k, LP_HOST, &dy0))) return st;
+static void solve_mark(lp_ctx* c, int k) {
+  c->stats.k = k;
+  c->stats.n = c->n;
+  c->stats.d = c->d;
+  c->stats.m = c->m;
+  c->stats.path = c->path;
+  c->solved = true;
+}
+
+lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, const double* y0,
+                   int refine_rounds, unsigned flags) {
+  const double* dy0 = nullptr;
+  lp_status st = solve_prepare(c, k, p_schedule, T, agg, y0, refine_rounds, flags, true, &dy0);
+  if (st) return st;
+  const bool timing = (flags & LP_FLAG_TIMING) != 0;
   // The launch sequence depends only on these; a matching key replays the captured graph.
   std::vector<int64_t> key = {int64_t(c->gen), k, T, int64_t(agg), refine_rounds, int64_t(flags), c->path};
   key.insert(key.end(), p_schedule, p_schedule + T);
@@ -922,12 +950,7 @@ lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator
     }
   }
   LP_CUDA(cudaEventRecord(c->ev1, c->stream));
-  c->stats.k = k;
-  c->stats.n = c->n;
-  c->stats.d = c->d;
-  c->stats.m = c->m;
-  c->stats.path = c->path;
-  c->solved = true;
+  solve_mark(c, k);
   return LP_OK;
 }
 
@@ -1123,3 +1146,29 @@ lp_status lp_align_aggregate(lp_ctx* c, int m, int64_t d, int k, lp_aggregator a
 }
 
 }  // extern "C"
+
+// ---- hooks for the batch runner (one graph over many contexts) ----------------
+lp_status lp::batch_prepare(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, const double* y0,
+                            int refine_rounds, unsigned flags) {
+  const double* dy0 = nullptr;
+  return solve_prepare(c, k, p_schedule, T, agg, y0, refine_rounds, flags, false, &dy0);
+}
+
+lp_status lp::batch_enqueue(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, int refine_rounds,
+                            unsigned flags, lp_stats* captured) {
+  std::memset(&c->stats, 0, sizeof(c->stats));
+  c->step_ev_used = 0;
+  LP_CUDA(record_event(c->ev0, c->stream));
+  const lp_status st = solve_body(c, k, p_schedule, T, agg, refine_rounds, (flags & LP_FLAG_TIMING) != 0, c->dStage);
+  if (st) return st;
+  LP_CUDA(record_event(c->ev1, c->stream));
+  *captured = c->stats;
+  return LP_OK;
+}
+
+void lp::batch_mark(lp_ctx* c, int k, const lp_stats& captured) {
+  c->stats = captured;
+  solve_mark(c, k);
+}
+
+cudaStream_t lp::ctx_stream(lp_ctx* c) { return c->stream; }

@@ -99,6 +99,16 @@ size_t estimate_bytes(int sms, int m, const int64_t* rows, int64_t d, int64_t pi
                       lp_ptr_space space);
 // 1: the last lp_solve finished on the device; 0: still running; -1: no solve or a CUDA error.
 int solve_state(lp_ctx* c);
+// A solve split for capture into one graph over many contexts: checks, kernel
+// choice and y0 upload (outside the capture); the launch sequence on the
+// context's stream (inside it; *captured receives its counters); and marking
+// the context solved after the graph ran.
+lp_status batch_prepare(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, const double* y0,
+                        int refine_rounds, unsigned flags);
+lp_status batch_enqueue(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, int refine_rounds,
+                        unsigned flags, lp_stats* captured);
+void batch_mark(lp_ctx* c, int k, const lp_stats& captured);
+cudaStream_t ctx_stream(lp_ctx* c);
 
 // Message returned by lp_last_error(NULL) (failures of calls without a context).
 void set_no_context_error(const char* msg);
@@ -116,9 +126,11 @@ cudaError_t launch_align(const float* Zl, int64_t z_stride, const float* Zb, int
 // Y = sum_i w_i Y_i G_i  (G == nullptr: identity; diag_only: G_i diagonal)
 cudaError_t launch_aggregate(const float* Yl, const float* w, const float* G, int diag_only, int m, int d, int K,
                              float* Y, cudaStream_t s);
-// Ritz: H = Z^T MZ (FP64), eig (FP64 Jacobi), Zout = Z W (FP64), sigma = sqrt(n lambda)
+// Ritz: H = Z^T MZ (FP64), eig (FP64 Jacobi), Zout = Z W (FP64), sigma = sqrt(n lambda).
+// Three launches; `scratch` holds ritz_scratch_bytes(d, K) bytes.
 cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, double n, double* Zout, double* sigma,
-                        int* status, cudaStream_t s);
+                        double* scratch, int* status, cudaStream_t s);
+size_t ritz_scratch_bytes(int d, int K);
 // FP64 d x k (row-major) <-> FP32 d x K padded blocks
 cudaError_t launch_pack(const double* src, float* dst, int batch, int d, int k, int K, cudaStream_t s);
 cudaError_t launch_unpack(const float* src, double* dst, int batch, int d, int k, int K, cudaStream_t s);

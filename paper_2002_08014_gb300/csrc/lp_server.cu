@@ -266,3 +266,247 @@ void lp_server_destroy(lp_server* s) {
 }
 
 }  // extern "C"
+
+// =============================================================================
+// Batch runner: many independent instances solved by one CUDA graph launch.
+//
+// Each instance owns a context (its partitions loaded once, its own stream and
+// state).  lp_batch_solve uploads every instance's start block, then - the
+// first time, or after instances or tuning changed - captures every instance's
+// whole launch sequence into one graph: a fork event on the batch stream, each
+// instance's sequence on its own stream, a join back.  The branches are
+// independent, so the GPU runs the instances' kernels side by side; later
+// solves replay the graph with one launch.
+namespace {
+
+struct Inst {
+  Request q;     // parameters (ctx, results unused here)
+  lp_ctx* ctx = nullptr;
+  lp_stats captured{};
+  cudaEvent_t join = nullptr, ready = nullptr;
+};
+
+}  // namespace
+
+struct lp_batch {
+  int device = 0;
+  int sms = 0;
+  size_t budget = 0, in_use = 0;
+  cudaStream_t root = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<std::unique_ptr<Inst>> inst;
+  cudaGraphExec_t exec = nullptr;
+  bool solved = false;
+  std::string err;
+};
+
+namespace {
+
+lp_status bfail(lp_batch* b, lp_status st, const std::string& msg) {
+  b->err = msg;
+  return st;
+}
+
+void drop_batch_graph(lp_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->solved = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+lp_status lp_batch_create(lp_batch** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return LP_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    (void)cudaGetLastError();
+    return ndev == 0 ? LP_ERR_CUDA : LP_ERR_INVALID;
+  }
+  lp_batch* b = new (std::nothrow) lp_batch();
+  if (!b) return LP_ERR_OOM;
+  b->device = device;
+  b->budget = hbm_budget_bytes;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    lp_batch_destroy(b);
+    return LP_ERR_CUDA;
+  }
+  *out = b;
+  return LP_OK;
+}
+
+lp_status lp_batch_add(lp_batch* b, const lp_request* q, int* index) {
+  if (!b) return LP_ERR_INVALID;
+  b->err.clear();
+  if (!q || !index) return bfail(b, LP_ERR_INVALID, "request and index must be non-NULL");
+  if (q->m < 1 || !q->rows || !q->parts || q->d < 1 || q->k < 1 || q->k > LP_MAX_K || q->k > q->d || !q->y0 ||
+      q->T < 0 || q->refine_rounds < 0 || q->T + q->refine_rounds < 1 || (q->T > 0 && !q->p_schedule) ||
+      (q->row_pitch != 0 && q->row_pitch < q->d) || (q->dtype == LP_FP8_E4M3 && !q->row_scales))
+    return bfail(b, LP_ERR_INVALID, "malformed request");
+  auto in = std::make_unique<Inst>();
+  Request& r = in->q;
+  r.m = q->m;
+  r.d = q->d;
+  r.pitch = q->row_pitch ? q->row_pitch : q->d;
+  r.dtype = q->dtype;
+  r.space = q->space;
+  r.rows.assign(q->rows, q->rows + q->m);
+  r.parts.assign(q->parts, q->parts + q->m);
+  if (q->dtype == LP_FP8_E4M3) r.scales.assign(q->row_scales, q->row_scales + q->m);
+  r.k = q->k;
+  r.T = q->T;
+  r.refine = q->refine_rounds;
+  r.agg = q->agg;
+  r.flags = q->flags;
+  if (q->T > 0) r.sched.assign(q->p_schedule, q->p_schedule + q->T);
+  r.y0.assign(q->y0, q->y0 + size_t(q->d) * q->k);
+  r.est = lp::estimate_bytes(b->sms, r.m, r.rows.data(), r.d, r.pitch, r.dtype, r.k, r.space);
+  if (b->budget && b->in_use + r.est > b->budget)
+    return bfail(b, LP_ERR_OOM, "instance does not fit the batch's HBM budget");
+  lp_status st = lp_create(&in->ctx, b->device, r.est, nullptr);
+  if (st) return bfail(b, st, lp_last_error(nullptr));
+  st = lp::load_pitched(in->ctx, r.m, r.rows.data(), r.d, r.pitch, r.dtype, r.parts.data(),
+                        r.dtype == LP_FP8_E4M3 ? r.scales.data() : nullptr, r.space);
+  if (!st && (cudaEventCreateWithFlags(&in->join, cudaEventDisableTiming) != cudaSuccess ||
+              cudaEventCreateWithFlags(&in->ready, cudaEventDisableTiming) != cudaSuccess)) {
+    (void)cudaGetLastError();
+    st = LP_ERR_CUDA;
+  }
+  if (st) {
+    const std::string msg = lp_last_error(in->ctx);
+    if (in->join) cudaEventDestroy(in->join);
+    if (in->ready) cudaEventDestroy(in->ready);
+    lp_destroy(in->ctx);
+    return bfail(b, st, msg);
+  }
+  b->in_use += r.est;
+  drop_batch_graph(b);
+  *index = static_cast<int>(b->inst.size());
+  b->inst.push_back(std::move(in));
+  return LP_OK;
+}
+
+lp_status lp_batch_autotune(lp_batch* b) {
+  if (!b) return LP_ERR_INVALID;
+  b->err.clear();
+  for (auto& in : b->inst) {
+    const lp_status st = lp_autotune(in->ctx, in->q.k, nullptr, nullptr, nullptr);
+    if (st) return bfail(b, st, lp_last_error(in->ctx));
+  }
+  drop_batch_graph(b);
+  return LP_OK;
+}
+
+lp_status lp_batch_solve(lp_batch* b) {
+  if (!b) return LP_ERR_INVALID;
+  b->err.clear();
+  if (b->inst.empty()) return bfail(b, LP_ERR_STATE, "empty batch");
+  if (cudaSetDevice(b->device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return bfail(b, LP_ERR_CUDA, "cudaSetDevice failed");
+  }
+  // the previous launch may still read the staged start blocks
+  if (cudaStreamSynchronize(b->root) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return bfail(b, LP_ERR_CUDA, "waiting for the previous batch solve");
+  }
+  b->solved = false;
+  // start blocks in; the graph waits for every upload
+  for (auto& in : b->inst) {
+    const Request& r = in->q;
+    lp_status st = lp::batch_prepare(in->ctx, r.k, r.sched.empty() ? nullptr : r.sched.data(), r.T, r.agg,
+                                     r.y0.data(), r.refine, r.flags);
+    if (st) return bfail(b, st, lp_last_error(in->ctx));
+    if (cudaEventRecord(in->ready, lp::ctx_stream(in->ctx)) != cudaSuccess ||
+        cudaStreamWaitEvent(b->root, in->ready, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return bfail(b, LP_ERR_CUDA, "ordering the uploads");
+    }
+  }
+  if (!b->exec) {
+    cudaError_t e = cudaStreamBeginCapture(b->root, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->root);
+    lp_status st = LP_OK;
+    for (size_t i = 0; e == cudaSuccess && !st && i < b->inst.size(); ++i) {
+      Inst& in = *b->inst[i];
+      const Request& r = in.q;
+      cudaStream_t s = lp::ctx_stream(in.ctx);
+      e = cudaStreamWaitEvent(s, b->fork, 0);
+      if (e != cudaSuccess) break;
+      st = lp::batch_enqueue(in.ctx, r.k, r.sched.empty() ? nullptr : r.sched.data(), r.T, r.agg, r.refine, r.flags,
+                             &in.captured);
+      if (st) {
+        b->err = lp_last_error(in.ctx);
+        break;
+      }
+      e = cudaEventRecord(in.join, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->root, in.join, 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->root, &g);
+    if (st || e != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      (void)cudaGetLastError();
+      if (st) return st;
+      return bfail(b, LP_ERR_CUDA, std::string("capturing the batch: ") +
+                                       cudaGetErrorString(e != cudaSuccess ? e : ee));
+    }
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->exec = nullptr;
+      (void)cudaGetLastError();
+      return bfail(b, LP_ERR_CUDA, std::string("instantiating the batch graph: ") + cudaGetErrorString(e));
+    }
+  }
+  if (cudaGraphLaunch(b->exec, b->root) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return bfail(b, LP_ERR_CUDA, "launching the batch graph");
+  }
+  for (auto& in : b->inst) lp::batch_mark(in->ctx, in->q.k, in->captured);
+  b->solved = true;
+  return LP_OK;
+}
+
+lp_status lp_batch_result(lp_batch* b, int index, double* z_out, double* sigma_out, lp_stats* stats) {
+  if (!b) return LP_ERR_INVALID;
+  b->err.clear();
+  if (index < 0 || index >= static_cast<int>(b->inst.size())) return bfail(b, LP_ERR_INVALID, "index out of range");
+  if (!b->solved) return bfail(b, LP_ERR_STATE, "no batch solve to report");
+  if (cudaStreamSynchronize(b->root) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return bfail(b, LP_ERR_CUDA, "waiting for the batch");
+  }
+  lp_ctx* c = b->inst[index]->ctx;
+  const lp_status st = lp_result(c, z_out, sigma_out, stats);
+  if (st) b->err = lp_last_error(c);
+  return st;
+}
+
+int lp_batch_size(const lp_batch* b) { return b ? static_cast<int>(b->inst.size()) : 0; }
+
+const char* lp_batch_error(const lp_batch* b) { return b ? b->err.c_str() : ""; }
+
+void lp_batch_destroy(lp_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->root) cudaStreamSynchronize(b->root);
+  drop_batch_graph(b);
+  for (auto& in : b->inst) {
+    if (in->join) cudaEventDestroy(in->join);
+    if (in->ready) cudaEventDestroy(in->ready);
+    lp_destroy(in->ctx);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->root) cudaStreamDestroy(b->root);
+  delete b;
+}
+
+}  // extern "C"

@@ -172,14 +172,25 @@ __device__ void gram_fp32(const float* __restrict__ Y, int d, float* red, double
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-  for (int r = sl; r < d; r += S) {
-    const float4 u = *reinterpret_cast<const float4*>(Y + int64_t(r) * K + 4 * bi);
-    const float4 v = *reinterpret_cast<const float4*>(Y + int64_t(r) * K + 4 * bj);
-    const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+  // eight rows per trip, all loads issued before the FMAs: one block reads the
+  // whole d x K block with ~16 loads in flight per thread instead of one
+  constexpr int U = 8;
+  for (int r0 = sl; r0 < d; r0 += S * U) {
+    float4 u[U], v[U];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < U; ++q) {
+      const int r = r0 + q * S;
+      u[q] = r < d ? *reinterpret_cast<const float4*>(Y + int64_t(r) * K + 4 * bi) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[q] = r < d ? *reinterpret_cast<const float4*>(Y + int64_t(r) * K + 4 * bj) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(uu[a], vv[b], acc[a][b]);
+    for (int q = 0; q < U; ++q) {
+      const float uu[4] = {u[q].x, u[q].y, u[q].z, u[q].w}, vv[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(uu[a], vv[b], acc[a][b]);
+    }
   }
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -409,22 +420,47 @@ __global__ void aggregate_kernel(const float* __restrict__ Yl, const float* __re
 }
 
 // ---------------------------------------------------------------- Ritz
-__global__ void __launch_bounds__(kT) ritz_kernel(const float* __restrict__ Z, const float* __restrict__ MZ, int d,
-                                                  int k, int K, double n, double* __restrict__ Zout,
-                                                  double* __restrict__ sigma, int* status) {
+// H = Z^T (M Z) in FP64, split over row slices: block g adds the products of
+// its rows (staged in shared memory) into Hpart[g]; ritz_solve adds the slices
+// in slice order (deterministic), symmetrises, diagonalises (FP64 Jacobi),
+// orders by descending Ritz value and writes sigma and the reordered V;
+// ritz_rotate forms Zout = Z V row by row.
+constexpr int kRitzRows = 64;  // rows per slice
+
+__global__ void __launch_bounds__(kT) ritz_partial_kernel(const float* __restrict__ Z, const float* __restrict__ MZ,
+                                                          int d, int k, int K, double* __restrict__ Hpart) {
+  __shared__ float zs[kRitzRows * LP_MAX_K], ms[kRitzRows * LP_MAX_K];
+  const int t = threadIdx.x;
+  const int r0 = blockIdx.x * kRitzRows;
+  const int nr = min(kRitzRows, d - r0);
+  for (int e = t; e < nr * K; e += kT) {
+    zs[e] = Z[int64_t(r0) * K + e];
+    ms[e] = MZ[int64_t(r0) * K + e];
+  }
+  __syncthreads();
+  double* H = Hpart + int64_t(blockIdx.x) * K * K;
+  for (int e = t; e < K * K; e += kT) {
+    const int a = e / K, b = e % K;
+    double sum = 0.0;
+    if (a < k && b < k)
+      for (int r = 0; r < nr; ++r) sum += static_cast<double>(zs[r * K + a]) * ms[r * K + b];
+    H[e] = sum;
+  }
+}
+
+__global__ void __launch_bounds__(kT) ritz_solve_kernel(const double* __restrict__ Hpart, int slices, int k, int K,
+                                                        double n, double* __restrict__ Vo,
+                                                        double* __restrict__ sigma, int* status) {
   extern __shared__ __align__(16) unsigned char sm[];
   double* H = reinterpret_cast<double*>(sm);  // K*K
   double* V = H + K * K;                       // K*K
   double* lam = V + K * K;                     // K
   int* order = reinterpret_cast<int*>(lam + K);
   const int t = threadIdx.x;
-  // H = Z^T (M Z) with FP64 accumulation.
   for (int e = t; e < K * K; e += kT) {
-    const int a = e / K, b = e % K;
-    double s = 0.0;
-    if (a < k && b < k)
-      for (int r = 0; r < d; ++r) s += static_cast<double>(Z[int64_t(r) * K + a]) * MZ[int64_t(r) * K + b];
-    H[e] = s;
+    double sum = 0.0;
+    for (int g = 0; g < slices; ++g) sum += Hpart[int64_t(g) * K * K + e];
+    H[e] = sum;
   }
   __syncthreads();
   if (t < 32) {
@@ -432,9 +468,9 @@ __global__ void __launch_bounds__(kT) ritz_kernel(const float* __restrict__ Z, c
     for (int e = t; e < K * K; e += 32) {
       const int a = e / K, b = e % K;
       if (a < b) {
-        const double s = 0.5 * (H[a * K + b] + H[b * K + a]);
-        H[a * K + b] = s;
-        H[b * K + a] = s;
+        const double v = 0.5 * (H[a * K + b] + H[b * K + a]);
+        H[a * K + b] = v;
+        H[b * K + a] = v;
       }
     }
     __syncwarp();
@@ -442,10 +478,10 @@ __global__ void __launch_bounds__(kT) ritz_kernel(const float* __restrict__ Z, c
     const bool ok = warp_jacobi(H, V, k, K);
     if (!ok && t == 0) atomicOr(status, ST_JACOBI);
     for (int j = 0; j < k; ++j) {
-      double s = 0.0;
-      if (t < k) s = H[t * K + j] * H[t * K + j];
-      s = warp_sum(s);
-      if (t == 0) lam[j] = s > 0.0 ? s * rsqrt_nr(s) : 0.0;
+      double v = 0.0;
+      if (t < k) v = H[t * K + j] * H[t * K + j];
+      v = warp_sum(v);
+      if (t == 0) lam[j] = v > 0.0 ? v * rsqrt_nr(v) : 0.0;
     }
     __syncwarp();
     if (t == 0) {
@@ -462,14 +498,20 @@ __global__ void __launch_bounds__(kT) ritz_kernel(const float* __restrict__ Z, c
     __syncwarp();
   }
   __syncthreads();
-  // Zout = Z V(:, order), FP64
-  for (int64_t e = t; e < int64_t(d) * k; e += kT) {
-    const int r = static_cast<int>(e / k), j = static_cast<int>(e % k);
-    const int oj = order[j];
-    double s = 0.0;
-    for (int l = 0; l < k; ++l) s += static_cast<double>(Z[int64_t(r) * K + l]) * V[l * K + oj];
-    Zout[e] = s;
+  for (int e = t; e < K * K; e += kT) {
+    const int l = e / K, j = e % K;
+    Vo[e] = j < k ? V[l * K + order[j]] : 0.0;
   }
+}
+
+__global__ void ritz_rotate_kernel(const float* __restrict__ Z, const double* __restrict__ Vo, int d, int k, int K,
+                                   double* __restrict__ Zout) {
+  const int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (e >= int64_t(d) * k) return;
+  const int r = static_cast<int>(e / k), j = static_cast<int>(e % k);
+  double sum = 0.0;
+  for (int l = 0; l < k; ++l) sum += static_cast<double>(Z[int64_t(r) * K + l]) * Vo[l * K + j];
+  Zout[e] = sum;
 }
 
 }  // namespace
@@ -531,10 +573,24 @@ cudaError_t launch_aggregate(const float* Yl, const float* w, const float* G, in
 }
 
 cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, double n, double* Zout, double* sigma,
-                        int* status, cudaStream_t s) {
+                        double* scratch, int* status, cudaStream_t s) {
+  const int slices = (d + kRitzRows - 1) / kRitzRows;
+  double* Hpart = scratch;
+  double* Vo = scratch + size_t(slices) * K * K;
+  ritz_partial_kernel<<<slices, kT, 0, s>>>(Z, MZ, d, k, K, Hpart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const size_t sm = size_t(2) * K * K * 8 + size_t(K) * 8 + size_t(K) * 4 + 16;
-  ritz_kernel<<<1, kT, sm, s>>>(Z, MZ, d, k, K, n, Zout, sigma, status);
+  ritz_solve_kernel<<<1, kT, sm, s>>>(Hpart, slices, k, K, n, Vo, sigma, status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int64_t total = int64_t(d) * k;
+  ritz_rotate_kernel<<<static_cast<unsigned>((total + kT - 1) / kT), kT, 0, s>>>(Z, Vo, d, k, K, Zout);
   return cudaGetLastError();
+}
+
+size_t ritz_scratch_bytes(int d, int K) {
+  const int slices = (d + kRitzRows - 1) / kRitzRows;
+  return (size_t(slices) + 1) * K * K * 8;
 }
 
 }  // namespace lp

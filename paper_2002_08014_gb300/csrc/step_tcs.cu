@@ -479,7 +479,11 @@ bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan*
   if (planes != 1 && planes != 2) return false;
   const int K = k <= 8 ? 8 : (k <= 16 ? 16 : 32);
   const int N = 2 * K;
-  const int ncd_max = K == 32 ? 8 : 16;  // keeps the resident Z slice at <= 64 KB
+  // <= 64 KB of resident Z slice; with two planes at most 512 columns, so a
+  // tile's units (and with them the distance from a unit's first read to its L2
+  // re-read) stay at 256 KB per CTA
+  int ncd_max = K == 32 ? 8 : 16;
+  if (planes == 2 && ncd_max > 8) ncd_max = 8;
   int nc = (d + 63) / 64;
   nc += nc & 1;
   int cl = 1;

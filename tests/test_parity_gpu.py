@@ -414,10 +414,11 @@ def test_graph_replay_matches_eager_launches(gpu_lib, dtype):
     with B.LocalPower(stored, dtype=dtype) as lp:
         runs = []
         for sched, agg in [([3, 2, 1], "sign"), ([3, 2, 1], "sign"), ([2, 2], "opt"), ([3, 2, 1], "sign")]:
-            for flags in (B.LP_FLAG_RITZ | B.LP_FLAG_NO_GRAPH, B.LP_FLAG_RITZ, B.LP_FLAG_RITZ | B.LP_FLAG_TIMING):
+            for flags in (B.LP_FLAG_RITZ | B.LP_FLAG_NO_GRAPH | B.LP_FLAG_TIMING, B.LP_FLAG_RITZ,
+                          B.LP_FLAG_RITZ | B.LP_FLAG_TIMING):
                 B.lp_solve(lp.ctx, 8, sched, agg, Y0, 1, flags)
                 Z, sig, st = lp.result(8)
-                if flags & B.LP_FLAG_TIMING:   # step events recorded inside the graph
+                if flags & B.LP_FLAG_TIMING:   # step events recorded eagerly and inside the graph
                     assert st["ms_step_kernels"] > 0
                 runs.append((sched, agg, Z, sig, st))
     for i in range(0, len(runs), 3):
