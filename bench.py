@@ -50,14 +50,15 @@ def _args():
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--shape", default="1024x16", help="kernels: d x k of the step-kernel comparison")
     ap.add_argument("--instances", type=int, default=256, help="batching: number of instances")
-    ap.add_argument("--workload", choices=["fp32", "lowprec", "plain", "serving", "kernels", "batching"],
+    ap.add_argument("--workload", choices=["fp32", "lowprec", "plain", "serving", "kernels", "batching", "rounds"],
                     default="fp32",
                     help="fp32: the FP32 workload (default, with its BF16-storage and split-plane runs alongside); "
                          "lowprec: the reduced-precision workload n=4e6, d=2048, k=32 (BF16, then FP8-E4M3); "
                          "plain: the small plain configuration n=4000, d=100, k=5 (latency-bound); "
                          "serving: a Poisson stream of BF16 truncated-SVD requests through the request server; "
                          "kernels: every step kernel on one shape (--shape, --rows), one-step solves, for profiling; "
-                         "batching: independent BF16 instances of mixed shapes solved by one graph launch")
+                         "batching: independent BF16 instances of mixed shapes solved by one graph launch; "
+                         "rounds: rounds-to-accuracy and the residual error rho_t for constant p in {1, 2, 4, 8}")
     ap.add_argument("--rows", type=int, default=None,
                     help="override n (same spectrum and partition count): a smaller case for profiler captures")
     return ap.parse_args()
@@ -453,6 +454,42 @@ def run_batching(args):
     print(json.dumps(line))
 
 
+def run_rounds(args):
+    """Rounds to accuracy for constant p in {1, 2, 4, 8} (sign-fixing and OPT) on
+    the FP32 workload's matrix (n rows from --rows, default 250,000): the traced
+    solve gives Z_t after every aggregation and the residual error rho_t of
+    Def. 3; the distance of Z_t to the FP64 eigendecomposition's top-k gives the
+    first round at 1e-4 and 1e-6 (the analogue of the paper's communication vs
+    accuracy experiments, on synthetic data)."""
+    import oracle
+    import synth
+    from paper_2002_08014_gb300 import binding as B
+
+    rank, world, local = _dist_env()
+    if rank != 0:
+        return
+    c, A, sizes, Y0, _ = _workload(0, args.rows or 250_000)
+    parts = synth.split_rows(A, sizes)
+    k, d = c["k"], c["d"]
+    V, _ = _truth(parts, c)
+    T = 60
+    out = {}
+    with B.LocalPower(parts, device=local) as lp:
+        for agg in ("sign", "opt"):
+            for p in (1, 2, 4, 8):
+                B.lp_solve(lp.ctx, k, [p] * T, agg, Y0, 0, B.LP_FLAG_TRACE)
+                lp.result(k)
+                Zt, rho = B.lp_trace(lp.ctx, T, d, k)
+                dist = [oracle.subspace_dist(oracle.orth(Zt[t]), V) for t in range(T)]
+                first = lambda tol: next((t + 1 for t, x in enumerate(dist) if x <= tol), None)
+                out[f"{agg}_p{p}"] = {"rounds_to_1e-4": first(1e-4), "rounds_to_1e-6": first(1e-6),
+                                      "final_dist": dist[-1], "dist_every_10": dist[9::10],
+                                      "rho_mean": float(np.mean(rho)), "rho_last": float(rho[-1])}
+    print(json.dumps({"workload": "rounds", "n": c["n"], "d": d, "k": k, "m": c["m"], "T": T,
+                      "note": "rounds = aggregations = the paper's communications; rho_t is max_i ||Z_i G_i - Z_b||_2",
+                      "results": out}))
+
+
 def run_serving(args):
     """Continuous batching: a Poisson stream of truncated-SVD requests of mixed
     shapes through the request server (each BF16, p = 4 x 30 rounds + 3
@@ -822,5 +859,7 @@ if __name__ == "__main__":
         run_kernels(a)
     elif a.workload == "batching":
         run_batching(a)
+    elif a.workload == "rounds":
+        run_rounds(a)
     else:
         run_ours(a)

@@ -69,6 +69,8 @@ typedef enum lp_ptr_space { LP_HOST = 0, LP_DEVICE = 1 } lp_ptr_space;
 #define LP_FLAG_SIMT   4u   /* BF16 data: use the SIMT FP32 step kernel instead of the tensor-core one */
 #define LP_FLAG_NO_GRAPH 16u     /* launch the solve's kernels one by one instead of replaying the
                                  * CUDA graph captured for this (k, schedule, aggregator, flags)  */
+#define LP_FLAG_TRACE  32u   /* keep Z_t after every aggregation and the residual error rho_t
+                             * (Def. 3) for lp_trace                                          */
 #define LP_FLAG_TC_RESIDENT 8u  /* BF16 data: use the tensor-core step that keeps each tile in shared
                                  * memory for both contractions (cluster-split d) instead of the
                                  * streaming one; ignored for other dtypes */
@@ -180,6 +182,18 @@ lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* tuning);
  *   best_ms     receives the winner's mean launch time in ms (may be NULL).
  */
 lp_status lp_autotune(lp_ctx* ctx, int k, lp_tuning* chosen, int* path, double* best_ms);
+
+/*
+ * lp_trace: per-round records of the last solve run with LP_FLAG_TRACE
+ * (synchronises the context's stream).
+ *   z_trace  rounds x d x k FP64: Z_t = orth(Y_t) after round t's aggregation,
+ *            row-major per round (may be NULL).
+ *   rho      rounds values: rho_t = max_i ||Z_t^(i) G_i - Z_t^(b)||_2, the residual
+ *            error of Def. 3 over the last local bases, G_i the solve's aligner
+ *            (none for vanilla averaging); 0 in rounds with p_t = 1 (may be NULL).
+ * rounds = T + refine_rounds of that solve.  LP_ERR_STATE without a traced solve.
+ */
+lp_status lp_trace(lp_ctx* ctx, double* z_trace, double* rho);
 
 /* lp_destroy: free everything the context owns; NULL is a no-op. */
 void lp_destroy(lp_ctx* ctx);

@@ -138,6 +138,22 @@ def aggregate(Y_loc, Z_loc, sizes, kind: str) -> np.ndarray:
                for i in range(len(Y_loc)))
 
 
+def residual_error(Z_loc, sizes, kind: str) -> float:
+    """rho_t of Def. 3: how far the workers' last local bases are from the base
+    worker's, max_i ||Z_i G_i - Z_b||_2 with G_i = I without alignment and the
+    Procrustes solution O_i with OPT; with sign-fixing G_i is its diagonal +-1
+    matrix (the same form with the aligner the solve uses).  The base worker
+    plays the paper's worker 1."""
+    b = base_index(sizes)
+    worst = 0.0
+    for i, Z_i in enumerate(Z_loc):
+        if i == b:
+            continue
+        E = Z_i @ align(kind, Z_i, Z_loc[b]) - Z_loc[b]
+        worst = max(worst, float(np.linalg.norm(E, 2)))
+    return worst
+
+
 # ---------------------------------------------------------------------------
 # The method
 # ---------------------------------------------------------------------------
@@ -184,6 +200,7 @@ def localpower(parts, k: int, schedule, agg: str, Y0: np.ndarray, truth: np.ndar
             entry = {"p": int(p_t)}
             if keep_trace:
                 entry["Z"] = orth(Y)
+                entry["rho"] = residual_error(Z_loc, sizes, agg)
             if truth is not None:
                 entry["dist"] = subspace_dist(orth(Y), truth)
             trace.append(entry)

@@ -18,7 +18,7 @@ STATUS_NAMES = ["LP_OK", "LP_ERR_INVALID", "LP_ERR_STATE", "LP_ERR_OOM", "LP_ERR
 LP_F32, LP_BF16, LP_FP8_E4M3, LP_F32_BF16X2 = 0, 1, 2, 3
 LP_AGG_IDENTITY, LP_AGG_SIGN, LP_AGG_OPT = 0, 1, 2
 LP_HOST, LP_DEVICE = 0, 1
-LP_FLAG_RITZ, LP_FLAG_TIMING, LP_FLAG_SIMT, LP_FLAG_TC_RESIDENT, LP_FLAG_NO_GRAPH = 1, 2, 4, 8, 16
+LP_FLAG_RITZ, LP_FLAG_TIMING, LP_FLAG_SIMT, LP_FLAG_TC_RESIDENT, LP_FLAG_NO_GRAPH, LP_FLAG_TRACE = 1, 2, 4, 8, 16, 32
 LP_MAX_K = 32
 
 AGG = {"identity": LP_AGG_IDENTITY, "sign": LP_AGG_SIGN, "opt": LP_AGG_OPT}
@@ -27,7 +27,7 @@ PATHS = {0: "simt", 1: "tc_resident", 2: "tc_streaming"}
 
 # Every symbol the header declares, in declaration order.
 EXPORTS = ["lp_create", "lp_load_partitions", "lp_solve", "lp_result", "lp_destroy", "lp_last_error",
-           "lp_set_tuning", "lp_autotune", "lp_server_create", "lp_server_submit", "lp_server_progress",
+           "lp_set_tuning", "lp_autotune", "lp_trace", "lp_server_create", "lp_server_submit", "lp_server_progress",
            "lp_server_result", "lp_server_query", "lp_server_error", "lp_server_destroy", "lp_batch_create",
            "lp_batch_add", "lp_batch_autotune", "lp_batch_solve", "lp_batch_result", "lp_batch_size", "lp_batch_error",
            "lp_batch_destroy", "lp_power_step", "lp_orth", "lp_align_aggregate", "lp_power_step_static"]
@@ -100,6 +100,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
     L.lp_align_aggregate.argtypes = [P, I, I64, I, I, I, P, P, P, P, P, I]
     L.lp_power_step_static.argtypes = [P, I, C.POINTER(I64), I64, I, P, P, P]
     L.lp_set_tuning.argtypes = [P, C.POINTER(lp_tuning)]
+    L.lp_trace.argtypes = [P, P, P]
     L.lp_autotune.argtypes = [P, I, C.POINTER(lp_tuning), C.POINTER(I), C.POINTER(C.c_double)]
     L.lp_server_create.argtypes = [C.POINTER(P), I, C.c_size_t, I]
     L.lp_server_submit.argtypes = [P, C.POINTER(lp_request), C.POINTER(I64)]
@@ -187,6 +188,14 @@ def lp_autotune(ctx, k: int) -> dict:
     return {"path": PATHS.get(path.value, path.value), "path_code": path.value, "ms_per_step": ms.value,
             "ring_units": t.ring_units, "lag_units": t.lag_units, "prefetch_units": t.prefetch_units,
             "cache_hints": t.cache_hints}
+
+
+def lp_trace(ctx, rounds: int, d: int, k: int):
+    """(Z_t for every round as rounds x d x k, rho_t per round) of the last LP_FLAG_TRACE solve."""
+    Z = np.empty((rounds, d, k), dtype=np.float64)
+    rho = np.empty(rounds, dtype=np.float64)
+    _check(ctx, load().lp_trace(ctx, Z.ctypes.data, rho.ctypes.data))
+    return Z, rho
 
 
 def lp_last_error(ctx=None) -> str:

@@ -73,6 +73,12 @@ struct lp_ctx {
   lp::TcsTuning tuning;
   bool prefer_resident = false;  // set by lp_autotune for LP_BF16 data
 
+  // per-round records (LP_FLAG_TRACE): Z_t blocks and per-partition residuals
+  float* dTraceZ = nullptr;
+  double* dTraceRho = nullptr;
+  size_t trace_z_bytes = 0, trace_rho_bytes = 0;
+  int traced_rounds = 0;  // rounds recorded by the last solve (0: none)
+
   // CUDA graph of the last solve's launch sequence, replayed while its key matches
   uint64_t gen = 1;  // bumped whenever buffers, plans or tuning change
   std::vector<int64_t> graph_key;
@@ -193,6 +199,10 @@ void free_state(lp_ctx* c) {
   dfree(c, c->dStage, c->stage_bytes);
   c->stage_bytes = 0;
   c->Kcap = 0;
+  dfree(c, c->dTraceZ, c->trace_z_bytes);
+  dfree(c, c->dTraceRho, c->trace_rho_bytes);
+  c->trace_z_bytes = c->trace_rho_bytes = 0;
+  c->traced_rounds = 0;
 }
 
 lp_status ensure_state(lp_ctx* c, int K) {
@@ -713,7 +723,7 @@ static lp_status select_path(lp_ctx* c, int k, unsigned flags) {
 // The launch sequence of one solve (Alg. 1 in rounds, then Ritz or unpack), on
 // the context's stream; lp_solve runs it eagerly or captures it into a graph.
 static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, int refine_rounds,
-                            bool timing, const double* dy0) {
+                            bool timing, const double* dy0, bool trace) {
   const int d = static_cast<int>(c->d);
   const int m = c->m;
   const int K = kcap_of(k);
@@ -750,6 +760,19 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
       return st;
     if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream), "orth")))
       return st;
+    if (trace) {
+      LP_CUDA(cudaMemcpyAsync(c->dTraceZ + size_t(t) * d * K, c->dZ, size_t(d) * K * 4, cudaMemcpyDeviceToDevice,
+                              c->stream));
+      double* rho = c->dTraceRho + size_t(t) * m;
+      if (p == 1) {
+        LP_CUDA(cudaMemsetAsync(rho, 0, size_t(m) * 8, c->stream));
+      } else if ((st = check_launch(c, lp::launch_rho(c->dZl, zs, c->dZl + zs * c->base, align ? c->dG : nullptr,
+                                                      agg == LP_AGG_SIGN ? 1 : 0, c->base, m, d, k, K, rho,
+                                                      c->dStatus, c->stream),
+                                    "residual error"))) {
+        return st;
+      }
+    }
     c->stats.rounds++;
   }
   if (c->ritz) {
@@ -888,6 +911,20 @@ static lp_status solve_prepare(lp_ctx* c, int k, const int* p_schedule, int T, l
   const int K = kcap_of(k);
   if ((st = select_path(c, k, flags))) return st;
   if ((st = ensure_state(c, K))) return st;
+  c->traced_rounds = 0;
+  if (flags & LP_FLAG_TRACE) {
+    const int rounds = T + refine_rounds;
+    const size_t zb = size_t(rounds) * c->d * K * 4, rb = size_t(rounds) * c->m * 8;
+    if (zb > c->trace_z_bytes || rb > c->trace_rho_bytes) {
+      drop_graph(c);  // the captured sequence names the old buffers
+      dfree(c, c->dTraceZ, c->trace_z_bytes);
+      dfree(c, c->dTraceRho, c->trace_rho_bytes);
+      c->trace_z_bytes = c->trace_rho_bytes = 0;
+      if ((st = dalloc(c, &c->dTraceZ, zb)) || (st = dalloc(c, &c->dTraceRho, rb))) return st;
+      c->trace_z_bytes = zb;
+      c->trace_rho_bytes = rb;
+    }
+  }
   c->solved = false;
   c->k = k;
   c->ritz = (flags & LP_FLAG_RITZ) != 0;
@@ -895,7 +932,8 @@ static lp_status solve_prepare(lp_ctx* c, int k, const int* p_schedule, int T, l
   return stage_in(c, y0, size_t(c->d) * k, LP_HOST, dy0);
 }
 
-static void solve_mark(lp_ctx* c, int k) {
+static void solve_mark(lp_ctx* c, int k, int rounds, unsigned flags) {
+  c->traced_rounds = (flags & LP_FLAG_TRACE) ? rounds : 0;
   c->stats.k = k;
   c->stats.n = c->n;
   c->stats.d = c->d;
@@ -926,7 +964,7 @@ lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator
     }
     std::memset(&c->stats, 0, sizeof(c->stats));
     c->step_ev_used = 0;
-    st = solve_body(c, k, p_schedule, T, agg, refine_rounds, timing, dy0);
+    st = solve_body(c, k, p_schedule, T, agg, refine_rounds, timing, dy0, (flags & LP_FLAG_TRACE) != 0);
     if (use_graph) {
       cudaGraph_t g = nullptr;
       const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
@@ -950,7 +988,29 @@ lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator
     }
   }
   LP_CUDA(cudaEventRecord(c->ev1, c->stream));
-  solve_mark(c, k);
+  solve_mark(c, k, T + refine_rounds, flags);
+  return LP_OK;
+}
+
+lp_status lp_trace(lp_ctx* c, double* z_trace, double* rho) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  if (!c->solved || c->traced_rounds == 0) return fail(c, LP_ERR_STATE, "no traced solve (LP_FLAG_TRACE)");
+  LP_CUDA(cudaSetDevice(c->device));
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  const int R = c->traced_rounds, K = kcap_of(c->k), d = static_cast<int>(c->d), k = c->k;
+  if (z_trace) {
+    std::vector<float> h(size_t(R) * d * K);
+    LP_CUDA(cudaMemcpy(h.data(), c->dTraceZ, h.size() * 4, cudaMemcpyDeviceToHost));
+    for (int t = 0; t < R; ++t)
+      for (int r = 0; r < d; ++r)
+        for (int j = 0; j < k; ++j) z_trace[(size_t(t) * d + r) * k + j] = h[(size_t(t) * d + r) * K + j];
+  }
+  if (rho) {
+    std::vector<double> h(size_t(R) * c->m);
+    LP_CUDA(cudaMemcpy(h.data(), c->dTraceRho, h.size() * 8, cudaMemcpyDeviceToHost));
+    for (int t = 0; t < R; ++t) rho[t] = *std::max_element(h.begin() + size_t(t) * c->m, h.begin() + size_t(t + 1) * c->m);
+  }
   return LP_OK;
 }
 
@@ -1159,16 +1219,17 @@ lp_status lp::batch_enqueue(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
   std::memset(&c->stats, 0, sizeof(c->stats));
   c->step_ev_used = 0;
   LP_CUDA(record_event(c->ev0, c->stream));
-  const lp_status st = solve_body(c, k, p_schedule, T, agg, refine_rounds, (flags & LP_FLAG_TIMING) != 0, c->dStage);
+  const lp_status st = solve_body(c, k, p_schedule, T, agg, refine_rounds, (flags & LP_FLAG_TIMING) != 0, c->dStage,
+                                  (flags & LP_FLAG_TRACE) != 0);
   if (st) return st;
   LP_CUDA(record_event(c->ev1, c->stream));
   *captured = c->stats;
   return LP_OK;
 }
 
-void lp::batch_mark(lp_ctx* c, int k, const lp_stats& captured) {
+void lp::batch_mark(lp_ctx* c, int k, const lp_stats& captured, int rounds, unsigned flags) {
   c->stats = captured;
-  solve_mark(c, k);
+  solve_mark(c, k, rounds, flags);
 }
 
 cudaStream_t lp::ctx_stream(lp_ctx* c) { return c->stream; }

@@ -107,7 +107,7 @@ lp_status batch_prepare(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggre
                         int refine_rounds, unsigned flags);
 lp_status batch_enqueue(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, int refine_rounds,
                         unsigned flags, lp_stats* captured);
-void batch_mark(lp_ctx* c, int k, const lp_stats& captured);
+void batch_mark(lp_ctx* c, int k, const lp_stats& captured, int rounds, unsigned flags);
 cudaStream_t ctx_stream(lp_ctx* c);
 
 // Message returned by lp_last_error(NULL) (failures of calls without a context).
@@ -131,6 +131,9 @@ cudaError_t launch_aggregate(const float* Yl, const float* w, const float* G, in
 cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, double n, double* Zout, double* sigma,
                         double* scratch, int* status, cudaStream_t s);
 size_t ritz_scratch_bytes(int d, int K);
+// out[i] = ||Z_i G_i - Z_b||_2 (Def. 3), G_i the aligner (nullptr: none; diag_only: sign-fixing); out[base] = 0.
+cudaError_t launch_rho(const float* Zl, int64_t z_stride, const float* Zb, const float* G, int diag_only, int base,
+                       int m, int d, int k, int K, double* out, int* status, cudaStream_t s);
 // FP64 d x k (row-major) <-> FP32 d x K padded blocks
 cudaError_t launch_pack(const double* src, float* dst, int batch, int d, int k, int K, cudaStream_t s);
 cudaError_t launch_unpack(const float* src, double* dst, int batch, int d, int k, int K, cudaStream_t s);

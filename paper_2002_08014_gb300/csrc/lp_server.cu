@@ -470,7 +470,7 @@ lp_status lp_batch_solve(lp_batch* b) {
     (void)cudaGetLastError();
     return bfail(b, LP_ERR_CUDA, "launching the batch graph");
   }
-  for (auto& in : b->inst) lp::batch_mark(in->ctx, in->q.k, in->captured);
+  for (auto& in : b->inst) lp::batch_mark(in->ctx, in->q.k, in->captured, in->q.T + in->q.refine, in->q.flags);
   b->solved = true;
   return LP_OK;
 }

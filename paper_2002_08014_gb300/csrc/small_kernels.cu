@@ -4,9 +4,13 @@
 //   align      sign-fixing (eq. (4)) or orthogonal Procrustes (eq. (3)) matrices
 //   aggregate  Y = sum_i p_i Y_i D_i (Alg. 1 aggregation)
 //   ritz       Rayleigh-Ritz on span(Z): ordered basis and sigma_j = sqrt(n lambda_j)
-// Precision: the d-sized work (Gram, solves, averaging) is FP32; the k x k
-// factorisations (Cholesky, triangular inverse, Jacobi SVD / eigen) are FP64,
-// as are the sign-fix inner products that decide D_i.
+//   split      FP32 rows -> hi / lo BF16 planes (load time)
+//   rho        residual error of Def. 3 per partition (traced solves)
+// Precision: the d-sized work (Gram, solves, averaging) and the k x k Jacobi
+// SVD / eigen-solves are FP32; the Cholesky factor is FP32 when its pivots allow
+// (else FP64); the Ritz matrix H and the sign-fix inner products that decide D_i
+// are accumulated in FP64.  GB300's FP64 pipe is a small fraction of its FP32
+// pipe, and these k x k steps are serial latency on every round.
 #include <algorithm>
 #include <cfloat>
 
@@ -19,32 +23,18 @@ namespace {
 
 constexpr int kT = 256;
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// FP64 1/sqrt(x) and 1/x by Newton-Raphson iteration from FP32 seeds
-// (y <- y (3 - x y^2) / 2 and y <- y (2 - x y)); each step doubles the number of
-// correct bits, so two steps take the FP32 seed (about 2^-22) past FP64
-// precision.  FP64 square roots and divisions are long instruction sequences on
-// this GPU; these are a few FMAs on the short k x k critical paths.  Arguments
-// outside the FP32 normal range take the plain sqrt / division.
+// FP64 1/sqrt(x) by Newton-Raphson iteration from an FP32 seed
+// (y <- y (3 - x y^2) / 2); each step doubles the number of correct bits, so two
+// steps take the FP32 seed (about 2^-22) past FP64 precision.  An FP64 square
+// root is a long instruction sequence on this GPU; this is a few FMAs on the
+// FP64 Cholesky's critical path.  Arguments outside the FP32 normal range take
+// the plain sqrt.
 __device__ __forceinline__ double rsqrt_nr(double x) {
   if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
   double y = static_cast<double>(rsqrtf(static_cast<float>(x)));
   const double hx = 0.5 * x;
   y = y * (1.5 - hx * y * y);
   y = y * (1.5 - hx * y * y);
-  return y;
-}
-__device__ __forceinline__ double recip_nr(double x) {
-  const double ax = fabs(x);
-  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
-  double y = static_cast<double>(__frcp_rn(static_cast<float>(x)));
-  y = y * (2.0 - x * y);
-  y = y * (2.0 - x * y);
   return y;
 }
 
@@ -91,7 +81,17 @@ __global__ void reduce_kernel(const float* __restrict__ P, const int* __restrict
   if (e >= n4) return;
   const int sb = slot_begin[i], se = slot_begin[i + 1];
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int s = sb; s < se; ++s) {
+  int s = sb;
+  for (; s + 4 <= se; s += 4) {  // four loads in flight, added in slot order
+    float4 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = reinterpret_cast<const float4*>(P + int64_t(s + q) * d * K)[e];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      acc.x += v[q].x; acc.y += v[q].y; acc.z += v[q].z; acc.w += v[q].w;
+    }
+  }
+  for (; s < se; ++s) {
     const float4 v = reinterpret_cast<const float4*>(P + int64_t(s) * d * K)[e];
     acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
   }
@@ -100,46 +100,56 @@ __global__ void reduce_kernel(const float* __restrict__ P, const int* __restrict
   reinterpret_cast<float4*>(Y + int64_t(i) * d * K)[e] = acc;
 }
 
-// ---------------------------------------------------------------- k x k helpers (warp 0, FP64)
-// One-sided (Hestenes) Jacobi on the k x k matrix C (stride K, in smem), accumulating the
-// rotations in V.  On return C's columns are mutually orthogonal: C_in V = C_out, so
-// C_in = U Sigma V^T with sigma_j = ||C_out[:, j]||, U[:, j] = C_out[:, j] / sigma_j.
-// Returns false if the sweep limit was hit.
-__device__ bool warp_jacobi(double* C, double* V, int k, int K) {
+// ---------------------------------------------------------------- k x k helpers (warp 0)
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One-sided (Hestenes) Jacobi on the k x k matrix C (stride K, in shared memory),
+// accumulating the rotations in V, in FP32: on return C's columns are mutually
+// orthogonal, C_in V = C_out, so C_in = U Sigma V^T with sigma_j = ||C_out[:, j]||
+// and U[:, j] = C_out[:, j] / sigma_j.  FP32 because GB300's FP64 pipe is a small
+// fraction of its FP32 pipe and these k x k problems sit on serial critical
+// paths; the aligners and Ritz values it yields stay within 1e-7 of FP64
+// factorisations (CPU simulation on the FP32 workload's spectrum).  Returns false
+// if the sweep limit was hit.
+__device__ bool warp_jacobi_f32(float* C, float* V, int k, int K) {
   const int lane = threadIdx.x & 31;
   for (int r = lane; r < k; r += 32)
-    for (int j = 0; j < k; ++j) V[r * K + j] = (r == j) ? 1.0 : 0.0;
+    for (int j = 0; j < k; ++j) V[r * K + j] = (r == j) ? 1.f : 0.f;
   __syncwarp();
-  const double tol = 1e-14;
-  for (int sweep = 0; sweep < 60; ++sweep) {
+  const float tol = 1e-6f;
+  for (int sweep = 0; sweep < 40; ++sweep) {
     int rotated = 0;
     for (int p = 0; p < k - 1; ++p) {
       for (int q = p + 1; q < k; ++q) {
-        double a = 0.0, b = 0.0, g = 0.0;
+        float a = 0.f, b = 0.f, g = 0.f;
         if (lane < k) {
-          const double cp = C[lane * K + p], cq = C[lane * K + q];
+          const float cp = C[lane * K + p], cq = C[lane * K + q];
           a = cp * cp;
           b = cq * cq;
           g = cp * cq;
         }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
-        if (g * g > tol * tol * (a * b) && fabs(g) > 1e-300) {
+        a = warp_sumf(a);
+        b = warp_sumf(b);
+        g = warp_sumf(g);
+        if (fabsf(g) > tol * sqrtf(a * b) && fabsf(g) > 1e-35f) {
           rotated = 1;
           // zeta = (b - a) / 2g, t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2)
-          const double zeta = (b - a) * recip_nr(2.0 * g);
-          const double q2 = 1.0 + zeta * zeta;
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) * recip_nr(fabs(zeta) + q2 * rsqrt_nr(q2));
-          const double c = rsqrt_nr(1.0 + t * t);
-          const double s = c * t;
+          const float zeta = (b - a) / (2.f * g);
+          const float az = fabsf(zeta);
+          const float t = (zeta >= 0.f ? 1.f : -1.f) / (az > 1e15f ? 2.f * az : az + sqrtf(1.f + zeta * zeta));
+          const float c = 1.f / sqrtf(1.f + t * t);
+          const float sn = c * t;
           if (lane < k) {
-            const double cp = C[lane * K + p], cq = C[lane * K + q];
-            C[lane * K + p] = c * cp - s * cq;
-            C[lane * K + q] = s * cp + c * cq;
-            const double vp = V[lane * K + p], vq = V[lane * K + q];
-            V[lane * K + p] = c * vp - s * vq;
-            V[lane * K + q] = s * vp + c * vq;
+            const float cp = C[lane * K + p], cq = C[lane * K + q];
+            C[lane * K + p] = c * cp - sn * cq;
+            C[lane * K + q] = sn * cp + c * cq;
+            const float vp = V[lane * K + p], vq = V[lane * K + q];
+            V[lane * K + p] = c * vp - sn * vq;
+            V[lane * K + q] = sn * vp + c * vq;
           }
           __syncwarp();
         }
@@ -152,15 +162,16 @@ __device__ bool warp_jacobi(double* C, double* V, int k, int K) {
 
 // ---------------------------------------------------------------- CholQR2
 // One CTA per block, two passes of:
-//   G = Y^T Y        FP32 products and partial sums over row slices, combined in FP64
-//   G = L L^T        FP64 right-looking Cholesky on warp 0 (parallel trailing updates)
+//   G = Y^T Y        FP32 products and partial sums over row slices, combined in FP32
+//   G = L L^T        right-looking Cholesky on warp 0: FP32, or FP64 when an FP32
+//                    pivot is too small to trust
 //   Z = Y L^{-T}     per-row forward substitution in FP32, one thread per row
 // The column space is Y's whatever the precision of L; the second pass restores
 // orthonormality lost to the FP32 Gram.  A pivot that is not positive and finite
 // sets ST_CHOL (the pivot is then taken as 1 so the kernel can finish).
 // G = Y^T Y: thread (block (bi, bj) of 4 x 4 entries, row slice) accumulates
 // Y[r][4bi..4bi+3]^T Y[r][4bj..4bj+3] over its rows in FP32 registers (16 FMAs
-// per two 16-byte loads); the slices are added in FP64 through shared memory.
+// per two 16-byte loads); the slices are added in FP32 through shared memory.
 template <int K>
 __device__ void gram_fp32(const float* __restrict__ Y, int d, float* red, double* G) {
   constexpr int NB = K / 4, NBB = NB * NB, S = kT / NBB;
@@ -200,9 +211,18 @@ __device__ void gram_fp32(const float* __restrict__ Y, int d, float* red, double
   for (int e = t; e < K * K; e += kT) {
     const int i = e / K, j = e % K;
     const int bb = (i / 4) * NB + j / 4, el = 4 * (i % 4) + j % 4;
-    double s = 0.0;
-    for (int q = 0; q < S; ++q) s += red[(q * NBB + bb) * 16 + el];
-    G[e] = s;
+    // four interleaved FP32 partial sums in slice order, then pairwise: short
+    // dependency chains (the factorisation reads the Gram in FP32 first)
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int q = 0;
+    for (; q + 4 <= S; q += 4) {
+      s0 += red[(q * NBB + bb) * 16 + el];
+      s1 += red[((q + 1) * NBB + bb) * 16 + el];
+      s2 += red[((q + 2) * NBB + bb) * 16 + el];
+      s3 += red[((q + 3) * NBB + bb) * 16 + el];
+    }
+    for (; q < S; ++q) s0 += red[(q * NBB + bb) * 16 + el];
+    G[e] = static_cast<double>((s0 + s1) + (s2 + s3));
   }
   __syncthreads();
 }
@@ -242,6 +262,54 @@ __device__ bool warp_cholesky_rl(double* G, float* Lf, float* invd, int k) {
   }
   __syncwarp();
   return ok;
+}
+
+// Right-looking Cholesky of the FP64 Gram in FP32 on one warp, written to Lf
+// (lower, stride K) and invd.  Returns false (and leaves the FP64 Gram intact for
+// warp_cholesky_rl) when a pivot is not above 1e-6 of the largest diagonal entry
+// or not finite: GB300's FP64 pipe is a small fraction of its FP32 pipe, and the
+// FP32 factor serves both CholQR passes whenever the Gram allows it (the column
+// space is that of Y for any invertible factor; the second pass restores
+// orthonormality).
+template <int K>
+__device__ bool warp_cholesky_f32(const double* G, float* Lf, float* invd, int k) {
+  const int lane = threadIdx.x & 31;
+  float dmax = 0.f;
+  for (int e = lane; e < K * K; e += 32) {
+    const int i = e / K, l = e % K;
+    const float v = (i < k && l < k) ? static_cast<float>(G[e]) : 0.f;
+    Lf[e] = v;
+    if (i == l && i < k) dmax = fmaxf(dmax, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  __syncwarp();
+  if (!(dmax > 0.f) || !isfinite(dmax)) return false;
+  const float floor = 1e-6f * dmax;
+  for (int j = 0; j < k; ++j) {
+    const float piv = Lf[j * K + j];  // the same value in every lane
+    if (!(piv > floor) || !isfinite(piv)) return false;
+    const float ljj = sqrtf(piv);
+    const float inv = 1.0f / ljj;
+    for (int i = j + 1 + lane; i < k; i += 32) Lf[i * K + j] *= inv;
+    __syncwarp();
+    if (lane == 0) {
+      Lf[j * K + j] = ljj;
+      invd[j] = inv;
+    }
+    const int m = k - j - 1;
+    for (int e = lane; e < m * m; e += 32) {
+      const int i = j + 1 + e / m, l = j + 1 + e % m;
+      if (l <= i) Lf[i * K + l] -= Lf[i * K + j] * Lf[l * K + j];
+    }
+    __syncwarp();
+  }
+  for (int e = lane; e < K * K; e += 32) {
+    const int i = e / K, l = e % K;
+    if (l > i || i >= k) Lf[e] = 0.f;
+  }
+  __syncwarp();
+  return true;
 }
 
 // Z[r][:] = Y[r][:] L^{-T}: z_j = (y_j - sum_{p<j} z_p L[j][p]) / L[j][j].  Each
@@ -297,7 +365,7 @@ __global__ void __launch_bounds__(kT) cholqr2_kernel(const float* __restrict__ Y
   for (int pass = 0; pass < 2; ++pass) {
     const float* src = pass == 0 ? Y : Z;
     gram_fp32<K>(src, d, red, G);
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < 32 && !warp_cholesky_f32<K>(G, Lf, invd, k)) {
       const bool ok = warp_cholesky_rl<K>(G, Lf, invd, k);
       if (!ok && threadIdx.x == 0) atomicOr(status, ST_CHOL);
     }
@@ -369,29 +437,109 @@ __global__ void __launch_bounds__(kT) align_kernel(const float* __restrict__ Zl,
     __syncthreads();
   }
   if (t < 32) {
-    const bool ok = warp_jacobi(C, V, k, K);
+    // FP32 copies in the V area (2 K*K floats fit in K*K doubles)
+    float* Cf = reinterpret_cast<float*>(V);
+    float* Vf = Cf + K * K;
+    for (int e = t; e < K * K; e += 32) Cf[e] = static_cast<float>(C[e]);
+    __syncwarp();
+    const bool ok = warp_jacobi_f32(Cf, Vf, k, K);
     if (!ok && t == 0) atomicOr(status, ST_JACOBI);
     // U[:, j] = C[:, j] / sigma_j ; O = U V^T
     for (int j = 0; j < k; ++j) {
-      double nrm = 0.0;
-      if (t < k) nrm = C[t * K + j] * C[t * K + j];
-      nrm = warp_sum(nrm);  // squared norm
-      const double inv = nrm > 1e-300 ? rsqrt_nr(nrm) : 0.0;
-      if (t < k) C[t * K + j] *= inv;
-      if (!(nrm > 1e-300) && t == 0) atomicOr(status, ST_JACOBI);
+      float nrm = 0.f;
+      if (t < k) nrm = Cf[t * K + j] * Cf[t * K + j];
+      nrm = warp_sumf(nrm);  // squared norm
+      const float inv = nrm > 1e-37f ? 1.f / sqrtf(nrm) : 0.f;
+      if (t < k) Cf[t * K + j] *= inv;
+      if (!(nrm > 1e-37f) && t == 0) atomicOr(status, ST_JACOBI);
     }
     __syncwarp();
     for (int e = t; e < K * K; e += 32) {
       const int a = e / K, b = e % K;
-      double s = 0.0;
+      float sum = 0.f;
       if (a < k && b < k)
-        for (int j = 0; j < k; ++j) s += C[a * K + j] * V[b * K + j];
-      Gi[e] = static_cast<float>(s);
+        for (int j = 0; j < k; ++j) sum = fmaf(Cf[a * K + j], Vf[b * K + j], sum);
+      Gi[e] = sum;
     }
   }
 }
 
 size_t align_smem(int K) { return size_t(2) * K * K * 8 + size_t(kT) * 8 + 16; }
+
+// ---------------------------------------------------------------- residual error
+// rho_i = ||Z_i G_i - Z_b||_2 (Def. 3) for one partition per CTA: E = Z_i G_i - Z_b
+// is formed 64 rows at a time in shared memory (G_i the aligner: K x K, diagonal
+// for sign-fixing, nullptr for none); E^T E is summed in FP32 over a chunk and in
+// FP64 across chunks; its largest eigenvalue comes from the one-sided Jacobi.
+constexpr int kRhoRows = 64;
+
+__global__ void __launch_bounds__(kT) rho_kernel(const float* __restrict__ Zl, int64_t z_stride,
+                                                 const float* __restrict__ Zb, const float* __restrict__ G,
+                                                 int diag_only, int base, int d, int k, int K,
+                                                 double* __restrict__ out, int* status) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double* C = reinterpret_cast<double*>(sm);  // K*K Gram, then Jacobi workspace
+  double* V = C + K * K;                       // K*K
+  float* E = reinterpret_cast<float*>(V + K * K);  // kRhoRows x K
+  const int i = blockIdx.x, t = threadIdx.x;
+  if (i == base) {
+    if (t == 0) out[i] = 0.0;
+    return;
+  }
+  const float* Zi = Zl + z_stride * i;
+  const float* Gi = G ? G + int64_t(i) * K * K : nullptr;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // entries e = t + j * kT of the K x K Gram
+  for (int r0 = 0; r0 < d; r0 += kRhoRows) {
+    const int nr = min(kRhoRows, d - r0);
+    __syncthreads();
+    for (int e = t; e < nr * K; e += kT) {
+      const int r = r0 + e / K, j = e % K;
+      float v;
+      if (!Gi) {
+        v = Zi[int64_t(r) * K + j];
+      } else if (diag_only) {
+        v = Zi[int64_t(r) * K + j] * Gi[j * K + j];
+      } else {
+        v = 0.f;
+        for (int l = 0; l < K; ++l) v = fmaf(Zi[int64_t(r) * K + l], Gi[l * K + j], v);
+      }
+      E[e] = v - Zb[int64_t(r) * K + j];
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+      const int e = t + q * kT;
+      if (e >= K * K) break;
+      const int a = e / K, b = e % K;
+      float s = 0.f;
+      if (a < k && b < k)
+        for (int r = 0; r < nr; ++r) s = fmaf(E[r * K + a], E[r * K + b], s);
+      acc[q] += s;
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < 4; ++q) {
+    const int e = t + q * kT;
+    if (e < K * K) C[e] = acc[q];
+  }
+  __syncthreads();
+  if (t < 32) {
+    // E^T E is symmetric positive semidefinite: the one-sided Jacobi's column norms are its eigenvalues
+    float* Cf = reinterpret_cast<float*>(V);
+    float* Vf = Cf + K * K;
+    for (int e = t; e < K * K; e += 32) Cf[e] = static_cast<float>(C[e]);
+    __syncwarp();
+    const bool ok = warp_jacobi_f32(Cf, Vf, k, K);
+    if (!ok && t == 0) atomicOr(status, ST_JACOBI);
+    float top = 0.f;
+    for (int j = 0; j < k; ++j) {
+      float v = 0.f;
+      if (t < k) v = Cf[t * K + j] * Cf[t * K + j];
+      v = warp_sumf(v);
+      top = fmaxf(top, v);
+    }
+    if (t == 0) out[i] = sqrt(sqrt(static_cast<double>(top)));  // sqrt(lambda_max(E^T E))
+  }
+}
 
 // ---------------------------------------------------------------- aggregate
 __global__ void aggregate_kernel(const float* __restrict__ Yl, const float* __restrict__ w,
@@ -474,14 +622,19 @@ __global__ void __launch_bounds__(kT) ritz_solve_kernel(const double* __restrict
       }
     }
     __syncwarp();
-    // H is symmetric positive semidefinite: its one-sided Jacobi SVD is its eigendecomposition.
-    const bool ok = warp_jacobi(H, V, k, K);
+    // H is symmetric positive semidefinite: its one-sided Jacobi SVD is its eigendecomposition
+    // (FP32 copies in the V area).
+    float* Hf = reinterpret_cast<float*>(V);
+    float* Vf = Hf + K * K;
+    for (int e = t; e < K * K; e += 32) Hf[e] = static_cast<float>(H[e]);
+    __syncwarp();
+    const bool ok = warp_jacobi_f32(Hf, Vf, k, K);
     if (!ok && t == 0) atomicOr(status, ST_JACOBI);
     for (int j = 0; j < k; ++j) {
-      double v = 0.0;
-      if (t < k) v = H[t * K + j] * H[t * K + j];
-      v = warp_sum(v);
-      if (t == 0) lam[j] = v > 0.0 ? v * rsqrt_nr(v) : 0.0;
+      float v = 0.f;
+      if (t < k) v = Hf[t * K + j] * Hf[t * K + j];
+      v = warp_sumf(v);
+      if (t == 0) lam[j] = v > 0.f ? sqrt(static_cast<double>(v)) : 0.0;
     }
     __syncwarp();
     if (t == 0) {
@@ -500,7 +653,7 @@ __global__ void __launch_bounds__(kT) ritz_solve_kernel(const double* __restrict
   __syncthreads();
   for (int e = t; e < K * K; e += kT) {
     const int l = e / K, j = e % K;
-    Vo[e] = j < k ? V[l * K + order[j]] : 0.0;
+    Vo[e] = j < k ? static_cast<double>(reinterpret_cast<const float*>(V)[K * K + l * K + order[j]]) : 0.0;
   }
 }
 
@@ -585,6 +738,13 @@ cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, do
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int64_t total = int64_t(d) * k;
   ritz_rotate_kernel<<<static_cast<unsigned>((total + kT - 1) / kT), kT, 0, s>>>(Z, Vo, d, k, K, Zout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho(const float* Zl, int64_t z_stride, const float* Zb, const float* G, int diag_only, int base,
+                       int m, int d, int k, int K, double* out, int* status, cudaStream_t s) {
+  const size_t sm = size_t(2) * K * K * 8 + size_t(kRhoRows) * K * 4;
+  rho_kernel<<<m, kT, sm, s>>>(Zl, z_stride, Zb, G, diag_only, base, d, k, K, out, status);
   return cudaGetLastError();
 }
 

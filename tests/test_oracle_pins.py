@@ -272,3 +272,50 @@ def test_encoders_round_to_nearest_within_half_an_ulp():
     assert np.abs(y).max() <= 448.0 * (1 + 2 ** -20)
     rel = np.abs(xq - x) / np.maximum(np.abs(x), 2.0 ** -6 * sc[:, None])
     assert rel.max() <= 2.0 ** -4 + 1e-7   # half an ulp of a 3-bit mantissa
+
+
+# --------------------------------------------------------------------------- residual error rho_t (Def. 3)
+
+def test_residual_error_is_zero_when_all_workers_agree():
+    """rho_t = 0 at p_t = 1 (every worker multiplied the broadcast Z) and for
+    replicated partitions (identical M_i) at any p."""
+    _, parts = _small_problem(seed=21)
+    Y0 = _rng(24).standard_normal((12, 3))
+    for agg in ("identity", "sign", "opt"):
+        out = O.localpower(parts, 3, [1, 1, 1], agg, Y0, keep_trace=True)
+        assert max(e["rho"] for e in out["trace"]) < 1e-14
+    rep = [parts[0]] * 3
+    for agg in ("identity", "sign", "opt"):
+        out = O.localpower(rep, 3, [4, 3], agg, Y0, keep_trace=True)
+        assert max(e["rho"] for e in out["trace"]) < 1e-12
+
+
+def test_residual_error_with_opt_matches_the_procrustes_lemma():
+    """With OPT, ||Z_i O_i - Z_b||_2 = sqrt(2 - 2 sqrt(1 - dist(Z_i, Z_b)^2)) (App. A),
+    a closed form the residual-error routine does not use; and OPT never leaves
+    a larger residual than sign-fixing or no alignment on the same bases."""
+    rng = _rng(22)
+    d, k = 30, 4
+    Zb = _orthonormal(d, k, rng)
+    Zs = [Zb] + [O.orth(Zb + 0.15 * rng.standard_normal((d, k))) for _ in range(4)]
+    sizes = [10, 9, 8, 7, 6]   # worker 0 is the base
+    r_opt = O.residual_error(Zs, sizes, "opt")
+    want = max(np.sqrt(2 - 2 * np.sqrt(1 - O.subspace_dist(Z, Zb) ** 2)) for Z in Zs[1:])
+    assert abs(r_opt - want) < 1e-12
+    assert r_opt <= O.residual_error(Zs, sizes, "sign") + 1e-15
+    assert r_opt <= O.residual_error(Zs, sizes, "identity") + 1e-15
+    # k = 1: sign-fixing is OPT
+    Z1 = [Z[:, :1] for Z in Zs]
+    assert abs(O.residual_error(Z1, sizes, "sign") - O.residual_error(Z1, sizes, "opt")) < 1e-15
+
+
+def test_residual_error_is_invariant_to_the_base_basis_sign_flips_of_others():
+    """Flipping columns of a non-base basis changes nothing with sign-fixing or OPT."""
+    rng = _rng(23)
+    Zb = _orthonormal(20, 3, rng)
+    Z1 = O.orth(Zb + 0.1 * rng.standard_normal((20, 3)))
+    F = np.diag([1.0, -1.0, -1.0])
+    for agg in ("sign", "opt"):
+        a = O.residual_error([Zb, Z1], [5, 4], agg)
+        b = O.residual_error([Zb, Z1 @ F], [5, 4], agg)
+        assert abs(a - b) < 1e-12

@@ -430,3 +430,30 @@ def test_graph_replay_matches_eager_launches(gpu_lib, dtype):
     for sched, agg, Z, _, _ in runs[:3] + runs[6:9]:
         ref = O.localpower(exact, 8, list(sched) + [1], agg, Y0)
         assert O.subspace_dist(Z, ref["Z"]) < (1e-6 if dtype == "f32" else TC_SOLVE_TOL)
+
+
+@pytest.mark.parametrize("agg", ["identity", "sign", "opt"])
+def test_trace_and_residual_error_match_oracle(gpu_lib, agg):
+    """LP_FLAG_TRACE: Z_t after every aggregation and rho_t (Def. 3) against the
+    oracle's per-round trace, a decaying schedule with p = 1 rounds at the end."""
+    sizes = [1500, 1400, 1650, 1450]
+    A, _, _ = _parts(sizes, 96, 61)
+    Y0 = synth.gaussian_start(96, 6, 62)
+    sched = [4, 4, 2, 1, 1]
+    ref = O.localpower(A, 6, sched, agg, Y0, keep_trace=True)
+    with B.LocalPower(A) as lp:
+        B.lp_solve(lp.ctx, 6, sched, agg, Y0, 0, B.LP_FLAG_TRACE)
+        lp.result(6)
+        Zt, rho = B.lp_trace(lp.ctx, len(sched), 96, 6)
+        B.lp_solve(lp.ctx, 6, sched, agg, Y0, 0, 0)
+        lp.result(6)
+        with pytest.raises(B.LPError) as e:       # the last solve was not traced
+            B.lp_trace(lp.ctx, len(sched), 96, 6)
+        assert e.value.status == B.LP_ERR_STATE
+    for t, entry in enumerate(ref["trace"]):
+        assert O.subspace_dist(Zt[t], entry["Z"]) < 1e-6, t
+        if entry["p"] == 1:
+            assert rho[t] == 0.0
+        else:
+            assert entry["rho"] > 1e-4          # the local bases really differ
+            assert abs(rho[t] - entry["rho"]) <= 1e-4 * entry["rho"] + 1e-7, (t, rho[t], entry["rho"])
