@@ -175,6 +175,22 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# DRAM bytes per launch over algorithmic bytes, from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum) of each step kernel at n = 262,144, d = 1,024, k = 16; the traffic
+# grows with the rows, so a full launch's traffic is this ratio times its algorithmic bytes.
+# Keys: (path, planes, cache hints).  Configurations without a capture report null.
+DRAM_RATIO = {(0, 0, 0): 1079.3 / 1073.7,   # SIMT FP32
+              (1, 1, 0): 544.8 / 536.9,     # resident tcgen05, BF16
+              (2, 1, 0): 750.1 / 536.9,     # streaming tcgen05, BF16, no hints
+              (2, 1, 1): 606.8 / 536.9,     # streaming tcgen05, BF16, evict_last / evict_first hints
+              (2, 2, 0): 1753.6 / 1073.7}   # streaming tcgen05, hi/lo planes, no hints
+
+
+def _traffic(path, planes, hints, launch_bytes, d=1024, k=16):
+    r = DRAM_RATIO.get((path, planes, hints)) if (d, k) == (1024, 16) else None
+    return None if r is None else r * launch_bytes
+
+
 KERNELS = {0: "step_simt2_kernel (SIMT FP32 fused A_i^T (A_i Z_i))",
            1: "step_tc_kernel (tcgen05, tile resident in shared memory, cluster-split d)",
            2: "step_tcs_kernel (tcgen05 streaming, second pass re-read from L2)"}
@@ -768,7 +784,8 @@ def run_ours(args):
             "gpu_launches": f32["launches"], "e2e": e2e,
             "roofline": {"kernel": KERNELS[f32["path"]], "bound": "alu",
                          "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
-                         "traffic": None, "launch_ms": f32["step_ms"],
+                         "traffic": _traffic(0, 0, 0, f32["launch_bytes"]), "traffic_unit": "bytes per launch",
+                         "launch_ms": f32["step_ms"],
                          "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz"},
             "roofline_hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                              "frac": achieved_gbs / hbm_peak, "peak_source": f"{peak_src} HBM copy bandwidth",
@@ -795,7 +812,9 @@ def run_ours(args):
             "latency_ms": b16["latency_ms"], "clocks": clkb, "gpu_launches": b16["launches"],
             "speedup_solves_vs_fp32": b16["solves_per_s"] / f32["solves_per_s"],
             "roofline": {"bound": "hbm", "achieved": gbs_b, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": gbs_b / hbm_peak, "traffic": None, "launch_ms": b16["step_ms"],
+                         "frac": gbs_b / hbm_peak,
+                         "traffic": _traffic(b16["path"], 1, choice["cache_hints"], b16["launch_bytes"]),
+                         "traffic_unit": "bytes per launch", "launch_ms": b16["step_ms"],
                          "peak_source": f"{peak_src} HBM copy bandwidth"}}
 
     # ---------------- the FP32 data stored as hi + lo BF16 planes (same bytes, tensor cores)
@@ -817,7 +836,9 @@ def run_ours(args):
             "solves_per_s": sp["solves_per_s"], "ms_per_solve": sp["ms_per_solve"], "latency_ms": sp["latency_ms"],
             "clocks": clks, "speedup_solves_vs_fp32": sp["solves_per_s"] / f32["solves_per_s"],
             "roofline": {"bound": "hbm", "achieved": gbs_s, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": gbs_s / hbm_peak, "traffic": None, "launch_ms": sp["step_ms"],
+                         "frac": gbs_s / hbm_peak,
+                         "traffic": _traffic(sp["path"], 2, choice_s["cache_hints"], sp["launch_bytes"]),
+                         "traffic_unit": "bytes per launch", "launch_ms": sp["step_ms"],
                          "peak_source": f"{peak_src} HBM copy bandwidth"}}
 
     if rank == 0 and not args.no_accuracy:

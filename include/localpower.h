@@ -149,8 +149,10 @@ lp_status lp_solve(lp_ctx* ctx, int k, const int* p_schedule, int T, lp_aggregat
 lp_status lp_result(lp_ctx* ctx, double* z_out, double* sigma_out, lp_stats* stats);
 
 /* Tuning of the streaming tensor-core step kernel (LP_BF16 and LP_F32_BF16X2
- * data).  Zero in a field keeps the library's default for it.  These change
- * speed only: every setting computes the same products in the same order. */
+ * data).  Zero in a field keeps the library's default for it.  Ring depth, lag,
+ * prefetch and cache hints change speed only: the same products are summed in
+ * the same order.  slice_cols also changes how a tile's row products are
+ * summed (over the CTAs of a cluster), so results can differ in the last bits. */
 typedef struct lp_tuning {
     int32_t ring_units;      /* 32 KB shared-memory ring units (default: as many as fit, <= 8) */
     int32_t lag_units;       /* first-pass units of tile t+1 issued before the second pass of
@@ -158,6 +160,9 @@ typedef struct lp_tuning {
     int32_t prefetch_units;  /* first-pass units brought into L2 ahead of their load (default 0) */
     int32_t cache_hints;     /* 1: first-pass loads mark lines evict_last, second-pass loads
                               * evict_first (default 0: no hint)                                  */
+    int32_t slice_cols;      /* columns of A per CTA, a multiple of 128 (default: 1024 for one
+                              * plane, 512 for two); smaller slices split d over a cluster and
+                              * shorten the distance between a unit's HBM read and its L2 re-read */
 } lp_tuning;
 
 /*
@@ -173,8 +178,8 @@ lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* tuning);
  * partitions and keep the fastest for later solves on this context (it sets
  * the context's tuning, and for LP_BF16 data whether the resident or the
  * streaming tensor-core kernel runs).  Candidates: the streaming kernel with
- * lag in {1, 2, 4} and cache hints off/on, and the resident kernel where it
- * has a plan.  Each is timed over 3 launches after a warm-up launch, on the
+ * lag in {1, 2, 4}, cache hints off/on and the default or 512-column slices,
+ * and the resident kernel where it has a plan.  Each is timed over 3 launches after a warm-up launch, on the
  * context's stream; the call synchronises.  Other dtypes have one candidate
  * (the SIMT kernel) and return at once.
  *   chosen      receives the winning tuning (may be NULL).

@@ -45,7 +45,7 @@ class lp_stats(C.Structure):
 
 class lp_tuning(C.Structure):
     _fields_ = [("ring_units", C.c_int32), ("lag_units", C.c_int32), ("prefetch_units", C.c_int32),
-                ("cache_hints", C.c_int32)]
+                ("cache_hints", C.c_int32), ("slice_cols", C.c_int32)]
 
 
 class lp_request(C.Structure):
@@ -168,13 +168,13 @@ def lp_destroy(ctx) -> None:
 
 
 def lp_set_tuning(ctx, ring_units: int = 0, lag_units: int = 0, prefetch_units: int = 0, cache_hints: int = 0,
-                  reset: bool = False) -> None:
+                  reset: bool = False, slice_cols: int = 0) -> None:
     """Tuning of the streaming tensor-core step (zeros keep the defaults; reset=True passes NULL)."""
     L = load()
     if reset:
         _check(ctx, L.lp_set_tuning(ctx, None))
         return
-    t = lp_tuning(ring_units, lag_units, prefetch_units, cache_hints)
+    t = lp_tuning(ring_units, lag_units, prefetch_units, cache_hints, slice_cols)
     _check(ctx, L.lp_set_tuning(ctx, C.byref(t)))
 
 
@@ -187,7 +187,7 @@ def lp_autotune(ctx, k: int) -> dict:
     _check(ctx, L.lp_autotune(ctx, int(k), C.byref(t), C.byref(path), C.byref(ms)))
     return {"path": PATHS.get(path.value, path.value), "path_code": path.value, "ms_per_step": ms.value,
             "ring_units": t.ring_units, "lag_units": t.lag_units, "prefetch_units": t.prefetch_units,
-            "cache_hints": t.cache_hints}
+            "cache_hints": t.cache_hints, "slice_cols": t.slice_cols}
 
 
 def lp_trace(ctx, rounds: int, d: int, k: int):

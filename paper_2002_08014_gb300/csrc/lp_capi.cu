@@ -156,6 +156,16 @@ void dfree(lp_ctx* c, T*& p, size_t bytes) {
 
 enum Path { PATH_SIMT = 0, PATH_TC = 1, PATH_TCS = 2 };
 
+// The SIMT step for padded rank K: one launch, or - when the K = 32 variant does
+// not fit shared memory (Z is staged there) - two K = 16 launches on the column
+// halves of Z (each column of Y_i = A_i^T (A_i Z_i) depends only on the same
+// column of Z).  Returns the launches per step, 0 if unsupported.
+int simt_launches(int d, int64_t ld, lp_dtype dtype, int K) {
+  if (lp::step_simt_smem(d, ld, dtype, K, nullptr) != 0) return 1;
+  if (K == 32 && lp::step_simt_smem(d, ld, dtype, 16, nullptr) != 0) return 2;
+  return 0;
+}
+
 int kcap_of(int k) { return k <= 8 ? 8 : (k <= 16 ? 16 : 32); }
 // Algorithmic bytes per element of A (both planes for LP_F32_BF16X2).
 size_t elem_bytes(lp_dtype t) { return (t == LP_F32 || t == LP_F32_BF16X2) ? 4 : (t == LP_BF16 ? 2 : 1); }
@@ -344,8 +354,19 @@ lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool t
   else if (c->path == PATH_TC)
     e = lp::launch_step_tc(c->tc, c->dSegsTc, c->dSegPtrTc, Z, z_stride, c->dP, static_cast<int>(c->d), c->dStatus,
                            c->stream);
-  else
+  else if (simt_launches(static_cast<int>(c->d), c->ld, c->dtype, K) == 2) {
+    a.zld = a.pld = K;
+    e = lp::launch_step_simt(a, c->dtype, 16, c->stream);
+    if (e == cudaSuccess) {
+      lp::StepArgs b = a;
+      b.Z = a.Z + 16;
+      b.P = a.P + 16;
+      e = lp::launch_step_simt(b, c->dtype, 16, c->stream);
+      c->stats.kernel_launches++;
+    }
+  } else {
     e = lp::launch_step_simt(a, c->dtype, K, c->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "fused power-step launch");
   if (timing) {
     LP_CUDA(record_event(c->step_ev[c->step_ev_used + 1], c->stream));
@@ -634,7 +655,7 @@ static lp_status validate_k(lp_ctx* c, int k) {
   if (k > smin)
     return fail(c, LP_ERR_INVALID, "k exceeds the smallest partition's row count (its local Y_i would be rank deficient)");
   const int K = kcap_of(k);
-  if (c->planes == 0 && lp::step_simt_smem(static_cast<int>(c->d), c->ld, c->dtype, K, nullptr) == 0)
+  if (c->planes == 0 && simt_launches(static_cast<int>(c->d), c->ld, c->dtype, K) == 0)
     return fail(c, LP_ERR_UNSUPPORTED, "no step kernel for d=" + std::to_string(c->d) + ", k=" + std::to_string(k));
   return LP_OK;
 }
@@ -713,7 +734,7 @@ static lp_status select_path(lp_ctx* c, int k, unsigned flags) {
       return fail(c, LP_ERR_UNSUPPORTED,
                   "split-plane data run only on the streaming tensor-core kernel, which has no plan for d=" +
                       std::to_string(c->d) + ", k=" + std::to_string(k));
-    if (lp::step_simt_smem(static_cast<int>(c->d), c->ld, c->dtype, kcap_of(k), nullptr) == 0)
+    if (simt_launches(static_cast<int>(c->d), c->ld, c->dtype, kcap_of(k)) == 0)
       return fail(c, LP_ERR_UNSUPPORTED,
                   "no step kernel for d=" + std::to_string(c->d) + ", k=" + std::to_string(k) + " on this path");
   }
@@ -800,12 +821,14 @@ lp_status lp_set_tuning(lp_ctx* c, const lp_tuning* t) {
   c->err.clear();
   lp::TcsTuning nt;
   if (t) {
-    if (t->ring_units < 0 || t->lag_units < 0 || t->prefetch_units < 0 || t->cache_hints < 0)
-      return fail(c, LP_ERR_INVALID, "tuning fields must be >= 0");
+    if (t->ring_units < 0 || t->lag_units < 0 || t->prefetch_units < 0 || t->cache_hints < 0 || t->slice_cols < 0 ||
+        (t->slice_cols != 0 && t->slice_cols % 128 != 0))
+      return fail(c, LP_ERR_INVALID, "tuning fields must be >= 0, slice_cols a multiple of 128");
     nt.ring_units = t->ring_units;
     nt.lag_units = t->lag_units;
     nt.prefetch_units = t->prefetch_units;
     nt.cache_hints = t->cache_hints;
+    nt.slice_cols = t->slice_cols;
   }
   c->tuning = nt;
   c->prefer_resident = false;
@@ -830,14 +853,16 @@ lp_status lp_autotune(lp_ctx* c, int k, lp_tuning* chosen, int* path_out, double
   };
   std::vector<Cand> cands;
   if (c->planes > 0) {
-    for (int lag : {1, 2, 4})
-      for (int hint : {0, 1}) {
-        Cand cd;
-        cd.t.lag_units = lag;
-        cd.t.cache_hints = hint;
-        cd.resident = false;
-        cands.push_back(cd);
-      }
+    for (int slice : {0, 512})
+      for (int lag : {1, 2, 4})
+        for (int hint : {0, 1}) {
+          Cand cd;
+          cd.t.lag_units = lag;
+          cd.t.cache_hints = hint;
+          cd.t.slice_cols = slice;
+          cd.resident = false;
+          cands.push_back(cd);
+        }
     if (c->dtype == LP_BF16 && c->tc_ready) cands.push_back(Cand{lp::TcsTuning{}, true});
   }
   const lp::TcsTuning saved = c->tuning;
@@ -885,6 +910,7 @@ lp_status lp_autotune(lp_ctx* c, int k, lp_tuning* chosen, int* path_out, double
     chosen->lag_units = win.t.lag_units;
     chosen->prefetch_units = win.t.prefetch_units;
     chosen->cache_hints = win.t.cache_hints;
+    chosen->slice_cols = win.t.slice_cols;
   }
   if (path_out) *path_out = win_path;
   if (best_ms) *best_ms = best;

@@ -37,6 +37,8 @@ struct StepArgs {
   int64_t z_stride;       // floats between partitions' Z blocks (0: shared)
   float* P;               // slots x d x K partial sums of A_i^T (A_i Z_i)
   int grid;               // CTAs
+  int zld = 0, pld = 0;   // row strides of Z and P in floats (0: K); a launch on a column
+                          // range of wider blocks passes the wider stride and offset pointers
 };
 
 // Returns cudaErrorInvalidConfiguration when no SIMT instantiation fits.
@@ -77,7 +79,7 @@ struct TcsPlan {
 };
 // Tuning of the streaming kernel (lp_tuning without the C names); zeros are defaults.
 struct TcsTuning {
-  int ring_units = 0, lag_units = 0, prefetch_units = 0, cache_hints = 0;
+  int ring_units = 0, lag_units = 0, prefetch_units = 0, cache_hints = 0, slice_cols = 0;
 };
 // Fills the geometry for (d, k, planes).  False when the shape has no streaming kernel.
 bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan* p);

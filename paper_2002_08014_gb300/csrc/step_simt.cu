@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_simt_kernel(StepArgs a, Geo 
 
   const int tid = threadIdx.x;
   const int d = a.d;
+  const int zld = a.zld > 0 ? a.zld : K, pld = a.pld > 0 ? a.pld : K;
   const Tin* A = static_cast<const Tin*>(a.A);
   const int chunks_per_row = static_cast<int>(a.ld / kPer16);
   const int redst = R * K + 4;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_simt_kernel(StepArgs a, Geo 
       for (int e = tid; e < n4; e += kThreads) {
         const int c = e / (K / 4), jgz = e % (K / 4);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c < d) v = *reinterpret_cast<const float4*>(Zg + size_t(c) * K + 4 * jgz);
+        if (c < d) v = *reinterpret_cast<const float4*>(Zg + size_t(c) * zld + 4 * jgz);
         const int q = c >> 2, i = c & 3;
         float* dst = Zs + (size_t(jgz) * g.Qp + q) * 16 + 4 * (i ^ ((q >> 1) & 3));
         *reinterpret_cast<float4*>(dst) = v;
@@ -282,14 +283,14 @@ __global__ void __launch_bounds__(kThreads, 1) step_simt_kernel(StepArgs a, Geo 
     }
 
     // flush this segment's partial
-    float* Pd = a.P + size_t(sg.slot) * d * K;
+    float* Pd = a.P + size_t(sg.slot) * d * pld;
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
       const int c = tid + kThreads * q;
       if (c < d) {
 #pragma unroll
         for (int j = 0; j < K; j += 4)
-          *reinterpret_cast<float4*>(Pd + size_t(c) * K + j) = make_float4(y[q][j], y[q][j + 1], y[q][j + 2], y[q][j + 3]);
+          *reinterpret_cast<float4*>(Pd + size_t(c) * pld + j) = make_float4(y[q][j], y[q][j + 1], y[q][j + 2], y[q][j + 3]);
       }
 #pragma unroll
       for (int j = 0; j < K; ++j) y[q][j] = 0.f;
@@ -346,6 +347,7 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = a.d;
+  const int zld = a.zld > 0 ? a.zld : K, pld = a.pld > 0 ? a.pld : K;
   const float* A = static_cast<const float*>(a.A);
   const int cpr = static_cast<int>(a.ld / 4);  // 16-byte chunks per row
   const int sp = lane / MT, mt = lane % MT;
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
       for (int e = tid; e < g.Qp * 4 * (K / 4); e += kThreads2) {
         const int c = e / (K / 4), jz = e % (K / 4);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c < d) v = *reinterpret_cast<const float4*>(Zg + size_t(c) * K + 4 * jz);
+        if (c < d) v = *reinterpret_cast<const float4*>(Zg + size_t(c) * zld + 4 * jz);
         const int q = c >> 2, i = c & 3;
         *reinterpret_cast<float4*>(Zs + (size_t(q) * 4 + (i ^ (q & 1))) * K + 4 * jz) = v;
       }
@@ -483,14 +485,14 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
       }
       __syncthreads();
     }
-    float* Pd = a.P + size_t(sg.slot) * d * K;
+    float* Pd = a.P + size_t(sg.slot) * d * pld;
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
       const int c = tid + kThreads2 * q;
       if (c < d) {
 #pragma unroll
         for (int j = 0; j < K / 2; j += 2)
-          *reinterpret_cast<float4*>(Pd + size_t(c) * K + 2 * j) = make_float4(y[q][j].x, y[q][j].y, y[q][j + 1].x,
+          *reinterpret_cast<float4*>(Pd + size_t(c) * pld + 2 * j) = make_float4(y[q][j].x, y[q][j].y, y[q][j + 1].x,
                                                                               y[q][j + 1].y);
       }
 #pragma unroll

@@ -484,6 +484,7 @@ bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan*
   // re-read) stay at 256 KB per CTA
   int ncd_max = K == 32 ? 8 : 16;
   if (planes == 2 && ncd_max > 8) ncd_max = 8;
+  if (tune.slice_cols >= 128 && tune.slice_cols / 64 < ncd_max) ncd_max = (tune.slice_cols / 128) * 2;
   int nc = (d + 63) / 64;
   nc += nc & 1;
   int cl = 1;

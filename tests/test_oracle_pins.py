@@ -319,3 +319,17 @@ def test_residual_error_is_invariant_to_the_base_basis_sign_flips_of_others():
         a = O.residual_error([Zb, Z1], [5, 4], agg)
         b = O.residual_error([Zb, Z1 @ F], [5, 4], agg)
         assert abs(a - b) < 1e-12
+
+
+def test_bf16x2_planes_represent_fp32_within_2_to_minus_17():
+    """hi = BF16(a) (the plain encoder), lo = BF16(a - hi); hi + lo is within
+    2^-17 |a| of a (and equal to a whenever a has at most 16 significant bits)."""
+    rng = _rng(31)
+    a = (rng.standard_normal(200_000) * 10.0 ** rng.uniform(-6, 6, 200_000)).astype(np.float32)
+    hi, lo = synth.f32_to_bf16x2_planes(a)
+    assert np.array_equal(hi, synth.f32_to_bf16_bits(a))
+    v = O.decode_bf16(hi) + O.decode_bf16(lo)
+    a64 = a.astype(np.float64)
+    assert np.all(np.abs(v - a64) <= 2.0 ** -17 * np.abs(a64))
+    short = (a.view(np.uint32) & np.uint32(0xFF)) == 0   # 16 significant bits: exact
+    assert np.array_equal(v[short], a64[short])

@@ -69,6 +69,7 @@ def _relF(a, b):
     ([40, 41, 42], 64, 32),            # k = 32
     ([20], 7, 1),                      # tiny d, k = 1
     ([300, 29], 512, 24),              # k padded to 32, partition of 29 rows
+    ([300, 211], 2048, 32),            # SIMT: two K = 16 launches on the column halves of Z
 ])
 def test_power_step_matches_oracle(gpu_lib, dtype, sizes, d, k):
     stored, exact, scales = _parts(sizes, d, 100 + d + k, dtype)
@@ -385,6 +386,15 @@ def test_tuning_changes_speed_not_results(gpu_lib):
         assert np.array_equal(Z, outs[0])
     ref = O.localpower(exact, 16, sched, "sign", Y0)
     assert O.subspace_dist(outs[0], ref["Z"]) < TC_SOLVE_TOL
+    # narrower column slices (a cluster splits d): another summation order, same result to the bar
+    with B.LocalPower(stored, dtype="bf16") as lp:
+        B.lp_set_tuning(lp.ctx, slice_cols=128)
+        Zs, _, st = lp.solve(16, sched, "sign", Y0)
+        assert st["path"] == TC_STREAM
+        with pytest.raises(B.LPError) as e:
+            B.lp_set_tuning(lp.ctx, slice_cols=100)
+        assert e.value.status == B.LP_ERR_INVALID
+    assert O.subspace_dist(Zs, ref["Z"]) < TC_SOLVE_TOL
 
 
 @pytest.mark.parametrize("dtype", ["bf16", "f32_bf16x2", "f32"])
