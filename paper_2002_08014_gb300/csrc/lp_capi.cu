@@ -156,14 +156,9 @@ void dfree(lp_ctx* c, T*& p, size_t bytes) {
 
 enum Path { PATH_SIMT = 0, PATH_TC = 1, PATH_TCS = 2 };
 
-// The SIMT step for padded rank K: one launch, or - when the K = 32 variant does
-// not fit shared memory (Z is staged there) - two K = 16 launches on the column
-// halves of Z (each column of Y_i = A_i^T (A_i Z_i) depends only on the same
-// column of Z).  Returns the launches per step, 0 if unsupported.
+// Launches of the SIMT step per local step (0: no SIMT kernel for the shape).
 int simt_launches(int d, int64_t ld, lp_dtype dtype, int K) {
-  if (lp::step_simt_smem(d, ld, dtype, K, nullptr) != 0) return 1;
-  if (K == 32 && lp::step_simt_smem(d, ld, dtype, 16, nullptr) != 0) return 2;
-  return 0;
+  return lp::step_simt_smem(d, ld, dtype, K, nullptr) != 0 ? 1 : 0;
 }
 
 int kcap_of(int k) { return k <= 8 ? 8 : (k <= 16 ? 16 : 32); }
@@ -354,19 +349,8 @@ lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool t
   else if (c->path == PATH_TC)
     e = lp::launch_step_tc(c->tc, c->dSegsTc, c->dSegPtrTc, Z, z_stride, c->dP, static_cast<int>(c->d), c->dStatus,
                            c->stream);
-  else if (simt_launches(static_cast<int>(c->d), c->ld, c->dtype, K) == 2) {
-    a.zld = a.pld = K;
-    e = lp::launch_step_simt(a, c->dtype, 16, c->stream);
-    if (e == cudaSuccess) {
-      lp::StepArgs b = a;
-      b.Z = a.Z + 16;
-      b.P = a.P + 16;
-      e = lp::launch_step_simt(b, c->dtype, 16, c->stream);
-      c->stats.kernel_launches++;
-    }
-  } else {
+  else
     e = lp::launch_step_simt(a, c->dtype, K, c->stream);
-  }
   if (e != cudaSuccess) return cuda_fail(c, e, "fused power-step launch");
   if (timing) {
     LP_CUDA(record_event(c->step_ev[c->step_ev_used + 1], c->stream));
