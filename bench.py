@@ -501,9 +501,31 @@ def run_rounds(args):
                 out[f"{agg}_p{p}"] = {"rounds_to_1e-4": first(1e-4), "rounds_to_1e-6": first(1e-6),
                                       "final_dist": dist[-1], "dist_every_10": dist[9::10],
                                       "rho_mean": float(np.mean(rho)), "rho_last": float(rho[-1])}
+        # iteration rank r > k (Alg. 1): dist(Z_t, U_k) = ||(I - Z_t Z_t^T) U_k||_2 with Z_t of r columns
+        ranks = {}
+        rng = np.random.default_rng(synth.configs.SEED_BASE + 7)
+        for r in (k, k + 8, 2 * k):
+            Yr = np.concatenate([Y0, rng.standard_normal((d, r - k))], axis=1) if r > k else Y0
+            B.lp_solve(lp.ctx, r, [4] * T, "sign", Yr, 0, B.LP_FLAG_TRACE)
+            lp.result(r)
+            Zt, _ = B.lp_trace(lp.ctx, T, d, r)
+            dist = [oracle.subspace_dist(oracle.orth(Zt[t]), V) for t in range(T)]
+            first = lambda tol: next((t + 1 for t, x in enumerate(dist) if x <= tol), None)
+            ranks[f"r{r}"] = {"rounds_to_1e-4": first(1e-4), "rounds_to_1e-6": first(1e-6), "final_dist": dist[-1]}
+        # eta of Def. 2 on the device, beside the oracle's value on the same matrix
+        t0 = time.perf_counter()
+        eta, norms = lp.eta()
+        eta_ms = (time.perf_counter() - t0) * 1e3
+    eta_ref = oracle.eta(parts)[0]
     print(json.dumps({"workload": "rounds", "n": c["n"], "d": d, "k": k, "m": c["m"], "T": T,
                       "note": "rounds = aggregations = the paper's communications; rho_t is max_i ||Z_i G_i - Z_b||_2",
-                      "results": out}))
+                      "results": out,
+                      "iteration_rank": {"note": "sign-fixing, p = 4; the first k columns of Y_0 are shared",
+                                         "results": ranks},
+                      "eta": {"value": eta, "oracle": eta_ref, "rel_err": abs(eta - eta_ref) / eta_ref,
+                              "norm_M": float(norms[-1]), "ms": eta_ms,
+                              "note": "Def. 2: max_i ||M_i - M||_2 / ||M||_2; lp_eta forms the M_i with "
+                                      "ceil(d/K) fused steps and measures norms by Lanczos"}}))
 
 
 def run_serving(args):

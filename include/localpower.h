@@ -200,6 +200,26 @@ lp_status lp_autotune(lp_ctx* ctx, int k, lp_tuning* chosen, int* path, double* 
  */
 lp_status lp_trace(lp_ctx* ctx, double* z_trace, double* rho);
 
+/*
+ * lp_eta: the local-approximation measure of Def. 2 (Sec. 4) for the loaded
+ * partitions, a property of the data that needs no solve:
+ *   eta = max_i ||M_i - M||_2 / ||M||_2,  M_i = (1/s_i) A_i^T A_i,  M = sum_i p_i M_i.
+ * Every M_i is formed on the device by ceil(d / 16) fused local power steps on
+ * identity blocks of Z (the same step kernel and precision as a solve), M by a
+ * p-weighted FP64 sum of the symmetrised M_i, and each spectral norm by a
+ * Lanczos run of min(d, 256) steps with full reorthogonalisation (exact once
+ * the run reaches d steps or an invariant subspace).
+ *   eta    out: one double.
+ *   norms  out, may be NULL: m + 1 doubles, ||M_i - M||_2 for i = 0 .. m-1, then ||M||_2.
+ * Device memory: (m + 1) d^2 * 4 + (m + 1) * min(d, 256) * d * 4 bytes, within
+ * the context's budget (LP_ERR_OOM otherwise), freed before the call returns.
+ * Synchronous.  The last solve's result, statistics and status stay as they were.
+ * Errors: LP_ERR_STATE (no partitions), LP_ERR_INVALID (eta NULL),
+ * LP_ERR_UNSUPPORTED (no step kernel for d, or d > 16384), LP_ERR_NUMERIC
+ * (M = 0 or a non-finite norm), LP_ERR_TIMEOUT (a bounded device wait gave up).
+ */
+lp_status lp_eta(lp_ctx* ctx, double* eta, double* norms);
+
 /* lp_destroy: free everything the context owns; NULL is a no-op. */
 void lp_destroy(lp_ctx* ctx);
 

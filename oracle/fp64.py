@@ -22,6 +22,11 @@ Pins (tests/test_oracle_*.py check each against something other than itself):
   * ritz                                   -> singular values of A (LAPACK SVD).
   * subspace_dist                          -> the definition ||UU^T - VV^T||_2 and
                                               principal angles (Def. 1).
+  * eta                                    -> closed form for partitions whose rows lie
+                                              on distinct coordinate axes; 0 for m = 1 and
+                                              replicated partitions; scale invariance.
+  * iteration rank r > k                   -> nested subspaces: at p = 1 the r-column
+                                              iterate's span contains the k-column one's.
   parity unpinned: the value of the constant-p error floor and the gap between
   OPT and sign-fixing have no closed form (Sec. 4, Thm. 1 gives bounds only);
   they are checked only qualitatively (monotone in p).
@@ -254,6 +259,20 @@ def top_k_truth(parts, k: int):
     M = explicit_M(parts)
     lam, V = np.linalg.eigh(M)
     return V[:, ::-1][:, :k], lam[::-1]
+
+
+def eta(parts):
+    """eta = max_i ||M_i - M||_2 / ||M||_2 with M_i = (1/s_i) A_i^T A_i and
+    M = sum_i p_i M_i (Def. 2), each spectral norm from a full symmetric
+    eigendecomposition.  Returns (eta, [||M_i - M||_2 ...] + [||M||_2])."""
+    As = [as_f64(P) for P in parts]
+    sizes = [A.shape[0] for A in As]
+    p = weights(sizes)
+    Ms = [A.T @ A / A.shape[0] for A in As]
+    M = sum(pi * Mi for pi, Mi in zip(p, Ms))
+    norms = [float(np.max(np.abs(np.linalg.eigvalsh(Mi - M)))) for Mi in Ms]
+    normM = float(np.max(np.abs(np.linalg.eigvalsh(M))))
+    return max(norms) / normM, np.array(norms + [normM])
 
 
 def subspace_iteration(M: np.ndarray, Y0: np.ndarray, steps: int) -> np.ndarray:

@@ -27,7 +27,7 @@ PATHS = {0: "simt", 1: "tc_resident", 2: "tc_streaming"}
 
 # Every symbol the header declares, in declaration order.
 EXPORTS = ["lp_create", "lp_load_partitions", "lp_solve", "lp_result", "lp_destroy", "lp_last_error",
-           "lp_set_tuning", "lp_autotune", "lp_trace", "lp_server_create", "lp_server_submit", "lp_server_progress",
+           "lp_set_tuning", "lp_autotune", "lp_trace", "lp_eta", "lp_server_create", "lp_server_submit", "lp_server_progress",
            "lp_server_result", "lp_server_query", "lp_server_error", "lp_server_destroy", "lp_batch_create",
            "lp_batch_add", "lp_batch_autotune", "lp_batch_solve", "lp_batch_result", "lp_batch_size", "lp_batch_error",
            "lp_batch_destroy", "lp_power_step", "lp_orth", "lp_align_aggregate", "lp_power_step_static"]
@@ -101,6 +101,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
     L.lp_power_step_static.argtypes = [P, I, C.POINTER(I64), I64, I, P, P, P]
     L.lp_set_tuning.argtypes = [P, C.POINTER(lp_tuning)]
     L.lp_trace.argtypes = [P, P, P]
+    L.lp_eta.argtypes = [P, P, P]
     L.lp_autotune.argtypes = [P, I, C.POINTER(lp_tuning), C.POINTER(I), C.POINTER(C.c_double)]
     L.lp_server_create.argtypes = [C.POINTER(P), I, C.c_size_t, I]
     L.lp_server_submit.argtypes = [P, C.POINTER(lp_request), C.POINTER(I64)]
@@ -188,6 +189,14 @@ def lp_autotune(ctx, k: int) -> dict:
     return {"path": PATHS.get(path.value, path.value), "path_code": path.value, "ms_per_step": ms.value,
             "ring_units": t.ring_units, "lag_units": t.lag_units, "prefetch_units": t.prefetch_units,
             "cache_hints": t.cache_hints, "slice_cols": t.slice_cols}
+
+
+def lp_eta(ctx, m: int):
+    """(eta of Def. 2, [||M_i - M||_2 for each i] + [||M||_2]) for the loaded partitions."""
+    eta = np.zeros(1, dtype=np.float64)
+    norms = np.empty(m + 1, dtype=np.float64)
+    _check(ctx, load().lp_eta(ctx, eta.ctypes.data, norms.ctypes.data))
+    return float(eta[0]), norms
 
 
 def lp_trace(ctx, rounds: int, d: int, k: int):
@@ -350,6 +359,9 @@ class LocalPower:
 
     def power_step(self, k: int, z, shared: bool = True):
         return lp_power_step(self.ctx, k, z, shared, self.m, self.d)
+
+    def eta(self):
+        return lp_eta(self.ctx, self.m)
 
     def close(self) -> None:
         if self.ctx is not None:

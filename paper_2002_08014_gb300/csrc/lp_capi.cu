@@ -631,6 +631,9 @@ int lp::solve_state(lp_ctx* c) {
 
 extern "C" {
 
+// Widest d for which lp_eta forms the d x d matrices (its Lanczos vectors live in shared memory).
+static constexpr int kEtaMaxD = 16384;
+
 static lp_status validate_k(lp_ctx* c, int k) {
   if (c->m == 0) return fail(c, LP_ERR_STATE, "no partitions loaded");
   if (k < 1 || k > LP_MAX_K) return fail(c, LP_ERR_INVALID, "k must be in [1, 32]");
@@ -1082,6 +1085,84 @@ lp_status lp_power_step(lp_ctx* c, int k, const double* z, int z_shared, double*
   if (space == LP_HOST)
     LP_CUDA(cudaMemcpyAsync(y_out, dst, size_t(c->m) * d * k * 8, cudaMemcpyDeviceToHost, c->stream));
   LP_CUDA(cudaStreamSynchronize(c->stream));
+  return LP_OK;
+}
+
+lp_status lp_eta(lp_ctx* c, double* eta, double* norms) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  if (c->m == 0) return fail(c, LP_ERR_STATE, "no partitions loaded");
+  if (!eta) return fail(c, LP_ERR_INVALID, "eta must be non-NULL");
+  const int d = static_cast<int>(c->d), m = c->m;
+  if (d > kEtaMaxD) return fail(c, LP_ERR_UNSUPPORTED, "eta is computed for d <= " + std::to_string(kEtaMaxD));
+  LP_CUDA(cudaSetDevice(c->device));
+  // kb identity columns per step, in the padded width the context already has
+  // (growing the state would free the last solve's result); no
+  // orthonormalisation follows, so partitions with fewer rows than kb are fine.
+  const int K = c->Kcap > 0 ? c->Kcap : kcap_of(std::min(16, d));
+  const int kb = std::min(K, d);
+  if (c->planes == 0 && simt_launches(d, c->ld, c->dtype, K) == 0)
+    return fail(c, LP_ERR_UNSUPPORTED, "no step kernel for d=" + std::to_string(d));
+  lp_status st;
+  if ((st = select_path(c, kb, 0))) return st;
+  if ((st = ensure_state(c, K))) return st;
+  // the last solve's statistics and status word stay as they were
+  const lp_stats saved = c->stats;
+  int saved_status = 0;
+  LP_CUDA(cudaMemcpyAsync(&saved_status, c->dStatus, 4, cudaMemcpyDeviceToHost, c->stream));
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  LP_CUDA(cudaMemsetAsync(c->dStatus, 0, 4, c->stream));
+  const size_t dd = size_t(d) * d;
+  const size_t mat_bytes = (size_t(m) + 1) * dd * 4;
+  const size_t v_bytes = (size_t(m) + 1) * lp::lanczos_steps(d) * size_t(d) * 4;
+  const size_t out_bytes = (size_t(m) + 1) * 8;
+  float* dM = nullptr;
+  float* dV = nullptr;
+  double* dOut = nullptr;
+  auto release = [&]() {
+    dfree(c, dM, mat_bytes);
+    dfree(c, dV, v_bytes);
+    dfree(c, dOut, out_bytes);
+    c->stats = saved;
+  };
+  if ((st = dalloc(c, &dM, mat_bytes)) || (st = dalloc(c, &dV, v_bytes)) || (st = dalloc(c, &dOut, out_bytes))) {
+    release();
+    return st;
+  }
+  std::vector<double> out(size_t(m) + 1, 0.0);
+  int status = 0;
+  auto run = [&]() -> lp_status {
+    lp_status s2;
+    for (int c0 = 0; c0 < d; c0 += kb) {
+      if ((s2 = check_launch(c, lp::launch_identity_block(c->dZ, d, K, c0, c->stream), "identity block"))) return s2;
+      if ((s2 = launch_step(c, K, c->dZ, 0, false))) return s2;
+      if ((s2 = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream),
+                             "reduce")))
+        return s2;
+      if ((s2 = check_launch(
+               c, lp::launch_scatter_columns(c->dYl, dM, m, d, K, c0, std::min(kb, d - c0), c->stream), "scatter")))
+        return s2;
+    }
+    if ((s2 = check_launch(c, lp::launch_deviations(dM, c->dW, m, d, c->stream), "deviations"))) return s2;
+    if ((s2 = check_launch(c, lp::launch_lanczos_norms(dM, m + 1, d, dV, dOut, c->stream), "lanczos"))) return s2;
+    LP_CUDA(cudaMemcpyAsync(out.data(), dOut, out_bytes, cudaMemcpyDeviceToHost, c->stream));
+    LP_CUDA(cudaMemcpyAsync(&status, c->dStatus, 4, cudaMemcpyDeviceToHost, c->stream));
+    LP_CUDA(cudaStreamSynchronize(c->stream));
+    LP_CUDA(cudaMemcpyAsync(c->dStatus, &saved_status, 4, cudaMemcpyHostToDevice, c->stream));
+    LP_CUDA(cudaStreamSynchronize(c->stream));
+    return LP_OK;
+  };
+  st = run();
+  release();
+  if (st) return st;
+  if (status & lp::ST_TIMEOUT) return fail(c, LP_ERR_TIMEOUT, "device wait timed out");
+  double worst = 0.0;
+  for (int i = 0; i <= m; ++i)
+    if (!std::isfinite(out[i])) return fail(c, LP_ERR_NUMERIC, "non-finite matrix norm");
+  for (int i = 0; i < m; ++i) worst = std::max(worst, out[i]);
+  if (!(out[m] > 0.0)) return fail(c, LP_ERR_NUMERIC, "M is zero");
+  *eta = worst / out[m];
+  if (norms) std::memcpy(norms, out.data(), out_bytes);
   return LP_OK;
 }
 

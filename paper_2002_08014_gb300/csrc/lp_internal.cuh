@@ -136,6 +136,20 @@ size_t ritz_scratch_bytes(int d, int K);
 // out[i] = ||Z_i G_i - Z_b||_2 (Def. 3), G_i the aligner (nullptr: none; diag_only: sign-fixing); out[base] = 0.
 cudaError_t launch_rho(const float* Zl, int64_t z_stride, const float* Zb, const float* G, int diag_only, int base,
                        int m, int d, int k, int K, double* out, int* status, cudaStream_t s);
+// ---- eta of Def. 2 --------------------------------------------------------
+// Z = columns [c0, c0 + K) of the d x d identity (d x K FP32 block).
+cudaError_t launch_identity_block(float* Z, int d, int K, int c0, cudaStream_t s);
+// Rows c0 .. c0 + ncols - 1 of slot i (d x d FP32, slot stride d^2) = columns of Y_i (d x K blocks).
+cudaError_t launch_scatter_columns(const float* Y, float* Mall, int m, int d, int K, int c0, int ncols,
+                                   cudaStream_t s);
+// Slot m = M = sum_i w_i sym(slot i) (FP64 sums); slot i = sym(slot i) - M for i < m.
+cudaError_t launch_deviations(float* Mall, const float* w, int m, int d, cudaStream_t s);
+// out[j] = ||slot j||_2 for j < nmat (symmetric slots) by Lanczos with full
+// reorthogonalisation; V holds nmat x lanczos_steps(d) x d floats.
+cudaError_t launch_lanczos_norms(const float* Mall, int nmat, int d, float* V, double* out, cudaStream_t s);
+int lanczos_steps(int d);
+size_t lanczos_smem(int d);
+
 // FP64 d x k (row-major) <-> FP32 d x K padded blocks
 cudaError_t launch_pack(const double* src, float* dst, int batch, int d, int k, int K, cudaStream_t s);
 cudaError_t launch_unpack(const float* src, double* dst, int batch, int d, int k, int K, cudaStream_t s);

@@ -333,3 +333,71 @@ def test_bf16x2_planes_represent_fp32_within_2_to_minus_17():
     assert np.all(np.abs(v - a64) <= 2.0 ** -17 * np.abs(a64))
     short = (a.view(np.uint32) & np.uint32(0xFF)) == 0   # 16 significant bits: exact
     assert np.array_equal(v[short], a64[short])
+
+
+# --------------------------------------------------------------------------- eta (Def. 2)
+
+def _axis_partitions(xs, sizes, d):
+    """Partition i holds s_i copies of the row x_i e_i, so M_i = x_i^2 e_i e_i^T."""
+    return [np.tile(np.eye(d)[i] * x, (s, 1)) for i, (x, s) in enumerate(zip(xs, sizes))]
+
+
+def test_eta_closed_form_for_axis_aligned_partitions():
+    """With M_i = x_i^2 e_i e_i^T, M = diag(p_j x_j^2) and M_i - M = diag((delta_ij - p_j) x_j^2),
+    so ||M_i - M||_2 = max((1 - p_i) x_i^2, max_{j != i} p_j x_j^2) and ||M||_2 = max_j p_j x_j^2.
+    Unequal sizes make a 1/n-for-1/s_i or unweighted-mean slip show."""
+    cases = [((1.0, 1.0), (5, 5)), ((2.0, 0.5, 1.5), (3, 10, 7)), ((0.3, 3.0, 1.0, 2.0), (40, 1, 9, 20))]
+    for xs, sizes in cases:
+        q = len(xs)
+        parts = _axis_partitions(xs, sizes, q + 2)
+        p = np.array(sizes, dtype=np.float64) / sum(sizes)
+        x2 = np.array(xs) ** 2
+        want = [max((1 - p[i]) * x2[i], max(p[j] * x2[j] for j in range(q) if j != i)) for i in range(q)]
+        normM = float(np.max(p * x2))
+        e, norms = O.eta(parts)
+        np.testing.assert_allclose(norms[:-1], want, rtol=1e-13)
+        assert abs(norms[-1] - normM) <= 1e-13 * normM
+        assert abs(e - max(want) / normM) <= 1e-13
+    assert abs(O.eta(_axis_partitions((1.0, 1.0), (5, 5), 3))[0] - 1.0) < 1e-14
+
+
+def test_eta_vanishes_without_local_differences_and_is_scale_free():
+    """One partition, or identical partitions, give M_i = M (eta = 0); scaling A
+    scales every M_i and M alike; more rows per worker shrink eta for iid rows
+    (the remark after Def. 2)."""
+    _, parts = _small_problem(seed=41)
+    assert O.eta(parts[:1])[0] == 0.0
+    assert O.eta([parts[0]] * 3)[0] < 1e-14
+    e1 = O.eta(parts)[0]
+    assert abs(O.eta([2.0 * P for P in parts])[0] - e1) < 1e-12 * e1
+    lam = np.array([9.0, 5.0, 3.0, 1.0])
+    small = synth.split_rows(synth.spiked_rows(400, 12, lam, 0.3, 44, out_dtype=np.float64, threads=1), [100] * 4)
+    big = synth.split_rows(synth.spiked_rows(40_000, 12, lam, 0.3, 44, out_dtype=np.float64, threads=1),
+                           [10_000] * 4)
+    assert O.eta(big)[0] < 0.3 * O.eta(small)[0]
+
+
+# --------------------------------------------------------------------------- iteration rank r > k
+
+def test_larger_iteration_rank_nests_the_target_subspace():
+    """Alg. 1 takes an iteration rank r >= k.  At p = 1 the iterate spans M^t Y_0,
+    so when Y_0's first k columns are the k-column start, span(Z^(k)) lies in
+    span(Z^(r)) and dist(Z^(r), U_k) = ||(I - Z^(r) Z^(r)T) U_k||_2 is never the
+    larger one; the first k Ritz vectors of the r-column iterate approach U_k
+    at least as fast."""
+    _, parts = _small_problem(seed=43)
+    k, r = 2, 4
+    Y0 = _rng(45).standard_normal((12, r))
+    V, _ = O.top_k_truth(parts, k)
+    last = None
+    for T in (1, 3, 6):
+        Zk = O.localpower(parts, k, [1] * T, "sign", Y0[:, :k])["Z"]
+        Zr = O.localpower(parts, r, [1] * T, "sign", Y0)["Z"]
+        assert np.linalg.norm(Zk - Zr @ (Zr.T @ Zk), 2) < 1e-10
+        dk, dr = O.subspace_dist(Zk, V), O.subspace_dist(Zr, V)
+        assert dr <= dk + 1e-12
+        Zr_ritz, _ = O.ritz(parts, Zr)
+        assert O.subspace_dist(Zr_ritz[:, :k], V) <= dk + 1e-12
+        if last is not None:
+            assert dr < last
+        last = dr
