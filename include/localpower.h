@@ -126,7 +126,9 @@ lp_status lp_load_partitions(lp_ctx* ctx, int m, const int64_t* rows, int64_t d,
  * Z_i <- orth(Y_i), then one aggregation Y <- sum_i p_i Y_i D_i and Z <- orth(Y).
  * D_i = I whenever p_t = 1 (the remark after eq. (4)).  The base partition for
  * alignment is the one with the most rows (lowest index on ties).
- *   k              target rank, 1 <= k <= min(LP_MAX_K, d, min_i s_i).
+ *   k              rank of the iterate (Alg. 1's iteration rank r >= the target
+ *                  rank), 1 <= k <= min(LP_MAX_K, d, min_i s_i).  For a target
+ *                  rank below k, use LP_FLAG_RITZ and take the leading columns.
  *   p_schedule[T]  p_t >= 1 (a decaying p is just a schedule, Sec. 3).
  *   y0             host pointer, d x k row-major FP64: the Gaussian start block
  *                  Y_0 (Alg. 1 initialisation); the library computes Z_0 = orth(Y_0).
