@@ -445,19 +445,20 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
             acc[aa][h].x += __shfl_xor_sync(0xffffffffu, acc[aa][h].x, off);
             acc[aa][h].y += __shfl_xor_sync(0xffffffffu, acc[aa][h].y, off);
           }
+      // per-warp partial W in row-major R x K blocks: a micro-tile row is 16
+      // contiguous bytes and the lanes' rows are contiguous, so both the writes
+      // and the column-wise reads below are conflict free
       if (sp == 0) {
-        float* dst = red + (size_t(warp) * MT + mt) * 16;
 #pragma unroll
         for (int aa = 0; aa < 4; ++aa)
-          *reinterpret_cast<float4*>(dst + 4 * aa) = make_float4(acc[aa][0].x, acc[aa][0].y, acc[aa][1].x, acc[aa][1].y);
+          *reinterpret_cast<float4*>(red + (size_t(warp) * R + rg + RG * aa) * K + 4 * jg) =
+              make_float4(acc[aa][0].x, acc[aa][0].y, acc[aa][1].x, acc[aa][1].y);
       }
       __syncthreads();
       for (int e = tid; e < R * K; e += kThreads2) {
-        const int r = e / K, j = e % K;
-        const int m2 = (r % RG) * (K / 4) + j / 4, el = (r / RG) * 4 + (j & 3);
         float sum = 0.f;
 #pragma unroll 4
-        for (int w = 0; w < 16; ++w) sum += red[(size_t(w) * MT + m2) * 16 + el];
+        for (int w = 0; w < 16; ++w) sum += red[size_t(w) * R * K + e];
         Ws[e] = sum;
       }
       __syncthreads();
