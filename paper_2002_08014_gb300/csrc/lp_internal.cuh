@@ -43,6 +43,10 @@ struct StepArgs {
 
 // Returns cudaErrorInvalidConfiguration when no SIMT instantiation fits.
 cudaError_t launch_step_simt(const StepArgs& a, lp_dtype dtype, int K, cudaStream_t s);
+// FP32 SIMT step with Z_i resident in tensor memory (K = 16, d <= 1024); the FP32
+// dispatch of launch_step_simt prefers it where it is supported.
+bool step_simt_tmem_supported(int d, int64_t ld, int K);
+cudaError_t launch_step_simt_tmem(const StepArgs& a, cudaStream_t s);
 // Shared memory the SIMT step needs (0 if unsupported); used to validate up front.
 size_t step_simt_smem(int d, int64_t ld, lp_dtype dtype, int K, int* rows_per_tile);
 

@@ -350,6 +350,8 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
   const int zld = a.zld > 0 ? a.zld : K, pld = a.pld > 0 ? a.pld : K;
   const float* A = static_cast<const float*>(a.A);
   const int cpr = static_cast<int>(a.ld / 4);  // 16-byte chunks per row
+  // row-tile copy plan: rows per pass, this thread's first row and chunk (cpr <= threads)
+  const int cp_rstep = kThreads2 / cpr, cp_r0 = tid / cpr, cp_ch = tid % cpr;
   const int sp = lane / MT, mt = lane % MT;
   const int rg = mt / (K / 4), jg = mt % (K / 4);
   const int s_id = warp * SPW + sp;
@@ -384,14 +386,17 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
         *reinterpret_cast<float4*>(Zs + (size_t(q) * 4 + (i ^ (q & 1))) * K + 4 * jz) = v;
       }
     }
+    // thread tid copies chunk cp_ch of rows cp_r0, cp_r0 + cp_rstep, ... (rows past
+    // the segment are zero-filled)
     auto issue = [&](int t, float* buf) {
       const int64_t r0 = sg.row0 + int64_t(t) * R;
-      for (int e = tid; e < R * cpr; e += kThreads2) {
-        const int r = e / cpr, ch = e % cpr;
-        const int64_t grow = r0 + r;
-        const bool ok = grow < sg.row1;
-        cp_async16(buf + size_t(r) * g.lds + ch * 4, A + (ok ? grow : sg.row0) * a.ld + int64_t(ch) * 4, ok ? 16 : 0);
-      }
+      if (cp_r0 < cp_rstep)
+        for (int r = cp_r0; r < R; r += cp_rstep) {
+          const int64_t grow = r0 + r;
+          const bool ok = grow < sg.row1;
+          cp_async16(buf + size_t(r) * g.lds + cp_ch * 4, A + (ok ? grow : sg.row0) * a.ld + int64_t(cp_ch) * 4,
+                     ok ? 16 : 0);
+        }
       cp_async_commit();
     };
     issue(0, buf0);
@@ -516,7 +521,7 @@ cudaError_t launch_two(const StepArgs& a, const Geo2& g, size_t bytes, cudaStrea
 // Chooses the row tile (16, else 8) whose shared memory fits; returns false if none.
 template <int K>
 bool simt2_pick(int d, int64_t ld, int* R, Geo2* g, size_t* bytes) {
-  if (d > 2 * kThreads2 || (d + kThreads2 - 1) / kThreads2 * K > 64) return false;
+  if (d > 2 * kThreads2 || ld / 4 > kThreads2 || (d + kThreads2 - 1) / kThreads2 * K > 64) return false;
   const Geo2 g16 = Simt2<K, 16>::geo(d, ld);
   if (32 % Simt2<K, 16>::MT == 0 && Simt2<K, 16>::bytes(g16) <= kSmemLimit2) {
     *R = 16; *g = g16; *bytes = Simt2<K, 16>::bytes(g16);
@@ -628,7 +633,9 @@ size_t smem_for(int d, int64_t ld, int K, int* rows) {
 
 cudaError_t launch_step_simt(const StepArgs& a, lp_dtype dtype, int K, cudaStream_t s) {
   switch (dtype) {
-    case LP_F32: return v2_supported(a.d, a.ld, K) ? launch_f32(a, K, s) : launch_k<float>(a, K, s);
+    case LP_F32:
+      if (step_simt_tmem_supported(a.d, a.ld, K)) return launch_step_simt_tmem(a, s);
+      return v2_supported(a.d, a.ld, K) ? launch_f32(a, K, s) : launch_k<float>(a, K, s);
     case LP_BF16: return launch_k<uint16_t>(a, K, s);
     case LP_FP8_E4M3: return launch_k<uint8_t>(a, K, s);
   }
