@@ -179,7 +179,7 @@ def run_reference(args):
 # dram__bytes_write.sum) of each step kernel at n = 262,144, d = 1,024, k = 16; the traffic
 # grows with the rows, so a full launch's traffic is this ratio times its algorithmic bytes.
 # Keys: (path, planes, cache hints).  Configurations without a capture report null.
-DRAM_RATIO = {(0, 0, 0): 1079.3 / 1073.7,   # SIMT FP32
+DRAM_RATIO = {(0, 0, 0): 1081.1 / 1073.7,   # SIMT FP32, Z_i in TMEM
               (1, 1, 0): 544.8 / 536.9,     # resident tcgen05, BF16
               (2, 1, 0): 750.1 / 536.9,     # streaming tcgen05, BF16, no hints
               (2, 1, 1): 606.8 / 536.9,     # streaming tcgen05, BF16, evict_last / evict_first hints
@@ -194,6 +194,17 @@ def _traffic(path, planes, hints, launch_bytes, d=1024, k=16):
 KERNELS = {0: "step_simt2_kernel (SIMT FP32 fused A_i^T (A_i Z_i))",
            1: "step_tc_kernel (tcgen05, tile resident in shared memory, cluster-split d)",
            2: "step_tcs_kernel (tcgen05 streaming, second pass re-read from L2)"}
+
+
+def _kernel(path, dtype="f32", d=1024, k=16):
+    """Name of the step kernel a solve ran (lp_stats.path plus the shape for the SIMT path)."""
+    if path != 0:
+        return KERNELS[path]
+    if dtype != "f32":
+        return "step_simt_kernel (SIMT, rows widened to FP32 in shared memory)"
+    if 8 < k <= 16 and d <= 1024:
+        return "step_simt_tmem_kernel (SIMT FP32 fused A_i^T (A_i Z_i), Z_i resident in TMEM)"
+    return KERNELS[0]
 
 
 def _config(c, sched, name: str = WORKLOAD):
@@ -251,7 +262,7 @@ def run_lowprec(args):
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": _config(c, sched, "lowprec"),
             "solves_per_s": s["solves_per_s"], "latency_ms": s["latency_ms"], "clocks": clk,
             "gpu_launches": s["launches"], "e2e": None, "autotune": choice,
-            "roofline": {"kernel": KERNELS[s["path"]], "bound": "hbm",
+            "roofline": {"kernel": _kernel(s["path"], "bf16", c["d"], c["k"]), "bound": "hbm",
                          "achieved": gbs_k, "peak": hbm_peak, "unit": "GB/s", "frac": gbs_k / hbm_peak,
                          "traffic": None, "launch_ms": s["step_ms"], "peak_source": f"{peak_src} HBM copy bandwidth"}}
     line["orthonormality"] = float(np.abs(Z.T @ Z - np.eye(k)).max())
@@ -267,7 +278,7 @@ def run_lowprec(args):
         ms8, st8, Z8, sig8, clk8 = _timed(torch, dist, world, dev, stream, lp8, k, sched, args.agg, 1, Clocks(local))
         s8 = _summary(world, 1, ms8, st8, 1, c)
         lp8.close()
-        fp8 = {"dtype": "e4m3 codes x FP32 row scales, FP32 accumulation", "step_kernel": KERNELS[s8["path"]],
+        fp8 = {"dtype": "e4m3 codes x FP32 row scales, FP32 accumulation", "step_kernel": _kernel(s8["path"], "e4m3", c["d"], c["k"]),
                "gbs": s8["gbs"], "solves_per_s": s8["solves_per_s"], "ms_per_solve": s8["ms_per_solve"],
                "step_launch_ms": s8["step_ms"], "clocks": clk8,
                "note": "FP8 runs on the SIMT kernel: the tensor-core kernels take BF16 operands only"}
@@ -326,7 +337,7 @@ def run_plain(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _config(c, sched, "plain"), "solves_per_s": s["solves_per_s"], "latency_ms": s["latency_ms"],
             "clocks": clk, "gpu_launches": s["launches"], "e2e": None,
-            "launches_per_solve": s["launches"] / solves, "step_kernel": KERNELS[s["path"]],
+            "launches_per_solve": s["launches"] / solves, "step_kernel": _kernel(s["path"], "f32", c["d"], c["k"]),
             "dist_to_oracle": oracle.subspace_dist(oracle.orth(Z), ref["Z"])}
     if rank == 0:
         print(json.dumps(line))
@@ -662,7 +673,7 @@ def run_kernels(args):
                     ms.append(st["ms_step_kernels"])
             best = min(ms[1:])
             out[f"{dtype}{'_resident' if flags else ''}"] = {
-                "kernel": KERNELS[st["path"]], "launch_ms": best, "gbs": n * d * eb / (best / 1e3) / 1e9}
+                "kernel": _kernel(st["path"], dtype if dtype == "f32" else "bf16", d, k), "launch_ms": best, "gbs": n * d * eb / (best / 1e3) / 1e9}
         except Exception as e:
             out[f"{dtype}{'_resident' if flags else ''}"] = {"error": str(e)[:200]}
     print(json.dumps({"workload": "kernels", "n": n, "d": d, "k": k, "m": m, "results": out}))
@@ -804,7 +815,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(c, sched),
             "solves_per_s": f32["solves_per_s"], "latency_ms": f32["latency_ms"], "clocks": clk,
             "gpu_launches": f32["launches"], "e2e": e2e,
-            "roofline": {"kernel": KERNELS[f32["path"]], "bound": "alu",
+            "roofline": {"kernel": _kernel(f32["path"], "f32", c["d"], c["k"]), "bound": "alu",
                          "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
                          "traffic": _traffic(0, 0, 0, f32["launch_bytes"]), "traffic_unit": "bytes per launch",
                          "launch_ms": f32["step_ms"],
