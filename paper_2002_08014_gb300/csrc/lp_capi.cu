@@ -64,6 +64,7 @@ struct lp_ctx {
   int tcs_state[3] = {0, 0, 0};
   int tcs_G = 0;  // clusters the device segment table below was built for
   int nslots_tcs = 0;
+  int max_slots[3] = {0, 0, 0};  // most slots of one partition, per path (SIMT, resident, streaming)
   Segment* dSegsTcs = nullptr;
   int* dSegPtrTcs = nullptr;
   int* dSlotBeginTcs = nullptr;
@@ -317,6 +318,12 @@ cudaError_t record_event(cudaEvent_t e, cudaStream_t s) {
                                                                              : cudaEventRecordDefault);
 }
 
+int max_slots_in(const std::vector<int>& slot_begin) {
+  int mx = 0;
+  for (size_t i = 0; i + 1 < slot_begin.size(); ++i) mx = std::max(mx, slot_begin[i + 1] - slot_begin[i]);
+  return mx;
+}
+
 const int* slot_begin_of(const lp_ctx* c) {
   return c->path == PATH_TCS ? c->dSlotBeginTcs : c->path == PATH_TC ? c->dSlotBeginTc : c->dSlotBegin;
 }
@@ -489,6 +496,7 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
   std::vector<int> seg_ptr, slot_begin;
   build_segments(c, c->grid, segs, seg_ptr, slot_begin);
   c->nslots = static_cast<int>(segs.size());
+  c->max_slots[PATH_SIMT] = max_slots_in(slot_begin);
   // Tensor-core step kernel (BF16): one segment table per cluster of CTAs.
   std::vector<Segment> segs_tc;
   std::vector<int> seg_ptr_tc, slot_begin_tc;
@@ -498,6 +506,7 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
     c->tc.nclusters = G;
     build_segments(c, G, segs_tc, seg_ptr_tc, slot_begin_tc);
     c->nslots_tc = static_cast<int>(segs_tc.size());
+    c->max_slots[PATH_TC] = max_slots_in(slot_begin_tc);
     c->tc_ready = true;
   }
   std::vector<float> invs(m), w(m);
@@ -687,6 +696,7 @@ static lp_status ensure_tcs(lp_ctx* c, int k) {
     // pageable sources: make sure the copies have read them before the vectors go
     LP_CUDA(cudaStreamSynchronize(c->stream));
     c->nslots_tcs = static_cast<int>(segs.size());
+    c->max_slots[PATH_TCS] = max_slots_in(slot_begin);
     c->tcs_G = G;
   }
   c->tcs_cur = &p;
@@ -749,7 +759,7 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
                                       "local orth")))
         return st;
       if ((st = launch_step(c, K, j == 0 ? c->dZ : c->dZl, j == 0 ? 0 : zs, timing))) return st;
-      if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream),
+      if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream, c->max_slots[c->path]),
                              "reduce")))
         return st;
       c->stats.local_steps++;
@@ -785,7 +795,7 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
   }
   if (c->ritz) {
     if ((st = launch_step(c, K, c->dZ, 0, timing))) return st;
-    if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream), "reduce")))
+    if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream, c->max_slots[c->path]), "reduce")))
       return st;
     if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, nullptr, 0, m, d, K, c->dMZ, c->stream),
                            "aggregate")))
@@ -1077,7 +1087,7 @@ lp_status lp_power_step(lp_ctx* c, int k, const double* z, int z_shared, double*
   float* Zt = z_shared ? c->dZ : c->dZl;
   if ((st = check_launch(c, lp::launch_pack(dz, Zt, nb, d, k, K, c->stream), "pack"))) return st;
   if ((st = launch_step(c, K, Zt, z_shared ? 0 : int64_t(d) * K, false))) return st;
-  if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, c->m, d, K, c->dYl, c->stream),
+  if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, c->m, d, K, c->dYl, c->stream, c->max_slots[c->path]),
                          "reduce")))
     return st;
   double* dst = space == LP_DEVICE ? y_out : c->dStage;
@@ -1136,7 +1146,7 @@ lp_status lp_eta(lp_ctx* c, double* eta, double* norms) {
     for (int c0 = 0; c0 < d; c0 += kb) {
       if ((s2 = check_launch(c, lp::launch_identity_block(c->dZ, d, K, c0, c->stream), "identity block"))) return s2;
       if ((s2 = launch_step(c, K, c->dZ, 0, false))) return s2;
-      if ((s2 = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream),
+      if ((s2 = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream, c->max_slots[c->path]),
                              "reduce")))
         return s2;
       if ((s2 = check_launch(

@@ -121,9 +121,10 @@ void set_no_context_error(const char* msg);
 inline void set_no_context_error(const std::string& msg) { set_no_context_error(msg.c_str()); }
 
 // ---- small kernels --------------------------------------------------------
-// Y_i = scale_i * sum_{slot in [slot_begin[i], slot_begin[i+1])} P[slot]
+// Y_i = scale_i * sum_{slot in [slot_begin[i], slot_begin[i+1])} P[slot]; max_slots (the most
+// slots any partition has) picks how many threads share one output.
 cudaError_t launch_reduce(const float* P, const int* slot_begin, const float* scale, int m, int d, int K,
-                          float* Y, cudaStream_t s);
+                          float* Y, cudaStream_t s, int max_slots);
 // Z_b = orth(Y_b) (CholQR2, FP32 data, FP64 k x k factors), batch blocks of d x K.
 cudaError_t launch_cholqr2(const float* Y, float* Z, int batch, int d, int k, int K, int* status, cudaStream_t s);
 // G_i = aligning matrices (K x K, FP32) for agg in {SIGN, OPT}; base gets I.

@@ -73,28 +73,46 @@ __global__ void unpack_kernel(const float* __restrict__ src, double* __restrict_
 }
 
 // ---------------------------------------------------------------- reduce
+// G adjacent threads share one float4 of Y_i: thread g of the group sums slots
+// sb + g, sb + g + G, ... in order (four loads in flight), then the group adds
+// its G partials by an xor butterfly.  The order is fixed for a given G, so
+// results are reproducible; G > 1 only when partitions have many slots (small
+// problems spread over many CTAs), where it cuts the chain of dependent loads.
+template <int G>
 __global__ void reduce_kernel(const float* __restrict__ P, const int* __restrict__ slot_begin,
                               const float* __restrict__ scale, int d, int K, float* __restrict__ Y) {
   const int i = blockIdx.y;
   const int64_t n4 = int64_t(d) * K / 4;
-  const int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (e >= n4) return;
+  const int g = threadIdx.x % G;
+  const int64_t e = blockIdx.x * int64_t(blockDim.x / G) + threadIdx.x / G;
+  const bool live = e < n4;
+  if (G == 1 && !live) return;
   const int sb = slot_begin[i], se = slot_begin[i + 1];
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  int s = sb;
-  for (; s + 4 <= se; s += 4) {  // four loads in flight, added in slot order
-    float4 v[4];
+  if (live) {
+    int s = sb + g;
+    for (; s + 3 * G < se; s += 4 * G) {
+      float4 v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = reinterpret_cast<const float4*>(P + int64_t(s + q) * d * K)[e];
+      for (int q = 0; q < 4; ++q) v[q] = reinterpret_cast<const float4*>(P + int64_t(s + q * G) * d * K)[e];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      acc.x += v[q].x; acc.y += v[q].y; acc.z += v[q].z; acc.w += v[q].w;
+      for (int q = 0; q < 4; ++q) {
+        acc.x += v[q].x; acc.y += v[q].y; acc.z += v[q].z; acc.w += v[q].w;
+      }
+    }
+    for (; s < se; s += G) {
+      const float4 v = reinterpret_cast<const float4*>(P + int64_t(s) * d * K)[e];
+      acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
     }
   }
-  for (; s < se; ++s) {
-    const float4 v = reinterpret_cast<const float4*>(P + int64_t(s) * d * K)[e];
-    acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
   }
+  if (!live || g != 0) return;
   const float sc = scale[i];
   acc.x *= sc; acc.y *= sc; acc.z *= sc; acc.w *= sc;
   reinterpret_cast<float4*>(Y + int64_t(i) * d * K)[e] = acc;
@@ -695,10 +713,19 @@ cudaError_t launch_unpack(const float* src, double* dst, int batch, int d, int k
 }
 
 cudaError_t launch_reduce(const float* P, const int* slot_begin, const float* scale, int m, int d, int K, float* Y,
-                          cudaStream_t s) {
+                          cudaStream_t s, int max_slots) {
   const int64_t n4 = int64_t(d) * K / 4;
-  dim3 grid(static_cast<unsigned>((n4 + kT - 1) / kT), static_cast<unsigned>(m));
-  reduce_kernel<<<grid, kT, 0, s>>>(P, slot_begin, scale, d, K, Y);
+  int G = 1;
+  while (G < 32 && max_slots > 4 * G) G <<= 1;
+  dim3 grid(static_cast<unsigned>((n4 + kT / G - 1) / (kT / G)), static_cast<unsigned>(m));
+  switch (G) {
+    case 1: reduce_kernel<1><<<grid, kT, 0, s>>>(P, slot_begin, scale, d, K, Y); break;
+    case 2: reduce_kernel<2><<<grid, kT, 0, s>>>(P, slot_begin, scale, d, K, Y); break;
+    case 4: reduce_kernel<4><<<grid, kT, 0, s>>>(P, slot_begin, scale, d, K, Y); break;
+    case 8: reduce_kernel<8><<<grid, kT, 0, s>>>(P, slot_begin, scale, d, K, Y); break;
+    case 16: reduce_kernel<16><<<grid, kT, 0, s>>>(P, slot_begin, scale, d, K, Y); break;
+    default: reduce_kernel<32><<<grid, kT, 0, s>>>(P, slot_begin, scale, d, K, Y); break;
+  }
   return cudaGetLastError();
 }
 

@@ -374,18 +374,6 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
   for (int si = sb; si < se; ++si) {
     const Segment sg = a.segs[si];
     const int ntiles = static_cast<int>((sg.row1 - sg.row0 + R - 1) / R);
-    if (sg.part != cur_part) {
-      __syncthreads();
-      cur_part = sg.part;
-      const float* Zg = a.Z + a.z_stride * sg.part;
-      for (int e = tid; e < g.Qp * 4 * (K / 4); e += kThreads2) {
-        const int c = e / (K / 4), jz = e % (K / 4);
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c < d) v = *reinterpret_cast<const float4*>(Zg + size_t(c) * zld + 4 * jz);
-        const int q = c >> 2, i = c & 3;
-        *reinterpret_cast<float4*>(Zs + (size_t(q) * 4 + (i ^ (q & 1))) * K + 4 * jz) = v;
-      }
-    }
     // thread tid copies chunk cp_ch of rows cp_r0, cp_r0 + cp_rstep, ... (rows past
     // the segment are zero-filled)
     auto issue = [&](int t, float* buf) {
@@ -399,7 +387,19 @@ __global__ void __launch_bounds__(kThreads2, 1) step_simt2_kernel(StepArgs a, Ge
         }
       cp_async_commit();
     };
-    issue(0, buf0);
+    issue(0, buf0);  // the first tile loads while Z_i is staged
+    if (sg.part != cur_part) {
+      __syncthreads();
+      cur_part = sg.part;
+      const float* Zg = a.Z + a.z_stride * sg.part;
+      for (int e = tid; e < g.Qp * 4 * (K / 4); e += kThreads2) {
+        const int c = e / (K / 4), jz = e % (K / 4);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < d) v = *reinterpret_cast<const float4*>(Zg + size_t(c) * zld + 4 * jz);
+        const int q = c >> 2, i = c & 3;
+        *reinterpret_cast<float4*>(Zs + (size_t(q) * 4 + (i ^ (q & 1))) * K + 4 * jz) = v;
+      }
+    }
     for (int t = 0; t < ntiles; ++t) {
       const float* T = (t & 1) ? buf1 : buf0;
       if (t + 1 < ntiles) {

@@ -119,6 +119,20 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
   for (int si = sb; si < se; ++si) {
     const Segment sg = a.segs[si];
     const int ntiles = static_cast<int>((sg.row1 - sg.row0 + kR - 1) / kR);
+    // thread tid copies chunk cp_ch of rows cp_r0, cp_r0 + cp_rstep, ... (rows past
+    // the segment are zero-filled)
+    auto issue = [&](int t, float* buf) {
+      const int64_t r0 = sg.row0 + int64_t(t) * kR;
+      if (cp_r0 < cp_rstep)
+        for (int r = cp_r0; r < kR; r += cp_rstep) {
+          const int64_t grow = r0 + r;
+          const bool ok = grow < sg.row1;
+          cp_async16(buf + size_t(r) * g.lds + cp_ch * 4, A + (ok ? grow : sg.row0) * a.ld + int64_t(cp_ch) * 4,
+                     ok ? 16 : 0);
+        }
+      cp_async_commit();
+    };
+    issue(0, buf0);  // the first tile loads while Z_i is staged
     if (sg.part != cur_part) {
       tc_sync();  // every warp's TMEM reads of the previous Z_i have completed
       cur_part = sg.part;
@@ -135,20 +149,6 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
       tmem_wait_st();
       tc_sync();
     }
-    // thread tid copies chunk cp_ch of rows cp_r0, cp_r0 + cp_rstep, ... (rows past
-    // the segment are zero-filled)
-    auto issue = [&](int t, float* buf) {
-      const int64_t r0 = sg.row0 + int64_t(t) * kR;
-      if (cp_r0 < cp_rstep)
-        for (int r = cp_r0; r < kR; r += cp_rstep) {
-          const int64_t grow = r0 + r;
-          const bool ok = grow < sg.row1;
-          cp_async16(buf + size_t(r) * g.lds + cp_ch * 4, A + (ok ? grow : sg.row0) * a.ld + int64_t(cp_ch) * 4,
-                     ok ? 16 : 0);
-        }
-      cp_async_commit();
-    };
-    issue(0, buf0);
     for (int t = 0; t < ntiles; ++t) {
       const float* Tt = (t & 1) ? buf1 : buf0;
       if (t + 1 < ntiles) {

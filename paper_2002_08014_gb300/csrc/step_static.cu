@@ -124,6 +124,8 @@ extern "C" lp_status lp_power_step_static(const float* A, int m, const int64_t* 
     slot_begin[m] = static_cast<int>(segs.size());
   }
   const int nslots = static_cast<int>(segs.size());
+  int max_slots = 0;
+  for (int i = 0; i < m; ++i) max_slots = std::max(max_slots, slot_begin[i + 1] - slot_begin[i]);
 
   // Carve the static array.
   unsigned char* cur = static_cast<unsigned char*>(base);
@@ -166,7 +168,7 @@ extern "C" lp_status lp_power_step_static(const float* A, int m, const int64_t* 
   a.z_stride = 0;
   a.P = dP;
   a.grid = G;
-  if ((e = lp::launch_step_simt(a, LP_F32, K, s)) || (e = lp::launch_reduce(dP, dSlotBegin, dInvS, m, di, K, dY, s)) ||
+  if ((e = lp::launch_step_simt(a, LP_F32, K, s)) || (e = lp::launch_reduce(dP, dSlotBegin, dInvS, m, di, K, dY, s, max_slots)) ||
       (e = lp::launch_unpack(dY, y, m, di, k, K, s)))
     return fail(LP_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
   // The host tables above are copied from pageable memory, so the copies have
