@@ -759,7 +759,8 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
                                       "local orth")))
         return st;
       if ((st = launch_step(c, K, j == 0 ? c->dZ : c->dZl, j == 0 ? 0 : zs, timing))) return st;
-      if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream, c->max_slots[c->path]),
+      if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream,
+                                                  c->max_slots[c->path]),
                              "reduce")))
         return st;
       c->stats.local_steps++;

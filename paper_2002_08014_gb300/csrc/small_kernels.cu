@@ -191,7 +191,7 @@ __device__ bool warp_jacobi_f32(float* C, float* V, int k, int K) {
 // Y[r][4bi..4bi+3]^T Y[r][4bj..4bj+3] over its rows in FP32 registers (16 FMAs
 // per two 16-byte loads); the slices are added in FP32 through shared memory.
 template <int K>
-__device__ void gram_fp32(const float* __restrict__ Y, int d, float* red, double* G) {
+__device__ void gram_fp32(const float* Y, int d, float* red, double* G) {
   constexpr int NB = K / 4, NBB = NB * NB, S = kT / NBB;
   const int t = threadIdx.x;
   const int blk = t % NBB, sl = t / NBB;
@@ -371,15 +371,14 @@ __device__ void forward_rows(const float* Yin, float* Zout, const float* Lf, con
   }
 }
 
+// Z = orth(Y) of one d x K block by the CTA.  Y and Z may be written earlier in
+// the same kernel (the fused reduction writes Y; the second pass reads Z).
 template <int K>
-__global__ void __launch_bounds__(kT) cholqr2_kernel(const float* __restrict__ Yall, float* __restrict__ Zall, int d,
-                                                     int k, int* status) {
+__device__ void cholqr2_block(const float* Y, float* Z, int d, int k, int* status) {
   __shared__ __align__(16) double G[K * K];
   __shared__ __align__(16) float Lf[K * K];
   __shared__ float invd[K];
   __shared__ __align__(16) float red[kT * 16];
-  const float* Y = Yall + int64_t(blockIdx.x) * d * K;
-  float* Z = Zall + int64_t(blockIdx.x) * d * K;
   for (int pass = 0; pass < 2; ++pass) {
     const float* src = pass == 0 ? Y : Z;
     gram_fp32<K>(src, d, red, G);
@@ -392,6 +391,13 @@ __global__ void __launch_bounds__(kT) cholqr2_kernel(const float* __restrict__ Y
     __syncthreads();
   }
 }
+
+template <int K>
+__global__ void __launch_bounds__(kT) cholqr2_kernel(const float* __restrict__ Yall, float* __restrict__ Zall, int d,
+                                                     int k, int* status) {
+  cholqr2_block<K>(Yall + int64_t(blockIdx.x) * d * K, Zall + int64_t(blockIdx.x) * d * K, d, k, status);
+}
+
 
 // ---------------------------------------------------------------- align
 // One CTA per partition.  G_i (K x K float, row-major) = D_i (sign) or O_i (OPT).

@@ -69,6 +69,7 @@ def _relF(a, b):
     ([40, 41, 42], 64, 32),            # k = 32
     ([20], 7, 1),                      # tiny d, k = 1
     ([300, 29], 512, 24),              # k padded to 32, partition of 29 rows
+    ([13] * 40 + [600], 200, 12),      # many tiny partitions: CTAs restage Z_i often (k padded to 16)
 ])
 def test_power_step_matches_oracle(gpu_lib, dtype, sizes, d, k):
     stored, exact, scales = _parts(sizes, d, 100 + d + k, dtype)
