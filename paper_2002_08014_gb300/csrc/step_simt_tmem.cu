@@ -77,26 +77,31 @@ __device__ __forceinline__ void fma_row(float2 (&acc)[kK / 2], float a, const ui
     acc[j] = __ffma2_rn(a2, make_float2(__uint_as_float(z[2 * j]), __uint_as_float(z[2 * j + 1])), acc[j]);
 }
 
-template <int CPT>
+// FULL: d = ld = 1024 exactly, so the lane steps, tile stride and copy plan are
+// compile-time constants (loops unroll, addresses become immediate offsets).
+template <int CPT, bool FULL>
 __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, GeoT g) {
   extern __shared__ __align__(16) float smt[];
   __shared__ uint32_t tmem_holder;
+  const int T = FULL ? 32 : g.T;
+  const int lds = FULL ? 1024 : g.lds;
+  const int d = FULL ? 1024 : a.d;
+  const int64_t ld = FULL ? 1024 : a.ld;
   float* buf0 = smt;
-  float* buf1 = buf0 + kR * g.lds;
-  float* Ws = buf1 + kR * g.lds;  // R x K
+  float* buf1 = buf0 + kR * lds;
+  float* Ws = buf1 + kR * lds;  // R x K
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int d = a.d;
   const int zld = a.zld > 0 ? a.zld : kK, pld = a.pld > 0 ? a.pld : kK;
   const float* A = static_cast<const float*>(a.A);
-  const int cpr = static_cast<int>(a.ld / 4);  // 16-byte chunks per row
+  const int cpr = static_cast<int>(ld / 4);  // 16-byte chunks per row
   // row-tile copy plan: rows per pass, this thread's first row and chunk (cpr <= threads)
   const int cp_rstep = kThr / cpr, cp_r0 = tid / cpr, cp_ch = tid % cpr;
 
   for (int r = 0; r < kR; ++r)
-    for (int c = static_cast<int>(a.ld) + tid; c < g.lds; c += kThr) {
-      buf0[r * g.lds + c] = 0.f;
-      buf1[r * g.lds + c] = 0.f;
+    for (int c = static_cast<int>(ld) + tid; c < lds; c += kThr) {
+      buf0[r * lds + c] = 0.f;
+      buf1[r * lds + c] = 0.f;
     }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_holder)),
@@ -127,7 +132,7 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
         for (int r = cp_r0; r < kR; r += cp_rstep) {
           const int64_t grow = r0 + r;
           const bool ok = grow < sg.row1;
-          cp_async16(buf + size_t(r) * g.lds + cp_ch * 4, A + (ok ? grow : sg.row0) * a.ld + int64_t(cp_ch) * 4,
+          cp_async16(buf + size_t(r) * lds + cp_ch * 4, A + (ok ? grow : sg.row0) * ld + int64_t(cp_ch) * 4,
                      ok ? 16 : 0);
         }
       cp_async_commit();
@@ -138,7 +143,7 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
       cur_part = sg.part;
       const float* Zg = a.Z + a.z_stride * sg.part;
       // the four warps of a lane quarter split its T steps
-      for (int t = warp >> 2; t < g.T; t += 4) {
+      for (int t = warp >> 2; t < T; t += 4) {
         const int c = lane + 32 * t;
         float4 v[4];
 #pragma unroll
@@ -160,12 +165,13 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
       __syncthreads();
 
       // ---- phase 1: row `warp` of W, lanes over the columns, Z_i from TMEM
-      const float* Arow = Tt + size_t(warp) * g.lds + lane;
+      const float* Arow = Tt + size_t(warp) * lds + lane;
       float2 acc[kK / 2];
 #pragma unroll
       for (int j = 0; j < kK / 2; ++j) acc[j] = make_float2(0.f, 0.f);
       int s = 0;
-      for (; s + 1 < g.T; s += 2) {
+#pragma unroll
+      for (; s + 1 < T; s += 2) {
         uint32_t z0[16], z1[16];
         tmem_ld16_async(tq + 16 * s, z0);
         tmem_ld16_async(tq + 16 * (s + 1), z1);
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
         fma_row(acc, a0, z0);
         fma_row(acc, a1, z1);
       }
-      if (s < g.T) {
+      if (s < T) {
         uint32_t z0[16];
         tmem_ld16_async(tq + 16 * s, z0);
         const float a0 = Arow[32 * s];
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
       __syncthreads();
 
       // ---- phase 2: Y += T^T W (packed FP32 FMAs)
-#pragma unroll 2
+#pragma unroll(FULL ? 4 : 2)
       for (int r = 0; r < kR; ++r) {
         float2 w[kK / 2];
 #pragma unroll
@@ -216,8 +222,8 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
           const int c = tid + kThr * q;
-          if (c < d) {
-            const float av = Tt[size_t(r) * g.lds + c];
+          if (FULL || c < d) {
+            const float av = Tt[size_t(r) * lds + c];
             const float2 a2 = make_float2(av, av);
 #pragma unroll
             for (int j = 0; j < kK / 2; ++j) y[q][j] = __ffma2_rn(a2, w[j], y[q][j]);
@@ -230,7 +236,7 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
       const int c = tid + kThr * q;
-      if (c < d) {
+      if (FULL || c < d) {
 #pragma unroll
         for (int j = 0; j < kK / 2; j += 2)
           *reinterpret_cast<float4*>(Pd + size_t(c) * pld + 2 * j) =
@@ -271,7 +277,9 @@ cudaError_t launch_step_simt_tmem(const StepArgs& a, cudaStream_t s) {
   GeoT g;
   size_t bytes;
   if (!geo_tmem(a.d, a.ld, &g, &bytes)) return cudaErrorInvalidConfiguration;
-  auto kern = a.d > kThr ? step_simt_tmem_kernel<2> : step_simt_tmem_kernel<1>;
+  auto kern = a.d == 1024 && a.ld == 1024 ? step_simt_tmem_kernel<2, true>
+             : a.d > kThr                 ? step_simt_tmem_kernel<2, false>
+                                          : step_simt_tmem_kernel<1, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
   if (e != cudaSuccess) return e;
   kern<<<a.grid, kThr, bytes, s>>>(a, g);
