@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
       __syncthreads();
 
       // ---- phase 2: Y += T^T W (packed FP32 FMAs)
-#pragma unroll(FULL ? 4 : 2)
+#pragma unroll(FULL ? 8 : 2)
       for (int r = 0; r < kR; ++r) {
         float2 w[kK / 2];
 #pragma unroll
