@@ -19,6 +19,9 @@
 //            sums the 32 lanes, so no cross-warp reduction is needed;
 //   phase 2  Y += A_tile^T W with each thread's columns c = tid + 512 q of the
 //            d x 16 partial Y in registers for the CTA's whole segment.
+// For d = 1024 (the row length of the FP32 benchmark) a second kernel with
+// compile-time geometry software-pipelines the tiles: phase 2 of tile t runs
+// interleaved with phase 1 of tile t + 1 in every warp.
 // Only one CTA fits an SM (512 threads x 128 registers), so the TMEM
 // allocation never waits on another CTA.
 #include "lp_internal.cuh"
@@ -77,16 +80,38 @@ __device__ __forceinline__ void fma_row(float2 (&acc)[kK / 2], float a, const ui
     acc[j] = __ffma2_rn(a2, make_float2(__uint_as_float(z[2 * j]), __uint_as_float(z[2 * j + 1])), acc[j]);
 }
 
-// FULL: d = ld = 1024 exactly, so the lane steps, tile stride and copy plan are
-// compile-time constants (loops unroll, addresses become immediate offsets).
-template <int CPT, bool FULL>
+// Sum a row's per-lane partials over the 32 lanes into Wrow[0..15]: a
+// reduce-scatter whose halving steps leave lane l with the sum of column l >> 1,
+// then the pair (l, l ^ 1) adds its halves.
+__device__ __forceinline__ void store_row_sum(const float2 (&acc)[kK / 2], int lane, float* Wrow) {
+  float v[kK];
+#pragma unroll
+  for (int j = 0; j < kK / 2; ++j) {
+    v[2 * j] = acc[j].x;
+    v[2 * j + 1] = acc[j].y;
+  }
+#pragma unroll
+  for (int h = kK / 2, mask = 16; h >= 1; h >>= 1, mask >>= 1) {
+    const bool up = (lane & mask) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const float send = up ? v[k] : v[k + h];
+      const float keep = up ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+    }
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  if ((lane & 1) == 0) Wrow[lane >> 1] = v[0];
+}
+
+template <int CPT>
 __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, GeoT g) {
   extern __shared__ __align__(16) float smt[];
   __shared__ uint32_t tmem_holder;
-  const int T = FULL ? 32 : g.T;
-  const int lds = FULL ? 1024 : g.lds;
-  const int d = FULL ? 1024 : a.d;
-  const int64_t ld = FULL ? 1024 : a.ld;
+  const int T = g.T;
+  const int lds = g.lds;
+  const int d = a.d;
+  const int64_t ld = a.ld;
   float* buf0 = smt;
   float* buf1 = buf0 + kR * lds;
   float* Ws = buf1 + kR * lds;  // R x K
@@ -187,30 +212,11 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
         tmem_wait_ld();
         fma_row(acc, a0, z0);
       }
-      // reduce-scatter over the 32 lanes: after the halving steps lane l holds
-      // the sum of column l >> 1, then the pair (l, l ^ 1) adds its halves
-      float v[kK];
-#pragma unroll
-      for (int j = 0; j < kK / 2; ++j) {
-        v[2 * j] = acc[j].x;
-        v[2 * j + 1] = acc[j].y;
-      }
-#pragma unroll
-      for (int h = kK / 2, mask = 16; h >= 1; h >>= 1, mask >>= 1) {
-        const bool up = (lane & mask) != 0;
-#pragma unroll
-        for (int k = 0; k < h; ++k) {
-          const float send = up ? v[k] : v[k + h];
-          const float keep = up ? v[k + h] : v[k];
-          v[k] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
-        }
-      }
-      v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-      if ((lane & 1) == 0) Ws[warp * kK + (lane >> 1)] = v[0];
+      store_row_sum(acc, lane, Ws + warp * kK);
       __syncthreads();
 
       // ---- phase 2: Y += T^T W (packed FP32 FMAs)
-#pragma unroll(FULL ? 8 : 2)
+#pragma unroll 2
       for (int r = 0; r < kR; ++r) {
         float2 w[kK / 2];
 #pragma unroll
@@ -222,7 +228,7 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
 #pragma unroll
         for (int q = 0; q < CPT; ++q) {
           const int c = tid + kThr * q;
-          if (FULL || c < d) {
+          if (c < d) {
             const float av = Tt[size_t(r) * lds + c];
             const float2 a2 = make_float2(av, av);
 #pragma unroll
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
       const int c = tid + kThr * q;
-      if (FULL || c < d) {
+      if (c < d) {
 #pragma unroll
         for (int j = 0; j < kK / 2; j += 2)
           *reinterpret_cast<float4*>(Pd + size_t(c) * pld + 2 * j) =
@@ -249,6 +255,171 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
   tc_sync();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.cols) : "memory");
+}
+
+// d = ld = 1024, software-pipelined across tiles: each warp interleaves phase 2
+// of tile t (row r of the tile against W(t)) with phase 1 of tile t + 1 (two
+// lane steps of its own row), so the FMAs of one hide the TMEM and shared-memory
+// latencies of the other and no phase leaves the FP32 pipe idle behind a
+// barrier.  Three tile buffers (t, t + 1 in use, t + 2 loading) and two W
+// buffers; one barrier per tile.  Same arithmetic as the kernel above.
+constexpr int kD = 1024, kT32 = 32, kTile = kR * kD;
+
+template <bool NEXT>
+__device__ __forceinline__ void fused_rows(const float* __restrict__ Acur, const float* __restrict__ Wcur,
+                                           const float* Anext_row, uint32_t tq, int tid, float2 (&y)[2][kK / 2],
+                                           float2 (&acc)[kK / 2]) {
+#pragma unroll 4
+  for (int r = 0; r < kR; ++r) {
+    uint32_t z0[16], z1[16];
+    float a0 = 0.f, a1 = 0.f;
+    if (NEXT) {
+      tmem_ld16_async(tq + 32 * r, z0);
+      tmem_ld16_async(tq + 32 * r + 16, z1);
+      a0 = Anext_row[64 * r];
+      a1 = Anext_row[64 * r + 32];
+    }
+    float2 w[kK / 2];
+#pragma unroll
+    for (int j = 0; j < kK; j += 4) {
+      const float4 q4 = *reinterpret_cast<const float4*>(Wcur + r * kK + j);
+      w[j / 2] = make_float2(q4.x, q4.y);
+      w[j / 2 + 1] = make_float2(q4.z, q4.w);
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float av = Acur[r * kD + tid + kThr * q];
+      const float2 a2 = make_float2(av, av);
+#pragma unroll
+      for (int j = 0; j < kK / 2; ++j) y[q][j] = __ffma2_rn(a2, w[j], y[q][j]);
+    }
+    if (NEXT) {
+      tmem_wait_ld();
+      fma_row(acc, a0, z0);
+      fma_row(acc, a1, z1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs a) {
+  extern __shared__ __align__(16) float smt[];
+  __shared__ uint32_t tmem_holder;
+  float* bufs = smt;                  // 3 tiles of R x 1024
+  float* Wb = smt + 3 * kTile;        // 2 x (R x K)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int zld = a.zld > 0 ? a.zld : kK, pld = a.pld > 0 ? a.pld : kK;
+  const float* A = static_cast<const float*>(a.A);
+  // tile copy plan: 256 16-byte chunks per row, two rows per pass
+  const int cp_r0 = tid >> 8, cp_ch = tid & 255;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_holder)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_sync();
+  const uint32_t tmem = tmem_holder;
+  const uint32_t tq = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+
+  float2 y[2][kK / 2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int j = 0; j < kK / 2; ++j) y[q][j] = make_float2(0.f, 0.f);
+
+  int cur_part = -1;
+  const int sb = a.seg_ptr[blockIdx.x], se = a.seg_ptr[blockIdx.x + 1];
+  for (int si = sb; si < se; ++si) {
+    const Segment sg = a.segs[si];
+    const int ntiles = static_cast<int>((sg.row1 - sg.row0 + kR - 1) / kR);
+    auto issue = [&](int t) {
+      float* buf = bufs + (t % 3) * kTile;
+      const int64_t r0 = sg.row0 + int64_t(t) * kR;
+#pragma unroll
+      for (int r = cp_r0; r < kR; r += 2) {
+        const int64_t grow = r0 + r;
+        const bool ok = grow < sg.row1;
+        cp_async16(buf + r * kD + cp_ch * 4, A + (ok ? grow : sg.row0) * kD + cp_ch * 4, ok ? 16 : 0);
+      }
+      cp_async_commit();
+    };
+    // every buffer is free here: the previous segment ended with a barrier
+    issue(0);
+    if (ntiles > 1) issue(1);
+    if (sg.part != cur_part) {
+      tc_sync();
+      cur_part = sg.part;
+      const float* Zg = a.Z + a.z_stride * sg.part;
+      for (int t = warp >> 2; t < kT32; t += 4) {
+        const int c = lane + 32 * t;
+        float4 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = *reinterpret_cast<const float4*>(Zg + size_t(c) * zld + 4 * j);
+        tmem_st16(tq + 16 * t, v);
+      }
+      tmem_wait_st();
+      tc_sync();
+    }
+    // prologue: phase 1 of tile 0 alone
+    if (ntiles > 1) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncthreads();
+    {
+      const float* Arow = bufs + warp * kD + lane;
+      float2 acc[kK / 2];
+#pragma unroll
+      for (int j = 0; j < kK / 2; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int s = 0; s < kT32; s += 2) {
+        uint32_t z0[16], z1[16];
+        tmem_ld16_async(tq + 16 * s, z0);
+        tmem_ld16_async(tq + 16 * (s + 1), z1);
+        const float a0 = Arow[32 * s], a1 = Arow[32 * (s + 1)];
+        tmem_wait_ld();
+        fma_row(acc, a0, z0);
+        fma_row(acc, a1, z1);
+      }
+      store_row_sum(acc, lane, Wb + warp * kK);
+    }
+    __syncthreads();
+    for (int t = 0; t < ntiles; ++t) {
+      const bool next = t + 1 < ntiles;
+      // tile t + 2 goes into the buffer tile t - 1 used (freed by the last barrier)
+      if (t + 2 < ntiles) {
+        issue(t + 2);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();  // tile t + 1 has landed for every thread
+      const float* Acur = bufs + (t % 3) * kTile;
+      const float* Wcur = Wb + (t & 1) * kR * kK;
+      float2 acc[kK / 2];
+#pragma unroll
+      for (int j = 0; j < kK / 2; ++j) acc[j] = make_float2(0.f, 0.f);
+      if (next) {
+        fused_rows<true>(Acur, Wcur, bufs + ((t + 1) % 3) * kTile + warp * kD + lane, tq, tid, y, acc);
+        store_row_sum(acc, lane, Wb + ((t + 1) & 1) * kR * kK + warp * kK);
+      } else {
+        fused_rows<false>(Acur, Wcur, nullptr, tq, tid, y, acc);
+      }
+      __syncthreads();  // W(t + 1) complete; tile t's buffer and W(t) free
+    }
+    float* Pd = a.P + size_t(sg.slot) * kD * pld;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int c = tid + kThr * q;
+#pragma unroll
+      for (int j = 0; j < kK / 2; j += 2)
+        *reinterpret_cast<float4*>(Pd + size_t(c) * pld + 2 * j) =
+            make_float4(y[q][j].x, y[q][j].y, y[q][j + 1].x, y[q][j + 1].y);
+#pragma unroll
+      for (int j = 0; j < kK / 2; ++j) y[q][j] = make_float2(0.f, 0.f);
+    }
+  }
+  tc_sync();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 constexpr size_t kSmemLimitT = 227 * 1024;
@@ -277,9 +448,15 @@ cudaError_t launch_step_simt_tmem(const StepArgs& a, cudaStream_t s) {
   GeoT g;
   size_t bytes;
   if (!geo_tmem(a.d, a.ld, &g, &bytes)) return cudaErrorInvalidConfiguration;
-  auto kern = a.d == 1024 && a.ld == 1024 ? step_simt_tmem_kernel<2, true>
-             : a.d > kThr                 ? step_simt_tmem_kernel<2, false>
-                                          : step_simt_tmem_kernel<1, false>;
+  if (a.d == kD && a.ld == kD) {
+    const size_t b3 = size_t(4) * (3 * kTile + 2 * kR * kK);
+    cudaError_t e = cudaFuncSetAttribute(step_simt_tmem_d1024_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(b3));
+    if (e != cudaSuccess) return e;
+    step_simt_tmem_d1024_kernel<<<a.grid, kThr, b3, s>>>(a);
+    return cudaGetLastError();
+  }
+  auto kern = a.d > kThr ? step_simt_tmem_kernel<2> : step_simt_tmem_kernel<1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
   if (e != cudaSuccess) return e;
   kern<<<a.grid, kThr, bytes, s>>>(a, g);
