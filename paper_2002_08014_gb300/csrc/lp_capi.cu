@@ -340,6 +340,7 @@ lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool t
   a.z_stride = z_stride;
   a.P = c->dP;
   a.grid = c->grid;
+  a.status = c->dStatus;
   if (timing) {
     const size_t need = size_t(c->step_ev_used) + 2;
     while (c->step_ev.size() < need) {

@@ -39,6 +39,7 @@ struct StepArgs {
   int grid;               // CTAs
   int zld = 0, pld = 0;   // row strides of Z and P in floats (0: K); a launch on a column
                           // range of wider blocks passes the wider stride and offset pointers
+  int* status = nullptr;  // device status word for ST_TIMEOUT (bounded waits), or nullptr
 };
 
 // Returns cudaErrorInvalidConfiguration when no SIMT instantiation fits.

@@ -262,8 +262,20 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_kernel(StepArgs a, Geo
 // lane steps of its own row), so the FMAs of one hide the TMEM and shared-memory
 // latencies of the other and no phase leaves the FP32 pipe idle behind a
 // barrier.  Three tile buffers (t, t + 1 in use, t + 2 loading) and two W
-// buffers; one barrier per tile.  Same arithmetic as the kernel above.
+// buffers; one barrier per tile.  A tile's 16 rows are 64 KB contiguous in both
+// global and shared memory, so one thread loads it with a single bulk copy
+// completing on the buffer's mbarrier (rows past the segment are zeroed by
+// plain stores); the waits on it are bounded.  Same arithmetic as the kernel
+// above.
 constexpr int kD = 1024, kT32 = 32, kTile = kR * kD;
+
+// Bulk copy global -> this CTA's shared memory, completion counted in bytes on
+// an mbarrier; addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
 
 template <bool NEXT>
 __device__ __forceinline__ void fused_rows(const float* __restrict__ Acur, const float* __restrict__ Wcur,
@@ -304,14 +316,17 @@ __device__ __forceinline__ void fused_rows(const float* __restrict__ Acur, const
 __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs a) {
   extern __shared__ __align__(16) float smt[];
   __shared__ uint32_t tmem_holder;
+  __shared__ __align__(8) uint64_t full[3];
   float* bufs = smt;                  // 3 tiles of R x 1024
   float* Wb = smt + 3 * kTile;        // 2 x (R x K)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int zld = a.zld > 0 ? a.zld : kK, pld = a.pld > 0 ? a.pld : kK;
   const float* A = static_cast<const float*>(a.A);
-  // tile copy plan: 256 16-byte chunks per row, two rows per pass
-  const int cp_r0 = tid >> 8, cp_ch = tid & 255;
 
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b) tc::mbar_init(&full[b], 1);
+    tc::fence_mbar_init();
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_holder)),
                  "r"(512)
@@ -328,21 +343,41 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs 
 #pragma unroll
     for (int j = 0; j < kK / 2; ++j) y[q][j] = make_float2(0.f, 0.f);
 
+  uint32_t g0 = 0;  // tiles of earlier segments: tile t of this one is the CTA's tile g0 + t
   int cur_part = -1;
   const int sb = a.seg_ptr[blockIdx.x], se = a.seg_ptr[blockIdx.x + 1];
   for (int si = sb; si < se; ++si) {
     const Segment sg = a.segs[si];
     const int ntiles = static_cast<int>((sg.row1 - sg.row0 + kR - 1) / kR);
+    // tile t -> buffer t % 3 (called by every thread: thread 0 issues the copy,
+    // all zero the rows past the segment)
     auto issue = [&](int t) {
-      float* buf = bufs + (t % 3) * kTile;
+      const int b = (g0 + t) % 3;
+      float* buf = bufs + b * kTile;
       const int64_t r0 = sg.row0 + int64_t(t) * kR;
-#pragma unroll
-      for (int r = cp_r0; r < kR; r += 2) {
-        const int64_t grow = r0 + r;
-        const bool ok = grow < sg.row1;
-        cp_async16(buf + r * kD + cp_ch * 4, A + (ok ? grow : sg.row0) * kD + cp_ch * 4, ok ? 16 : 0);
+      const int valid = static_cast<int>(sg.row1 - r0 < kR ? sg.row1 - r0 : kR);
+      if (tid == 0) {
+        tc::mbar_expect_tx(&full[b], static_cast<uint32_t>(valid) * kD * 4);
+        bulk_g2s(su32(buf), A + r0 * kD, static_cast<uint32_t>(valid) * kD * 4, su32(&full[b]));
       }
-      cp_async_commit();
+      if (valid < kR) {
+        for (int e = valid * kD + tid * 4; e < kTile; e += kThr * 4)
+          *reinterpret_cast<float4*>(buf + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+        tc::fence_async_smem();  // before a later bulk copy rewrites these rows
+      }
+    };
+    // wait for tile t (its buffer's latest fill); bounded
+    auto landed = [&](int t) {
+      const uint32_t g = g0 + t;
+      const uint32_t addr = su32(&full[g % 3]);
+      const uint32_t parity = (g / 3) & 1;
+      const long long t0 = clock64();
+      while (!tc::mbar_try(addr, parity)) {
+        if (clock64() - t0 > tc::kTimeoutCycles) {
+          if (a.status && lane == 0) atomicOr(a.status, ST_TIMEOUT);
+          break;
+        }
+      }
     };
     // every buffer is free here: the previous segment ended with a barrier
     issue(0);
@@ -362,11 +397,10 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs 
       tc_sync();
     }
     // prologue: phase 1 of tile 0 alone
-    if (ntiles > 1) cp_async_wait<1>();
-    else cp_async_wait<0>();
+    landed(0);
     __syncthreads();
     {
-      const float* Arow = bufs + warp * kD + lane;
+      const float* Arow = bufs + (g0 % 3) * kTile + warp * kD + lane;
       float2 acc[kK / 2];
 #pragma unroll
       for (int j = 0; j < kK / 2; ++j) acc[j] = make_float2(0.f, 0.f);
@@ -386,26 +420,23 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs 
     for (int t = 0; t < ntiles; ++t) {
       const bool next = t + 1 < ntiles;
       // tile t + 2 goes into the buffer tile t - 1 used (freed by the last barrier)
-      if (t + 2 < ntiles) {
-        issue(t + 2);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      __syncthreads();  // tile t + 1 has landed for every thread
-      const float* Acur = bufs + (t % 3) * kTile;
+      if (t + 2 < ntiles) issue(t + 2);
+      if (next) landed(t + 1);
+      __syncthreads();  // tile t + 1 (and any zeroed rows) visible to every thread
+      const float* Acur = bufs + ((g0 + t) % 3) * kTile;
       const float* Wcur = Wb + (t & 1) * kR * kK;
       float2 acc[kK / 2];
 #pragma unroll
       for (int j = 0; j < kK / 2; ++j) acc[j] = make_float2(0.f, 0.f);
       if (next) {
-        fused_rows<true>(Acur, Wcur, bufs + ((t + 1) % 3) * kTile + warp * kD + lane, tq, tid, y, acc);
+        fused_rows<true>(Acur, Wcur, bufs + ((g0 + t + 1) % 3) * kTile + warp * kD + lane, tq, tid, y, acc);
         store_row_sum(acc, lane, Wb + ((t + 1) & 1) * kR * kK + warp * kK);
       } else {
         fused_rows<false>(Acur, Wcur, nullptr, tq, tid, y, acc);
       }
       __syncthreads();  // W(t + 1) complete; tile t's buffer and W(t) free
     }
+    g0 += ntiles;
     float* Pd = a.P + size_t(sg.slot) * kD * pld;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
