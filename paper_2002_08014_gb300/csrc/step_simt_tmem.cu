@@ -281,7 +281,7 @@ template <bool NEXT>
 __device__ __forceinline__ void fused_rows(const float* __restrict__ Acur, const float* __restrict__ Wcur,
                                            const float* Anext_row, uint32_t tq, int tid, float2 (&y)[2][kK / 2],
                                            float2 (&acc)[kK / 2]) {
-#pragma unroll 4
+#pragma unroll 2
   for (int r = 0; r < kR; ++r) {
     uint32_t z0[16], z1[16];
     float a0 = 0.f, a1 = 0.f;
