@@ -202,6 +202,9 @@ def _kernel(path, dtype="f32", d=1024, k=16):
         return KERNELS[path]
     if dtype != "f32":
         return "step_simt_kernel (SIMT, rows widened to FP32 in shared memory)"
+    if 8 < k <= 16 and d == 1024:
+        return ("step_simt_tmem_d1024_kernel (SIMT FP32 fused A_i^T (A_i Z_i), Z_i resident in TMEM, "
+                "tiles software-pipelined)")
     if 8 < k <= 16 and d <= 1024:
         return "step_simt_tmem_kernel (SIMT FP32 fused A_i^T (A_i Z_i), Z_i resident in TMEM)"
     return KERNELS[0]
