@@ -157,6 +157,17 @@ void dfree(lp_ctx* c, T*& p, size_t bytes) {
 
 enum Path { PATH_SIMT = 0, PATH_TC = 1, PATH_TCS = 2 };
 
+// Tensor-core step kernels accumulate a segment's A^T W in TMEM, and the tensor
+// cores round that FP32 accumulator toward zero on every MMA, so a long chain
+// shrinks the result a little (about half an ulp per MMA).  Their segments are
+// cut into pieces of at most this many rows (32 tiles, 256 accumulating MMAs
+// per entry); the reduction adds the pieces with round-to-nearest.
+constexpr int64_t kTcChainRows = 4096;
+
+// Most segments any step kernel's table can have for `workers` workers: each
+// worker's row range is cut at partition ends and into kTcChainRows pieces.
+int64_t max_segments(int64_t workers, int64_t m, int64_t n) { return workers + m + n / kTcChainRows + 1; }
+
 // Launches of the SIMT step per local step (0: no SIMT kernel for the shape).
 int simt_launches(int d, int64_t ld, lp_dtype dtype, int K) {
   return lp::step_simt_smem(d, ld, dtype, K, nullptr) != 0 ? 1 : 0;
@@ -181,8 +192,7 @@ struct StateSizes {
 };
 StateSizes state_sizes(const lp_ctx* c, int K) {
   StateSizes s;
-  // every step kernel's segment table has at most (workers <= SMs) + m - 1 segments
-  s.P = size_t(c->sms + c->m) * c->d * K * 4;
+  s.P = size_t(max_segments(c->sms, c->m, c->n)) * c->d * K * 4;
   s.Yl = size_t(c->m) * c->d * K * 4;
   s.Y = size_t(c->d) * K * 4;
   s.G = size_t(c->m) * K * K * 4;
@@ -239,10 +249,10 @@ void free_partitions(lp_ctx* c) {
   dfree(c, c->dSlotBegin, (size_t(c->m) + 1) * 4);
   dfree(c, c->dInvS, size_t(c->m) * 4);
   dfree(c, c->dW, size_t(c->m) * 4);
-  dfree(c, c->dSegsTc, (size_t(c->tc.nclusters) + c->m) * sizeof(Segment));
+  dfree(c, c->dSegsTc, size_t(max_segments(c->tc.nclusters, c->m, c->n)) * sizeof(Segment));
   dfree(c, c->dSegPtrTc, (size_t(c->tc.nclusters) + 1) * 4);
   dfree(c, c->dSlotBeginTc, (size_t(c->m) + 1) * 4);
-  dfree(c, c->dSegsTcs, (size_t(c->sms) + c->m) * sizeof(Segment));
+  dfree(c, c->dSegsTcs, size_t(max_segments(c->sms, c->m, c->n)) * sizeof(Segment));
   dfree(c, c->dSegPtrTcs, (size_t(c->sms) + 1) * 4);
   dfree(c, c->dSlotBeginTcs, (size_t(c->m) + 1) * 4);
   free_state(c);
@@ -272,10 +282,11 @@ lp_status stage_in(lp_ctx* c, const double* src, size_t count, lp_ptr_space spac
 }
 
 // Contiguous row ranges for G workers (CTAs or clusters): worker g owns rows
-// [g n / G, (g+1) n / G), cut at partition ends; one output slot per piece.
-// Partition i's slots are the contiguous range [slot_begin[i], slot_begin[i+1]).
+// [g n / G, (g+1) n / G), cut at partition ends and, when max_rows > 0, into
+// pieces of at most max_rows rows; one output slot per piece.  Partition i's
+// slots are the contiguous range [slot_begin[i], slot_begin[i+1]).
 void build_segments(const lp_ctx* c, int G, std::vector<Segment>& segs, std::vector<int>& seg_ptr,
-                    std::vector<int>& slot_begin) {
+                    std::vector<int>& slot_begin, int64_t max_rows = 0) {
   const int64_t n = c->n;
   const int m = c->m;
   segs.clear();
@@ -288,7 +299,8 @@ void build_segments(const lp_ctx* c, int G, std::vector<Segment>& segs, std::vec
     while (r0 < r1) {
       while (c->row_off[part] + c->rows[part] <= r0) ++part;
       const int64_t pend = c->row_off[part] + c->rows[part];
-      const int64_t e = std::min(r1, pend);
+      int64_t e = std::min(r1, pend);
+      if (max_rows > 0) e = std::min(e, r0 + max_rows);
       Segment s;
       s.row0 = r0;
       s.row1 = e;
@@ -505,7 +517,7 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
   if (dtype == LP_BF16 && lp::tc_plan(static_cast<int>(d), LP_MAX_K, c->sms, &c->tc)) {
     const int G = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->tc.nclusters, (n + 127) / 128)));
     c->tc.nclusters = G;
-    build_segments(c, G, segs_tc, seg_ptr_tc, slot_begin_tc);
+    build_segments(c, G, segs_tc, seg_ptr_tc, slot_begin_tc, kTcChainRows);
     c->nslots_tc = static_cast<int>(segs_tc.size());
     c->max_slots[PATH_TC] = max_slots_in(slot_begin_tc);
     c->tc_ready = true;
@@ -524,7 +536,7 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
       (st = dalloc(c, &c->dSegPtr, (size_t(c->grid) + 1) * 4)) ||
       (st = dalloc(c, &c->dSlotBegin, (size_t(m) + 1) * 4)) || (st = dalloc(c, &c->dInvS, size_t(m) * 4)) ||
       (st = dalloc(c, &c->dW, size_t(m) * 4)) ||
-      (c->tc_ready && ((st = dalloc(c, &c->dSegsTc, (size_t(c->tc.nclusters) + m) * sizeof(Segment))) ||
+      (c->tc_ready && ((st = dalloc(c, &c->dSegsTc, size_t(max_segments(c->tc.nclusters, m, n)) * sizeof(Segment))) ||
                        (st = dalloc(c, &c->dSegPtrTc, (size_t(c->tc.nclusters) + 1) * 4)) ||
                        (st = dalloc(c, &c->dSlotBeginTc, (size_t(m) + 1) * 4))))) {
     std::string msg = c->err;
@@ -618,10 +630,10 @@ size_t lp::estimate_bytes(int sms, int m, const int64_t* rows, int64_t d, int64_
   size_t tot = r256(size_t(n) * ld * eb * planes);
   if (dtype == LP_FP8_E4M3) tot += r256(size_t(n) * 4);
   // segment tables of the three step kernels, weights
-  tot += 3 * (r256((size_t(sms) + M) * sizeof(Segment)) + r256((size_t(sms) + 1) * 4) + r256((M + 1) * 4)) +
-         2 * r256(M * 4);
+  const size_t segs_max = size_t(max_segments(sms, m, n));
+  tot += 3 * (r256(segs_max * sizeof(Segment)) + r256((size_t(sms) + 1) * 4) + r256((M + 1) * 4)) + 2 * r256(M * 4);
   // solve state
-  tot += r256((size_t(sms) + M) * D * K * 4) + 2 * r256(M * D * K * 4) + 3 * r256(D * K * 4) + r256(M * K * K * 4) +
+  tot += r256(segs_max * D * K * 4) + 2 * r256(M * D * K * 4) + 3 * r256(D * K * 4) + r256(M * K * K * 4) +
          r256(D * LP_MAX_K * 8) + r256(LP_MAX_K * 8) + r256(M * D * K * 8) + r256(16);
   if (dtype == LP_F32_BF16X2 && space == LP_HOST) {
     const int64_t chunk_rows = std::max<int64_t>(1, (int64_t(1) << 24) / d);
@@ -682,10 +694,10 @@ static lp_status ensure_tcs(lp_ctx* c, int k) {
   if (G != c->tcs_G) {
     std::vector<Segment> segs;
     std::vector<int> seg_ptr, slot_begin;
-    build_segments(c, G, segs, seg_ptr, slot_begin);
+    build_segments(c, G, segs, seg_ptr, slot_begin, kTcChainRows);
     lp_status st;
     if (!c->dSegsTcs &&
-        ((st = dalloc(c, &c->dSegsTcs, (size_t(c->sms) + c->m) * sizeof(Segment))) ||
+        ((st = dalloc(c, &c->dSegsTcs, size_t(max_segments(c->sms, c->m, c->n)) * sizeof(Segment))) ||
          (st = dalloc(c, &c->dSegPtrTcs, (size_t(c->sms) + 1) * 4)) ||
          (st = dalloc(c, &c->dSlotBeginTcs, (size_t(c->m) + 1) * 4))))
       return st;

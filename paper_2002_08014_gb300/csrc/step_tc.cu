@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_tc_kernel(const __grid_const
 
     // ---- stage Z slice as [Z_hi | Z_lo]^T (N rows x DC, K-major, SWIZZLE_128B)
     __syncthreads();
-    {
+    if (si == sb || sg.part != a.segs[si - 1].part) {  // consecutive pieces of a partition share Z_i
       const float* Zg = a.Z + a.z_stride * sg.part;
       for (int e = tid; e < DC * K; e += kThreads) {
         const int c = e / K, j = e % K;

@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     // ---- stage this slice of Z as [Z_hi | Z_lo]^T (N rows x DC, K-major, SWIZZLE_128B)
     __syncthreads();
-    {
+    if (si == sb || sg.part != a.segs[si - 1].part) {  // consecutive pieces of a partition share Z_i
       const float* Zg = a.Z + a.z_stride * sg.part;
       for (int e = tid; e < DC * K; e += kThreads) {
         const int c = e / K, j = e % K;

@@ -364,6 +364,34 @@ def test_full_size_fp32_step_sampled(gpu_lib):
     assert np.isfinite(MZ).all()
 
 
+def test_full_size_bf16_step_sampled(gpu_lib):
+    """The precision workload at full size (n=4e6, d=2048, k=32, m=128, BF16,
+    16.4 GB on the device), in the benchmark's launch configuration (the
+    autotuner's choice): one power step, checked on sampled partitions against
+    the oracle on the decoded BF16 values."""
+    A, sizes, Y0 = synth.make_config_data("lowprec", threads=16)
+    bits = [synth.f32_to_bf16_bits(p) for p in synth.split_rows(A, sizes)]
+    del A
+    Z = O.orth(Y0)
+    with B.LocalPower(bits, dtype="bf16") as lp:
+        B.lp_autotune(lp.ctx, 32)
+        Y = lp.power_step(32, Z, shared=True)
+    # The tensor cores round the FP32 accumulator toward zero on every MMA, so an
+    # accumulation chain shrinks Y_i by a nearly uniform factor: at most one unit
+    # in the last place (2^-23) per MMA that adds into an entry.  The library cuts
+    # the tensor-core segments into pieces of at most 4,096 rows, so a chain is at
+    # most 32 tiles x 8 MMAs in the second contraction plus d / 16 in the first.
+    # A common scale does not move span(Y_i); Y_i is checked at the step bar both
+    # as it is and after removing the best scale.
+    for i in (0, 77, 127):
+        ref = O.local_step(("bf16", bits[i]), Z)
+        alpha = float(np.vdot(Y[i], ref) / np.vdot(Y[i], Y[i]))
+        chain = (4096 // 128 + 1) * 8 + 2048 // 16
+        assert 0.0 <= alpha - 1.0 <= chain * 2.0 ** -23, (i, alpha)
+        assert _relF(alpha * Y[i], ref) < TC_STEP_TOL, (i, _relF(alpha * Y[i], ref), alpha)
+        assert _relF(Y[i], ref) < TC_STEP_TOL, (i, _relF(Y[i], ref))
+
+
 def test_tuning_changes_speed_not_results(gpu_lib):
     """Ring depth, lag, L2 prefetch and cache hints reorder loads only: the
     streaming kernel's products and their summation order are unchanged."""
