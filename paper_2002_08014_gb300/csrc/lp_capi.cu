@@ -476,7 +476,16 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
   }
   LP_CUDA(cudaSetDevice(c->device));
   LP_CUDA(cudaStreamSynchronize(c->stream));
-  free_partitions(c);
+  // New data of the same shapes (m, rows, d, dtype) go into the existing buffers:
+  // allocations, segment tables, tensor maps, tuning and captured graphs stay.
+  const bool reuse = c->dA && c->m == m && c->d == d && c->dtype == dtype && c->n == n &&
+                     std::equal(rows, rows + m, c->rows.begin());
+  if (!reuse) {
+    free_partitions(c);
+  } else {
+    c->solved = false;  // the last result belongs to the old data
+    c->traced_rounds = 0;
+  }
 
   const bool split = dtype == LP_F32_BF16X2;
   if (split) {
@@ -502,6 +511,8 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
   }
   c->base = static_cast<int>(std::max_element(c->rows.begin(), c->rows.end()) - c->rows.begin());
 
+  lp_status st;
+  if (!reuse) {
   // Row segments of the SIMT step kernel: CTA g owns rows [g n / G, (g+1) n / G), cut at partition ends.
   const int64_t min_rows = 32;
   c->grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->sms, n / min_rows)));
@@ -529,7 +540,6 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
   }
 
   c->dA_bytes = size_t(n) * size_t(c->ld) * eb * nplanes;
-  lp_status st;
   if ((st = dalloc(c, &c->dA, c->dA_bytes)) ||
       (dtype == LP_FP8_E4M3 && (st = dalloc(c, &c->dScales, size_t(n) * 4))) ||
       (st = dalloc(c, &c->dSegs, (size_t(c->grid) + m) * sizeof(Segment))) ||
@@ -555,6 +565,14 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
       LP_CUDA(cudaMemcpyAsync(c->dSlotBeginTc, slot_begin_tc.data(), slot_begin_tc.size() * 4,
                               cudaMemcpyHostToDevice, c->stream));
     }
+  }
+  LP_CUDA(cudaMemcpyAsync(c->dSegs, segs.data(), segs.size() * sizeof(Segment), cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dSegPtr, seg_ptr.data(), seg_ptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dSlotBegin, slot_begin.data(), slot_begin.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dInvS, invs.data(), m * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dW, w.data(), m * 4, cudaMemcpyHostToDevice, c->stream));
+  // the host vectors above are pageable: the copies must finish before they go
+  LP_CUDA(cudaStreamSynchronize(c->stream));
   }
   const cudaMemcpyKind kind = space == LP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   if (split) {
@@ -594,7 +612,7 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     dfree(c, stage, stage_bytes);
     if (e != cudaSuccess) return cuda_fail(c, e, "split-plane load");
-  } else if (c->ld != d) {
+  } else if (c->ld != d && !reuse) {  // padding columns; a reload rewrites only columns [0, d)
     LP_CUDA(cudaMemsetAsync(c->dA, 0, c->dA_bytes, c->stream));
   }
   for (int i = 0; i < m && !split; ++i) {
@@ -604,11 +622,6 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
     if (dtype == LP_FP8_E4M3)
       LP_CUDA(cudaMemcpyAsync(c->dScales + c->row_off[i], row_scales[i], size_t(rows[i]) * 4, kind, c->stream));
   }
-  LP_CUDA(cudaMemcpyAsync(c->dSegs, segs.data(), segs.size() * sizeof(Segment), cudaMemcpyHostToDevice, c->stream));
-  LP_CUDA(cudaMemcpyAsync(c->dSegPtr, seg_ptr.data(), seg_ptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
-  LP_CUDA(cudaMemcpyAsync(c->dSlotBegin, slot_begin.data(), slot_begin.size() * 4, cudaMemcpyHostToDevice, c->stream));
-  LP_CUDA(cudaMemcpyAsync(c->dInvS, invs.data(), m * 4, cudaMemcpyHostToDevice, c->stream));
-  LP_CUDA(cudaMemcpyAsync(c->dW, w.data(), m * 4, cudaMemcpyHostToDevice, c->stream));
   LP_CUDA(cudaStreamSynchronize(c->stream));
   return LP_OK;
 }

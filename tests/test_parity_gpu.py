@@ -392,6 +392,27 @@ def test_full_size_bf16_step_sampled(gpu_lib):
         assert _relF(Y[i], ref) < TC_STEP_TOL, (i, _relF(Y[i], ref))
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f32_bf16x2"])
+def test_reload_same_shape_reuses_the_context(gpu_lib, dtype):
+    """New data of the same shapes go into the existing buffers (tables, plans and
+    the captured graph stay): the result equals a fresh context's on that data,
+    and the old result is gone until the next solve."""
+    sizes, d, k = [700, 500, 900], 96, 6
+    A1, _, _ = _parts(sizes, d, 71, dtype)
+    A2, _, _ = _parts(sizes, d, 72, dtype)
+    Y0 = synth.gaussian_start(d, k, 73)
+    with B.LocalPower(A1, dtype=dtype) as lp:
+        lp.solve(k, [4, 2, 1], "sign", Y0)
+        B.lp_load_partitions(lp.ctx, A2, dtype)
+        with pytest.raises(B.LPError) as e:
+            lp.result(k)
+        assert e.value.status == B.LP_ERR_STATE
+        Z2, _, _ = lp.solve(k, [4, 2, 1], "sign", Y0)
+    with B.LocalPower(A2, dtype=dtype) as fresh:
+        Zf, _, _ = fresh.solve(k, [4, 2, 1], "sign", Y0)
+    assert np.array_equal(Z2, Zf)
+
+
 def test_tuning_changes_speed_not_results(gpu_lib):
     """Ring depth, lag, L2 prefetch and cache hints reorder loads only: the
     streaming kernel's products and their summation order are unchanged."""
