@@ -115,6 +115,10 @@ lp_status lp_create(lp_ctx** out, int device, size_t hbm_budget_bytes, void* cud
  *                  LP_F32_BF16X2 takes FP32 parts (like LP_F32) and splits them on the device.
  *   space          whether parts / row_scales are host or device pointers.
  * Replaces any previously loaded partitions.  The caller keeps its buffers.
+ * New data of the same shapes (m, rows, d, dtype) are copied into the existing
+ * device buffers: segment tables, kernel plans, tuning and captured solve graphs
+ * stay valid, and only the copy costs time.  The previous solve's result is
+ * invalidated either way (lp_result returns LP_ERR_STATE until the next solve).
  */
 lp_status lp_load_partitions(lp_ctx* ctx, int m, const int64_t* rows, int64_t d, lp_dtype dtype,
                              const void* const* parts, const float* const* row_scales, lp_ptr_space space);
