@@ -42,7 +42,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--agg", choices=["sign", "opt"], default="sign")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage (tensor-core) run of the workload")
@@ -786,32 +786,47 @@ def run_ours(args):
     achieved_gbs = f32["launch_bytes"] / (f32["step_ms"] / 1e3) / 1e9
 
     # ---------------- end to end through the public API, host buffers (pinned)
+    # Every step loads its data from pinned host memory (lp_load_partitions), solves
+    # and reads the result back.  Two contexts alternate, so step i+1's host-to-device
+    # copy overlaps step i's solve (a context reloads only after its previous solve).
     e2e_ms = []
     if args.e2e_steps > 0:
         pinned = torch.from_numpy(A).pin_memory()
         host_parts = [t.numpy() for t in torch.split(pinned, sizes)]
-        for it in range(args.e2e_steps + 1):
-            torch.cuda.synchronize(dev)
-            if world > 1:
-                dist.barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            B.lp_load_partitions(lp.ctx, host_parts, "f32")
-            lp.submit(k, sched, args.agg, Y0, ritz=True)
-            lp.result(k)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            if it > 0:   # the first is a warm-up
-                e2e_ms.append(e0.elapsed_time(e1))
+        stream2 = torch.cuda.Stream(device=dev)
+        lp2 = B.LocalPower(host_parts, device=local, stream=stream2)
+        ctxs = [lp, lp2]
+        for c2 in ctxs:   # warm-up: every context has loaded and solved (graphs captured) once
+            B.lp_load_partitions(c2.ctx, host_parts, "f32")
+            c2.submit(k, sched, args.agg, Y0, ritz=True)
+            c2.result(k)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for it in range(args.e2e_steps):
+            c2 = ctxs[it % 2]
+            B.lp_load_partitions(c2.ctx, host_parts, "f32")
+            c2.submit(k, sched, args.agg, Y0, ritz=True)
+            if it >= 1:
+                ctxs[(it - 1) % 2].result(k)
+        ctxs[(args.e2e_steps - 1) % 2].result(k)
+        torch.cuda.synchronize(dev)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(e0.elapsed_time(e1) / args.e2e_steps)
+        lp2.close()
         del pinned, host_parts
     e2e = None
     if e2e_ms:
-        # whole-job rate over the e2e steps (their summed time, slowest rank)
-        e2e_t = max_over_ranks(torch, dist, world, dev, sum(e2e_ms))
-        e2e = {"value": job_throughput(world, len(e2e_ms), f32["bytes_solve"], e2e_t)[0], "unit": "GB/s",
+        # whole-job rate over the e2e steps (slowest rank)
+        e2e_t = max_over_ranks(torch, dist, world, dev, e2e_ms[0] * args.e2e_steps)
+        e2e = {"value": job_throughput(world, args.e2e_steps, f32["bytes_solve"], e2e_t)[0], "unit": "GB/s",
                "h2d_bytes_per_step": int(A.nbytes + Y0.nbytes), "d2h_bytes_per_step": int(d * k * 8 + 8 * k),
-               "ms_per_step": e2e_t / len(e2e_ms), "ms_each": [round(x, 2) for x in e2e_ms]}
+               "ms_per_step": e2e_t / args.e2e_steps, "steps": args.e2e_steps,
+               "pipelining": "two contexts: step i+1's host-to-device copy overlaps step i's solve"}
     lp.close()
 
     line = {"metric": METRIC, "value": f32["gbs"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
