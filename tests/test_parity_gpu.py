@@ -70,6 +70,8 @@ def _relF(a, b):
     ([20], 7, 1),                      # tiny d, k = 1
     ([300, 29], 512, 24),              # k padded to 32, partition of 29 rows
     ([13] * 40 + [600], 200, 12),      # many tiny partitions: CTAs restage Z_i often (k padded to 16)
+    ([12, 15, 16, 17, 33, 500], 1024, 12),  # d = 1024 pipelined kernel: ragged last tiles, short segments
+    ([37] * 30 + [2000], 1024, 16),    # d = 1024: many partitions per CTA, Z_i restaged in TMEM
 ])
 def test_power_step_matches_oracle(gpu_lib, dtype, sizes, d, k):
     stored, exact, scales = _parts(sizes, d, 100 + d + k, dtype)
