@@ -8,7 +8,8 @@
 //   aggregation   D_i (sign / OPT, skipped when p_t = 1) then Y = sum_i p_i Y_i D_i
 //   output        Z_T = orth(Y), optionally Rayleigh-Ritz
 // Device state is FP32 d x K blocks (K = k rounded up to 8, 16 or 32, padding
-// columns zero); the k x k factorisations run in FP64 inside the kernels.
+// columns zero); the k x k factorisations run inside the kernels (FP32 with an
+// FP64 Cholesky fallback for small pivots; FP64 Ritz matrix).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

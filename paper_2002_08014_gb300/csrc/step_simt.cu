@@ -15,6 +15,9 @@
 // the phase-1 reads are bank-conflict free.  BF16 and FP8 tiles are widened to
 // FP32 in shared memory (FP8 rows times their scale) before the two phases;
 // all arithmetic is FP32.
+// This file holds the 256-thread kernel (FP8, forced-SIMT BF16, remaining
+// shapes) and a 512-thread FP32 kernel; FP32 at 8 < k <= 16 and d <= 1024 goes
+// to the kernels with Z_i in tensor memory (step_simt_tmem.cu) instead.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
