@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--requests", type=int, default=2000, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (requests/s)")
     ap.add_argument("--shape", default="1024x16", help="kernels: d x k of the step-kernel comparison")
+    ap.add_argument("--autotune", action="store_true",
+                    help="kernels workload: let the autotuner pick the tensor-core step's tuning first")
     ap.add_argument("--instances", type=int, default=256, help="batching: number of instances")
     ap.add_argument("--workload", choices=["fp32", "lowprec", "plain", "serving", "kernels", "batching", "rounds"],
                     default="fp32",
@@ -179,15 +181,18 @@ def run_reference(args):
 # dram__bytes_write.sum) of each step kernel at n = 262,144, d = 1,024, k = 16; the traffic
 # grows with the rows, so a full launch's traffic is this ratio times its algorithmic bytes.
 # Keys: (path, planes, cache hints).  Configurations without a capture report null.
-DRAM_RATIO = {(0, 0, 0): 1081.1 / 1073.7,   # SIMT FP32, Z_i in TMEM
-              (1, 1, 0): 544.8 / 536.9,     # resident tcgen05, BF16
-              (2, 1, 0): 750.1 / 536.9,     # streaming tcgen05, BF16, no hints
-              (2, 1, 1): 606.8 / 536.9,     # streaming tcgen05, BF16, evict_last / evict_first hints
-              (2, 2, 0): 1753.6 / 1073.7}   # streaming tcgen05, hi/lo planes, no hints
+# DRAM bytes per launch / algorithmic bytes at d = 1024, k = 16, from ncu
+# captures of the current kernels, keyed by (path, planes, cache hints, slice
+# columns, lag); other configurations report traffic as unknown.
+DRAM_RATIO = {(0, 0, 0, 0, 0): 1081.1 / 1073.7,    # SIMT FP32, Z_i in TMEM (n = 262,144)
+              (2, 1, 1, 0, 1): 2094.9 / 2048.0,    # streaming tcgen05, BF16, as autotuned (n = 1,000,000)
+              (2, 2, 1, 512, 1): 4496.9 / 4096.0}  # streaming tcgen05, hi/lo planes, as autotuned (n = 1,000,000)
 
 
-def _traffic(path, planes, hints, launch_bytes, d=1024, k=16):
-    r = DRAM_RATIO.get((path, planes, hints)) if (d, k) == (1024, 16) else None
+def _traffic(path, planes, tuning, launch_bytes, d=1024, k=16):
+    t = tuning or {}
+    key = (path, planes, t.get("cache_hints", 0), t.get("slice_cols", 0), t.get("lag_units", 0))
+    r = DRAM_RATIO.get(key) if (d, k) == (1024, 16) else None
     return None if r is None else r * launch_bytes
 
 
@@ -669,6 +674,7 @@ def run_kernels(args):
         eb = 2 if dtype == "bf16" else 4
         try:
             with B.LocalPower(data if data is not None else bits, dtype=dtype) as lp:
+                tuned = B.lp_autotune(lp.ctx, k) if args.autotune and dtype != "f32" and not flags else None
                 ms = []
                 for _ in range(max(args.steps, 2)):
                     B.lp_solve(lp.ctx, k, [1], "sign", Y0, 0, B.LP_FLAG_TIMING | B.LP_FLAG_NO_GRAPH | flags)
@@ -676,7 +682,8 @@ def run_kernels(args):
                     ms.append(st["ms_step_kernels"])
             best = min(ms[1:])
             out[f"{dtype}{'_resident' if flags else ''}"] = {
-                "kernel": _kernel(st["path"], dtype if dtype == "f32" else "bf16", d, k), "launch_ms": best, "gbs": n * d * eb / (best / 1e3) / 1e9}
+                "kernel": _kernel(st["path"], dtype if dtype == "f32" else "bf16", d, k), "tuning": tuned,
+                "launch_ms": best, "gbs": n * d * eb / (best / 1e3) / 1e9}
         except Exception as e:
             out[f"{dtype}{'_resident' if flags else ''}"] = {"error": str(e)[:200]}
     print(json.dumps({"workload": "kernels", "n": n, "d": d, "k": k, "m": m, "results": out}))
@@ -836,7 +843,7 @@ def run_ours(args):
             "gpu_launches": f32["launches"], "e2e": e2e,
             "roofline": {"kernel": _kernel(f32["path"], "f32", c["d"], c["k"]), "bound": "alu",
                          "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved_tf / alu_peak,
-                         "traffic": _traffic(0, 0, 0, f32["launch_bytes"]), "traffic_unit": "bytes per launch",
+                         "traffic": _traffic(0, 0, None, f32["launch_bytes"]), "traffic_unit": "bytes per launch",
                          "launch_ms": f32["step_ms"],
                          "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop x {sm_max_mhz:.0f} MHz"},
             "roofline_hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -865,7 +872,7 @@ def run_ours(args):
             "speedup_solves_vs_fp32": b16["solves_per_s"] / f32["solves_per_s"],
             "roofline": {"bound": "hbm", "achieved": gbs_b, "peak": hbm_peak, "unit": "GB/s",
                          "frac": gbs_b / hbm_peak,
-                         "traffic": _traffic(b16["path"], 1, choice["cache_hints"], b16["launch_bytes"]),
+                         "traffic": _traffic(b16["path"], 1, choice, b16["launch_bytes"]),
                          "traffic_unit": "bytes per launch", "launch_ms": b16["step_ms"],
                          "peak_source": f"{peak_src} HBM copy bandwidth"}}
 
@@ -889,7 +896,7 @@ def run_ours(args):
             "clocks": clks, "speedup_solves_vs_fp32": sp["solves_per_s"] / f32["solves_per_s"],
             "roofline": {"bound": "hbm", "achieved": gbs_s, "peak": hbm_peak, "unit": "GB/s",
                          "frac": gbs_s / hbm_peak,
-                         "traffic": _traffic(sp["path"], 2, choice_s["cache_hints"], sp["launch_bytes"]),
+                         "traffic": _traffic(sp["path"], 2, choice_s, sp["launch_bytes"]),
                          "traffic_unit": "bytes per launch", "launch_ms": sp["step_ms"],
                          "peak_source": f"{peak_src} HBM copy bandwidth"}}
 
