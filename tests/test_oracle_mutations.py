@@ -73,3 +73,42 @@ def test_ritz_with_wrong_scale_is_caught(monkeypatch):
         return Zr, s / np.sqrt(len(parts))
     _patch(monkeypatch, "ritz", bad)
     _fails(P.test_ritz_recovers_singular_values)
+
+
+def _eta_variant(mean_weights=None, local_scale=None, signed=False, by_trace=False):
+    """An eta with one planted mistake (Def. 2 is max_i ||M_i - M||_2 / ||M||_2)."""
+    def bad(parts):
+        As = [OL.as_f64(P_) for P_ in parts]
+        sizes = [A.shape[0] for A in As]
+        n = sum(sizes)
+        p = OL.weights(sizes) if mean_weights is None else mean_weights(sizes)
+        Ms = [A.T @ A / (A.shape[0] if local_scale is None else local_scale(n, A.shape[0])) for A in As]
+        M = sum(pi * Mi for pi, Mi in zip(p, Ms))
+        norm = (lambda X: float(np.max(np.linalg.eigvalsh(X)))) if signed else \
+               (lambda X: float(np.max(np.abs(np.linalg.eigvalsh(X)))))
+        norms = [norm(Mi - M) for Mi in Ms]
+        den = float(np.trace(M)) if by_trace else norm(M)
+        return max(norms) / den, np.array(norms + [den])
+    return bad
+
+
+@pytest.mark.parametrize("variant", [
+    dict(mean_weights=lambda sizes: np.full(len(sizes), 1.0 / len(sizes))),   # unweighted M
+    dict(local_scale=lambda n, s: n),                                        # M_i with 1/n
+    dict(signed=True),                                                       # largest eigenvalue, not |.|
+    dict(by_trace=True),                                                     # normalised by trace(M)
+])
+def test_eta_mistakes_are_caught(monkeypatch, variant):
+    _patch(monkeypatch, "eta", _eta_variant(**variant))
+    _fails(P.test_eta_closed_form_for_axis_aligned_partitions)
+
+
+def test_residual_error_in_frobenius_norm_is_caught(monkeypatch):
+    good_align = OL.align
+
+    def bad(Z_loc, sizes, kind):
+        b = OL.base_index(sizes)
+        Zb = Z_loc[b]
+        return max(float(np.linalg.norm(Z @ good_align(kind, Z, Zb) - Zb)) for i, Z in enumerate(Z_loc) if i != b)
+    _patch(monkeypatch, "residual_error", bad)
+    _fails(P.test_residual_error_with_opt_matches_the_procrustes_lemma)
