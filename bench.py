@@ -507,7 +507,7 @@ def run_rounds(args):
     parts = synth.split_rows(A, sizes)
     k, d = c["k"], c["d"]
     V, _ = _truth(parts, c)
-    T = 60
+    T = 120
     out = {}
     with B.LocalPower(parts, device=local) as lp:
         for agg in ("sign", "opt"):
