@@ -119,6 +119,26 @@ def test_failures_stay_with_their_request(gpu_lib):
     assert np.array_equal(Z0, Z2)
 
 
+def test_fp8_requests_with_row_scales(gpu_lib):
+    """FP8-E4M3 requests carry one FP32 scale per row; each result matches the
+    oracle on code x scale (SIMT FP32 arithmetic: the FP32 bar)."""
+    lam = 0.85 ** np.arange(1, 129)
+    reqs = []
+    for i, (n, d, k, m) in enumerate([(6000, 128, 8, 4), (9000, 96, 5, 6)]):
+        A = synth.spiked_rows(n, d, lam[:d], 0.0, 700 + i, threads=4)
+        A32 = synth.split_rows(A, synth.partition_sizes(n, m))
+        codes, scales = map(list, zip(*[synth.f32_to_e4m3_rowscaled(a) for a in A32]))
+        reqs.append((codes, scales, [O.decode_e4m3(c, s_) for c, s_ in zip(codes, scales)],
+                     synth.gaussian_start(d, k, 710 + i)))
+    with B.Server(max_active=4) as srv:
+        ids = [srv.submit(c, y0.shape[1], SCHED, "opt", y0, dtype="e4m3", row_scales=sc) for c, sc, _, y0 in reqs]
+        _drain(srv, ids)
+        outs = [srv.result(rid) for rid in ids]
+    for (_, _, exact, y0), (Z, _, _) in zip(reqs, outs):
+        ref = O.localpower(exact, y0.shape[1], SCHED, "opt", y0)
+        assert O.subspace_dist(Z, ref["Z"]) < 1e-6
+
+
 def test_pitched_device_rows(gpu_lib):
     """A request can name rows and the first d columns of a wider device pool."""
     torch = pytest.importorskip("torch")
