@@ -51,6 +51,17 @@ __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
+// 32 lanes x 32 consecutive 32-bit columns, no wait.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r0)[16], uint32_t (&r1)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r0[0]), "=r"(r0[1]), "=r"(r0[2]), "=r"(r0[3]), "=r"(r0[4]), "=r"(r0[5]), "=r"(r0[6]), "=r"(r0[7]),
+        "=r"(r0[8]), "=r"(r0[9]), "=r"(r0[10]), "=r"(r0[11]), "=r"(r0[12]), "=r"(r0[13]), "=r"(r0[14]), "=r"(r0[15]),
+        "=r"(r1[0]), "=r"(r1[1]), "=r"(r1[2]), "=r"(r1[3]), "=r"(r1[4]), "=r"(r1[5]), "=r"(r1[6]), "=r"(r1[7]),
+        "=r"(r1[8]), "=r"(r1[9]), "=r"(r1[10]), "=r"(r1[11]), "=r"(r1[12]), "=r"(r1[13]), "=r"(r1[14]), "=r"(r1[15])
+      : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float4 (&v)[4]) {
   asm volatile(
@@ -286,8 +297,7 @@ __device__ __forceinline__ void fused_rows(const float* __restrict__ Acur, const
     uint32_t z0[16], z1[16];
     float a0 = 0.f, a1 = 0.f;
     if (NEXT) {
-      tmem_ld16_async(tq + 32 * r, z0);
-      tmem_ld16_async(tq + 32 * r + 16, z1);
+      tmem_ld32_async(tq + 32 * r, z0, z1);
       a0 = Anext_row[64 * r];
       a1 = Anext_row[64 * r + 32];
     }
@@ -407,8 +417,7 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs 
 #pragma unroll 4
       for (int s = 0; s < kT32; s += 2) {
         uint32_t z0[16], z1[16];
-        tmem_ld16_async(tq + 16 * s, z0);
-        tmem_ld16_async(tq + 16 * (s + 1), z1);
+        tmem_ld32_async(tq + 16 * s, z0, z1);
         const float a0 = Arow[32 * s], a1 = Arow[32 * (s + 1)];
         tmem_wait_ld();
         fma_row(acc, a0, z0);
