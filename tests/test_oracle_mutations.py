@@ -65,6 +65,24 @@ def test_aggregation_without_alignment_is_caught(monkeypatch):
     _fails(P.test_aggregation_invariances)
 
 
+def test_round_loop_that_ignores_the_aggregator_is_caught(monkeypatch):
+    # the loop passes "identity" to the aggregation whatever the caller asked for
+    good = OL.aggregate
+    _patch(monkeypatch, "aggregate", lambda Y_loc, Z_loc, sizes, kind: good(Y_loc, Z_loc, sizes, "identity"))
+    _fails(P.test_round_loop_matches_matrix_power_route, "sign")
+    _fails(P.test_round_loop_matches_matrix_power_route, "opt")
+    _fails(P.test_aggregators_differ_at_p_above_1)
+
+
+def test_round_loop_that_aligns_the_wrong_basis_is_caught(monkeypatch):
+    # the loop aligns orth(Y_i) (the basis after the last multiply) instead of the
+    # basis Z_i that was multiplied (App. B: D_t aligns the iterate M_i was applied to)
+    good = OL.aggregate
+    _patch(monkeypatch, "aggregate",
+           lambda Y_loc, Z_loc, sizes, kind: good(Y_loc, [OL.orth(Y) for Y in Y_loc], sizes, kind))
+    _fails(P.test_round_loop_matches_matrix_power_route, "opt")
+
+
 def test_ritz_with_wrong_scale_is_caught(monkeypatch):
     good = OL.ritz
 

@@ -119,6 +119,88 @@ def test_decay_to_p1_converges_to_eigh(agg):
     assert O.subspace_dist(r["Z"], V[:, -3:]) < 1e-10
 
 
+def _heterogeneous_parts(seed, sizes=(250, 200, 150), d=12):
+    """Uneven partitions drawn from different spiked models (each its own Haar
+    rotation), so the local iterates drift far apart within a round and both
+    sign-fixing and OPT have work to do (large eta, Def. 2)."""
+    return [synth.spiked_rows(s, d, np.array((9.0, 5.0, 3.0, 1.0)), 0.3, seed * 10 + i,
+                              out_dtype=np.float64, threads=1) for i, s in enumerate(sizes)]
+
+
+def _polar_factor_newton(C, iters=60):
+    """Orthogonal polar factor of a nonsingular C by the Newton iteration
+    X <- (X + X^{-T}) / 2 (a route that uses no SVD).  For C = W1 S W2^T it
+    converges to W1 W2^T, the minimiser of eq. (3)."""
+    X = np.array(C, dtype=np.float64)
+    for _ in range(iters):
+        X = 0.5 * (X + np.linalg.inv(X).T)
+    return X
+
+
+def _sign_by_enumeration(Z_i, Z_b):
+    """The +-1 diagonal D minimising ||Z_i D - Z_b||_F, by trying all 2^k of them (eq. (4))."""
+    k = Z_i.shape[1]
+    best = min(itertools.product((1.0, -1.0), repeat=k),
+               key=lambda s: np.linalg.norm(Z_i * np.array(s) - Z_b))
+    return np.diag(best)
+
+
+def _round_by_matrix_powers(parts, Y, p, kind):
+    """One round of Alg. 1 with the aligned aggregation of eqs. (3)-(4), built by a
+    route the oracle never takes: every M_i is formed densely, the basis worker i
+    multiplies in its last local step is orth(M_i^(p-1) Z) from one matrix power
+    and one QR (the local iterate is the Q factor of the i-th matrix power times
+    Z, Sec. 3), Y_i = M_i times that basis, the aligner comes from enumeration
+    (signs) or a Newton polar iteration (OPT), and Y = sum_i (s_i/n) Y_i D_i with
+    D_b = I for the largest partition b (App. B update rule)."""
+    sizes = [P.shape[0] for P in parts]
+    n = float(sum(sizes))
+    b = sizes.index(max(sizes))
+    Ms = [P.T @ P / P.shape[0] for P in parts]
+    Z = _qr_power(np.eye(Y.shape[0]), Y, 0)
+    last = [_qr_power(M, Z, p - 1) for M in Ms]
+    out = np.zeros_like(Y)
+    for i, (M, Zl) in enumerate(zip(Ms, last)):
+        if i == b or p == 1 or kind == "identity":
+            D = np.eye(Y.shape[1])
+        elif kind == "sign":
+            D = _sign_by_enumeration(Zl, last[b])
+        else:
+            D = _polar_factor_newton(Zl.T @ last[b])
+        out += (sizes[i] / n) * (M @ Zl) @ D
+    return out
+
+
+@pytest.mark.parametrize("agg", ["identity", "sign", "opt"])
+def test_round_loop_matches_matrix_power_route(agg):
+    """The whole round loop at p > 1 with m = 3 uneven, heterogeneous partitions:
+    the oracle's Y after T = 1, 2 and 3 rounds (schedule 3, 3, then a p = 1
+    round that aggregates without alignment) equals the matrix-power route
+    round by round, for all three aggregators."""
+    parts = _heterogeneous_parts(6)
+    Y0 = synth.gaussian_start(12, 3, 13)
+    sched = [3, 3, 1]
+    Y = Y0
+    for T in range(1, len(sched) + 1):
+        Y = _round_by_matrix_powers(parts, Y, sched[T - 1], agg)
+        got = O.localpower(parts, 3, sched[:T], agg, Y0)["Y"]
+        assert np.abs(got - Y).max() <= 1e-12 * np.abs(Y).max(), (agg, T)
+
+
+def test_aggregators_differ_at_p_above_1():
+    """With drifting local iterates the three update rules of App. B give three
+    different aggregates (so a loop that ignores the aggregator is visible), and
+    at p = 1 they coincide."""
+    parts = _heterogeneous_parts(6)
+    Y0 = synth.gaussian_start(12, 3, 13)
+    Ys = {a: O.localpower(parts, 3, [3, 2], a, Y0)["Y"] for a in O.AGGREGATORS}
+    scale = np.abs(Ys["identity"]).max()
+    for a, c in (("identity", "sign"), ("identity", "opt"), ("sign", "opt")):
+        assert np.abs(Ys[a] - Ys[c]).max() > 1e-2 * scale, (a, c)
+    Y1 = {a: O.localpower(parts, 3, [1, 1], a, Y0)["Y"] for a in O.AGGREGATORS}
+    assert max(np.abs(Y1[a] - Y1["identity"]).max() for a in O.AGGREGATORS) == 0.0
+
+
 def test_constant_p_leaves_a_floor_that_p1_removes():
     """Sec. 5 (final precision): with a constant p > 1 the error stops decreasing at
     a non-zero floor; p = 1 does not have one.  Qualitative (the floor's value has
