@@ -198,7 +198,9 @@ def _traffic(path, planes, tuning, launch_bytes, d=1024, k=16):
 
 KERNELS = {0: "step_simt2_kernel (SIMT FP32 fused A_i^T (A_i Z_i))",
            1: "step_tc_kernel (tcgen05, tile resident in shared memory, cluster-split d)",
-           2: "step_tcs_kernel (tcgen05 streaming, second pass re-read from L2)"}
+           2: "step_tcs_kernel (tcgen05 streaming, second pass re-read from L2)",
+           3: "step_pair_kernel (tcgen05, the two passes on the two CTAs of a cluster: HBM pass forms W, "
+              "L2 pass accumulates A^T W)"}
 
 
 def _kernel(path, dtype="f32", d=1024, k=16):
@@ -656,7 +658,8 @@ def run_kernels(args):
     """Each step kernel on one shape: one-step solves (a single fused-step launch
     each) per kernel, in a fixed order, for profiler captures and quick scans:
     SIMT FP32, streaming tcgen05 BF16, resident tcgen05 BF16, streaming tcgen05
-    on hi/lo planes of the FP32 data."""
+    on hi/lo planes of the FP32 data, then the pass-split pair kernel on BF16 and
+    on the hi/lo planes."""
     import synth
     from paper_2002_08014_gb300 import binding as B
 
@@ -667,25 +670,30 @@ def run_kernels(args):
     A = synth.spiked_rows(n, d, lam, np.sqrt(0.1), synth.configs.SEED_BASE + 9, threads=os.cpu_count())
     parts = synth.split_rows(A, synth.partition_sizes(n, m))
     Y0 = synth.gaussian_start(d, k, 1)
-    runs = [("f32", parts, 0), ("bf16", None, 0), ("bf16", None, B.LP_FLAG_TC_RESIDENT), ("f32_bf16x2", parts, 0)]
+    runs = [("f32", parts, 0, None), ("bf16", None, 0, "stream"), ("bf16", None, B.LP_FLAG_TC_RESIDENT, None),
+            ("f32_bf16x2", parts, 0, "stream"), ("bf16", None, 0, "pair"), ("f32_bf16x2", parts, 0, "pair")]
     bits = [synth.f32_to_bf16_bits(p) for p in parts]
     out = {}
-    for dtype, data, flags in runs:
+    for dtype, data, flags, kern in runs:
         eb = 2 if dtype == "bf16" else 4
+        name = f"{dtype}{'_resident' if flags else ''}{'_' + kern if kern else ''}"
         try:
             with B.LocalPower(data if data is not None else bits, dtype=dtype) as lp:
-                tuned = B.lp_autotune(lp.ctx, k) if args.autotune and dtype != "f32" and not flags else None
+                if kern:
+                    B.lp_set_tuning(lp.ctx, kernel=kern)
+                tuned = (B.lp_autotune(lp.ctx, k) if args.autotune and dtype != "f32" and not flags and kern != "pair"
+                         else None)
                 ms = []
                 for _ in range(max(args.steps, 2)):
                     B.lp_solve(lp.ctx, k, [1], "sign", Y0, 0, B.LP_FLAG_TIMING | B.LP_FLAG_NO_GRAPH | flags)
                     _, _, st = lp.result(k)
                     ms.append(st["ms_step_kernels"])
             best = min(ms[1:])
-            out[f"{dtype}{'_resident' if flags else ''}"] = {
+            out[name] = {
                 "kernel": _kernel(st["path"], dtype if dtype == "f32" else "bf16", d, k), "tuning": tuned,
                 "launch_ms": best, "gbs": n * d * eb / (best / 1e3) / 1e9}
         except Exception as e:
-            out[f"{dtype}{'_resident' if flags else ''}"] = {"error": str(e)[:200]}
+            out[name] = {"error": str(e)[:200]}
     print(json.dumps({"workload": "kernels", "n": n, "d": d, "k": k, "m": m, "results": out}))
 
 

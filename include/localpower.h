@@ -85,7 +85,8 @@ typedef struct lp_stats {
     int64_t n, d;
     int32_t m;
     int32_t path;              /* step kernel: 0 = SIMT FP32, 1 = tcgen05 with the tile resident in
-                                * shared memory, 2 = tcgen05 streaming (second pass re-read from L2) */
+                                * shared memory, 2 = tcgen05 streaming (second pass re-read from L2),
+                                * 3 = tcgen05 pass-split pair (LP_KERNEL_PAIR)                        */
     double a_bytes;            /* algorithmic bytes of A read by the step kernels     */
     double ms_solve;           /* solve wall time on the stream (events)              */
     double ms_step_kernels;    /* summed step-kernel time (LP_FLAG_TIMING only)       */
@@ -169,7 +170,19 @@ typedef struct lp_tuning {
     int32_t slice_cols;      /* columns of A per CTA, a multiple of 128 (default: 1024 for one
                               * plane, 512 for two); smaller slices split d over a cluster and
                               * shorten the distance between a unit's HBM read and its L2 re-read */
+    int32_t kernel;          /* LP_KERNEL_DEFAULT, LP_KERNEL_STREAM or LP_KERNEL_PAIR          */
 } lp_tuning;
+
+/* Tensor-core step kernels selectable through lp_tuning::kernel.
+ * STREAM: one CTA per SM streams each 128-row tile through shared memory
+ *         twice (the second time from L2) and forms both products.
+ * PAIR:   the two passes run on the two CTAs of a cluster: rank 0 reads the
+ *         tile from HBM and forms W = A_t Z, copies W into rank 1's shared
+ *         memory, and rank 1 re-reads the tile from L2 and accumulates A_t^T W
+ *         (d <= 1024 for k <= 16, d <= 512 for k > 16).  Same products, same
+ *         summation order within a tile.
+ * DEFAULT picks the pass-split pair kernel where it has a plan, else STREAM. */
+enum { LP_KERNEL_DEFAULT = 0, LP_KERNEL_STREAM = 1, LP_KERNEL_PAIR = 2 };
 
 /*
  * lp_set_tuning: set (tuning != NULL) or reset to defaults (NULL) the tuning
@@ -411,6 +424,9 @@ lp_status lp_align_aggregate(lp_ctx* ctx, int m, int64_t d, int k, lp_aggregator
  * device address; make that first call before any stream capture.  Every call
  * shares the one array, which keeps the last call's contents: each call
  * writes everything it reads, but calls whose work overlaps on the GPU race.
+ * A bounded wait that gives up inside the step kernel (a stall of seconds)
+ * cannot be returned as a status by this asynchronous call; instead every
+ * entry of y is set to NaN.
  */
 lp_status lp_power_step_static(const float* A, int m, const int64_t* rows, int64_t d, int k, const double* z,
                                double* y, void* stream);

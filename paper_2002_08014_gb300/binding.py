@@ -23,7 +23,7 @@ LP_MAX_K = 32
 
 AGG = {"identity": LP_AGG_IDENTITY, "sign": LP_AGG_SIGN, "opt": LP_AGG_OPT}
 DTYPE = {"f32": LP_F32, "bf16": LP_BF16, "e4m3": LP_FP8_E4M3, "f32_bf16x2": LP_F32_BF16X2}
-PATHS = {0: "simt", 1: "tc_resident", 2: "tc_streaming"}
+PATHS = {0: "simt", 1: "tc_resident", 2: "tc_streaming", 3: "tc_pair"}
 
 # Every symbol the header declares, in declaration order.
 EXPORTS = ["lp_create", "lp_load_partitions", "lp_solve", "lp_result", "lp_destroy", "lp_last_error",
@@ -45,7 +45,7 @@ class lp_stats(C.Structure):
 
 class lp_tuning(C.Structure):
     _fields_ = [("ring_units", C.c_int32), ("lag_units", C.c_int32), ("prefetch_units", C.c_int32),
-                ("cache_hints", C.c_int32), ("slice_cols", C.c_int32)]
+                ("cache_hints", C.c_int32), ("slice_cols", C.c_int32), ("kernel", C.c_int32)]
 
 
 class lp_request(C.Structure):
@@ -168,14 +168,18 @@ def lp_destroy(ctx) -> None:
     load().lp_destroy(ctx)
 
 
+KERNELS = {"default": 0, "stream": 1, "pair": 2}
+
+
 def lp_set_tuning(ctx, ring_units: int = 0, lag_units: int = 0, prefetch_units: int = 0, cache_hints: int = 0,
-                  reset: bool = False, slice_cols: int = 0) -> None:
-    """Tuning of the streaming tensor-core step (zeros keep the defaults; reset=True passes NULL)."""
+                  reset: bool = False, slice_cols: int = 0, kernel: str = "default") -> None:
+    """Tuning of the tensor-core step (zeros keep the defaults; reset=True passes NULL);
+    kernel is "default", "stream" or "pair" (LP_KERNEL_*)."""
     L = load()
     if reset:
         _check(ctx, L.lp_set_tuning(ctx, None))
         return
-    t = lp_tuning(ring_units, lag_units, prefetch_units, cache_hints, slice_cols)
+    t = lp_tuning(ring_units, lag_units, prefetch_units, cache_hints, slice_cols, KERNELS[kernel])
     _check(ctx, L.lp_set_tuning(ctx, C.byref(t)))
 
 
@@ -188,7 +192,8 @@ def lp_autotune(ctx, k: int) -> dict:
     _check(ctx, L.lp_autotune(ctx, int(k), C.byref(t), C.byref(path), C.byref(ms)))
     return {"path": PATHS.get(path.value, path.value), "path_code": path.value, "ms_per_step": ms.value,
             "ring_units": t.ring_units, "lag_units": t.lag_units, "prefetch_units": t.prefetch_units,
-            "cache_hints": t.cache_hints, "slice_cols": t.slice_cols}
+            "cache_hints": t.cache_hints, "slice_cols": t.slice_cols,
+            "kernel": {v: k for k, v in KERNELS.items()}.get(t.kernel, t.kernel)}
 
 
 def lp_eta(ctx, m: int):

@@ -157,6 +157,10 @@ void dfree(lp_ctx* c, T*& p, size_t bytes) {
 }
 
 enum Path { PATH_SIMT = 0, PATH_TC = 1, PATH_TCS = 2 };
+// What LP_KERNEL_DEFAULT means for the tensor-core step.
+constexpr int kDefaultTcKernel = LP_KERNEL_STREAM;
+// lp_stats::path code of the pass-split pair kernel (it shares PATH_TCS's tables).
+constexpr int kReportedPathPair = 3;
 
 // Tensor-core step kernels accumulate a segment's A^T W in TMEM, and the tensor
 // cores round that FP32 accumulator toward zero on every MMA, so a long chain
@@ -337,6 +341,10 @@ int max_slots_in(const std::vector<int>& slot_begin) {
   return mx;
 }
 
+int reported_path(const lp_ctx* c) {
+  return c->path == PATH_TCS && c->tcs_cur && c->tcs_cur->pair ? kReportedPathPair : c->path;
+}
+
 const int* slot_begin_of(const lp_ctx* c) {
   return c->path == PATH_TCS ? c->dSlotBeginTcs : c->path == PATH_TC ? c->dSlotBeginTc : c->dSlotBegin;
 }
@@ -364,7 +372,10 @@ lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool t
     LP_CUDA(record_event(c->step_ev[c->step_ev_used], c->stream));
   }
   cudaError_t e;
-  if (c->path == PATH_TCS)
+  if (c->path == PATH_TCS && c->tcs_cur->pair)
+    e = lp::launch_step_pair(*c->tcs_cur, c->dSegsTcs, c->dSegPtrTcs, Z, z_stride, c->dP, static_cast<int>(c->d),
+                             c->dStatus, c->stream);
+  else if (c->path == PATH_TCS)
     e = lp::launch_step_tcs(*c->tcs_cur, c->dSegsTcs, c->dSegPtrTcs, Z, z_stride, c->dP, static_cast<int>(c->d),
                             c->dStatus, c->stream);
   else if (c->path == PATH_TC)
@@ -692,7 +703,15 @@ static lp_status ensure_tcs(lp_ctx* c, int k) {
   if (c->tcs_state[idx] == 0) {
     lp::TcsPlan& p = c->tcs[idx];
     c->tcs_state[idx] = -1;
-    if (!lp::tcs_plan(static_cast<int>(c->d), K, c->planes, c->sms, c->tuning, &p))
+    p = lp::TcsPlan{};
+    bool planned = false;
+    const int want = c->tuning.kernel == LP_KERNEL_DEFAULT ? kDefaultTcKernel : c->tuning.kernel;
+    if (want == LP_KERNEL_PAIR) planned = lp::pair_plan(static_cast<int>(c->d), K, c->planes, c->sms, c->tuning, &p);
+    if (!planned && c->tuning.kernel != LP_KERNEL_PAIR) {
+      p = lp::TcsPlan{};
+      planned = lp::tcs_plan(static_cast<int>(c->d), K, c->planes, c->sms, c->tuning, &p);
+    }
+    if (!planned)
       return fail(c, LP_ERR_UNSUPPORTED, "no streaming tensor-core plan for d=" + std::to_string(c->d));
     const uint16_t* hi = static_cast<const uint16_t*>(c->dA);
     const uint16_t* lo = c->planes == 2 ? hi + size_t(c->n) * c->ld : nullptr;
@@ -741,7 +760,7 @@ static lp_status select_path(lp_ctx* c, int k, unsigned flags) {
     if (!resident) {
       const lp_status st = ensure_tcs(c, k);
       if (st == LP_OK) c->path = PATH_TCS;
-      else if (st != LP_ERR_UNSUPPORTED) return st;
+      else if (st != LP_ERR_UNSUPPORTED || c->tuning.kernel != LP_KERNEL_DEFAULT) return st;  // no silent substitute
       c->err.clear();
     }
     if (c->path == PATH_SIMT && c->dtype == LP_BF16 && c->tc_ready) {
@@ -847,13 +866,15 @@ lp_status lp_set_tuning(lp_ctx* c, const lp_tuning* t) {
   lp::TcsTuning nt;
   if (t) {
     if (t->ring_units < 0 || t->lag_units < 0 || t->prefetch_units < 0 || t->cache_hints < 0 || t->slice_cols < 0 ||
-        (t->slice_cols != 0 && t->slice_cols % 128 != 0))
-      return fail(c, LP_ERR_INVALID, "tuning fields must be >= 0, slice_cols a multiple of 128");
+        (t->slice_cols != 0 && t->slice_cols % 128 != 0) || t->kernel < 0 || t->kernel > LP_KERNEL_PAIR)
+      return fail(c, LP_ERR_INVALID,
+                  "tuning fields must be >= 0, slice_cols a multiple of 128, kernel one of LP_KERNEL_*");
     nt.ring_units = t->ring_units;
     nt.lag_units = t->lag_units;
     nt.prefetch_units = t->prefetch_units;
     nt.cache_hints = t->cache_hints;
     nt.slice_cols = t->slice_cols;
+    nt.kernel = t->kernel;
   }
   c->tuning = nt;
   c->prefer_resident = false;
@@ -878,10 +899,17 @@ lp_status lp_autotune(lp_ctx* c, int k, lp_tuning* chosen, int* path_out, double
   };
   std::vector<Cand> cands;
   if (c->planes > 0) {
+    {
+      Cand cd;
+      cd.t.kernel = LP_KERNEL_PAIR;
+      cd.resident = false;
+      cands.push_back(cd);
+    }
     for (int slice : {0, 512})
       for (int lag : {1, 2, 4})
         for (int hint : {0, 1}) {
           Cand cd;
+          cd.t.kernel = LP_KERNEL_STREAM;
           cd.t.lag_units = lag;
           cd.t.cache_hints = hint;
           cd.t.slice_cols = slice;
@@ -917,12 +945,12 @@ lp_status lp_autotune(lp_ctx* c, int k, lp_tuning* chosen, int* path_out, double
       if (best < 0 || per < best) {
         best = per;
         win = cd;
-        win_path = c->path;
+        win_path = reported_path(c);
       }
     }
   } else {
     if ((st = select_path(c, k, 0))) return st;
-    win_path = c->path;
+    win_path = reported_path(c);
   }
   c->tuning = win.t;
   c->prefer_resident = win.resident;
@@ -936,6 +964,7 @@ lp_status lp_autotune(lp_ctx* c, int k, lp_tuning* chosen, int* path_out, double
     chosen->prefetch_units = win.t.prefetch_units;
     chosen->cache_hints = win.t.cache_hints;
     chosen->slice_cols = win.t.slice_cols;
+    chosen->kernel = win.t.kernel;
   }
   if (path_out) *path_out = win_path;
   if (best_ms) *best_ms = best;
@@ -989,7 +1018,7 @@ static void solve_mark(lp_ctx* c, int k, int rounds, unsigned flags) {
   c->stats.n = c->n;
   c->stats.d = c->d;
   c->stats.m = c->m;
-  c->stats.path = c->path;
+  c->stats.path = reported_path(c);
   c->solved = true;
 }
 

@@ -80,11 +80,18 @@ struct TcsPlan {
   int hints = 0;       // L2 eviction hints on the two passes
   uint32_t off_B1 = 0, off_B2 = 0, off_W = 0, off_Wrecv = 0, off_bar = 0, tmem_cols = 0;
   size_t smem = 0;     // dynamic shared memory per CTA
+  // pass-split pair kernel (step_pair.cu): cluster = 2, `ring` is rank 0's ring,
+  // off_B1 holds Z, off_B2 the W staging / W buffers
+  int pair = 0;        // 1: this plan is for the pair kernel
+  int ring1 = 0;       // rank 1 ring units
+  int nd2 = 0;         // rank 1 Y-slice buffers in tensor memory
+  uint32_t tmem_cols1 = 0;
   alignas(64) unsigned char tmap[2][128];  // CUtensorMaps of the planes
 };
 // Tuning of the streaming kernel (lp_tuning without the C names); zeros are defaults.
 struct TcsTuning {
   int ring_units = 0, lag_units = 0, prefetch_units = 0, cache_hints = 0, slice_cols = 0;
+  int kernel = 0;  // LP_KERNEL_* of lp_tuning
 };
 // Fills the geometry for (d, k, planes).  False when the shape has no streaming kernel.
 bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan* p);
@@ -92,6 +99,12 @@ bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan*
 cudaError_t tcs_encode_maps(const void* plane0, const void* plane1, int64_t n, int d, int64_t ld, TcsPlan* p);
 cudaError_t launch_step_tcs(const TcsPlan& p, const Segment* segs, const int* seg_ptr, const float* Z,
                             int64_t z_stride, float* P, int d, int* status, cudaStream_t s);
+// Pass-split pair kernel: the same product with the HBM pass and the L2 pass on
+// the two CTAs of a cluster.  False when the shape has no plan (d > 1024 at
+// k > 16, d > 2048, or a ring under two units).
+bool pair_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan* p);
+cudaError_t launch_step_pair(const TcsPlan& p, const Segment* segs, const int* seg_ptr, const float* Z,
+                             int64_t z_stride, float* P, int d, int* status, cudaStream_t s);
 // FP32 rows (pitch src_ld) -> hi = RNE_bf16(a), lo = RNE_bf16(a - hi) planes (pitch ld,
 // columns d..ld-1 zero).
 cudaError_t launch_split_planes(const float* src, int64_t src_ld, int64_t rows, int d, uint16_t* hi, uint16_t* lo,

@@ -1,0 +1,578 @@
+// Fused local power step on the 5th-generation tensor cores, the two passes
+// split over the two CTAs of a cluster (two SMs):
+//   P[slot] = A_seg^T (A_seg Z_i)   (the unscaled local product of eq. (2)),
+// FP32 accumulation in tensor memory, A stored as one BF16 plane or as two
+// (hi = RNE_bf16(a), lo = RNE_bf16(a - hi), the FP32 data of the partition).
+//
+// Why split.  Both products need the same 128-row tile: W = A_t Z needs whole
+// rows, and A_t^T W needs W.  A tile of the FP32 workload (128 rows x 1,024
+// columns x two planes) is 512 KB, far more than shared memory, so the tile
+// streams through shared memory twice, the second time from L2.  On one SM
+// the resident Z slice leaves room for only four 32 KB units and the MMA
+// issuer stalls on every tile's W; streaming measurements on GB300 show the
+// two-pass pattern holding 6.7-7.2 TB/s only while the L2 re-read follows the
+// first read within ~256 KB per SM and the ring keeps enough bytes in flight.
+// Here each pass has an SM of its own:
+//   rank 0  streams the tile from HBM through its ring (evict_last), holds
+//           [Z_hi | Z_lo] for all d columns, accumulates
+//             D1 += A_u [Z_hi | Z_lo]        (M = 128 rows, N = 2K)
+//           in one of two TMEM buffers, and its epilogue forms
+//             W = D1[:, :K] + D1[:, K:]  (rows past the segment zeroed)
+//           as the BF16 operand [W_hi | W_lo] and copies it (one bulk copy
+//           through distributed shared memory) into rank 1's W buffer;
+//   rank 1  re-reads the same units from L2 (evict_first) one tile behind,
+//           with a deeper ring (no Z), and accumulates
+//             D2[b] += A_u^T [W_hi | W_lo]   (M = 128 columns, N = 2K)
+//           over the segment in one of two TMEM buffers, which its epilogue
+//           drains into P[slot] (Y slice = D2[:, :K] + D2[:, K:]) while the
+//           next segment accumulates into the other.
+// W moves one way, once per tile; neither pass waits on the other except
+// through two W buffers (rank 0 may run up to two tiles ahead).  With Z and W
+// split hi/lo the products carry FP32-level accuracy on BF16 operands, and the
+// sums are formed in the same order as the single-SM streaming kernel's.
+//
+// Roles (256 threads per CTA): warp 0 lane 0 issues TMA; warp 1 lane 0 issues
+// MMAs; warps 4-7 (one per TMEM lane quadrant) run the epilogue; on rank 1,
+// warp 2 lane 0 recycles W buffers; on rank 0 all warps stage Z when the
+// partition changes.  Every wait is bounded: on expiry the CTA records
+// ST_TIMEOUT, stops issuing, waits (bounded) for its own copies in flight and
+// for W copies addressed to it, retires its MMAs, frees tensor memory and
+// returns; the partner's own bounded waits then expire the same way.
+#include "lp_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace lp {
+namespace {
+
+using namespace tc;
+
+constexpr int kUnitBytes = 2 * kChunkBytes;  // 128 rows x 128 columns of one BF16 plane
+constexpr int kMaxRing = 8;
+constexpr int kSmemLimit = 232448;
+
+enum PairBar {
+  R0_D1FULL = 0,     // [2] rank 0: MMA -> epilogue, D1 of a tile complete
+  R0_D1EMPTY = 2,    // [2] rank 0: epilogue (4 warps) -> MMA, D1 read out
+  R0_B2FREE = 4,     // [2] rank 0: rank 1's W buffer may be overwritten (remote arrive)
+  R0_ZDRAIN = 6,     // rank 0: MMAs of a run retired (before Z is restaged)
+  R1_B2FULL = 7,     // [2] rank 1: W bytes landed (bulk copy from rank 0, counted in bytes)
+  R1_B2USED = 9,     // [2] rank 1: MMA -> recycler, a tile's pass-2 MMAs retired
+  R1_D2FULL = 11,    // [2] rank 1: MMA -> epilogue, a segment's Y slice complete
+  R1_D2EMPTY = 13,   // [2] rank 1: epilogue (4 warps) -> MMA, Y slice read out
+  B_EPI = 15,        // the 128 epilogue threads (bounded barrier)
+  B_DONE = 16,       // teardown: every MMA retired
+  B_RING0 = 17       // FULL[s] = B_RING0 + s, EMPTY[s] = B_RING0 + kMaxRing + s
+};
+constexpr int kNumBars = B_RING0 + 2 * kMaxRing;
+
+struct PairArgs {
+  const Segment* segs;
+  const int* seg_ptr;  // per cluster
+  const float* Z;
+  int64_t z_stride;
+  float* P;
+  int d;
+  int* status;
+  int ncd;    // 64-column chunks covering d (even)
+  int ring0;  // rank 0 ring units
+  int ring1;  // rank 1 ring units
+  int nd2;    // rank 1 Y-slice buffers in TMEM (1 or 2)
+  int hints;  // 1: rank 0 loads evict_last, rank 1 loads evict_first
+  uint32_t off_Z, off_stage, off_bar, tmem0, tmem1;
+};
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+
+template <int K, int PL>
+__global__ void __launch_bounds__(kThreads, 1)
+    step_pair_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1, PairArgs a) {
+  constexpr int N = 2 * K;
+  constexpr uint32_t B2BUF = 2 * N * 128;  // [W_hi | W_lo]^T: N rows x 128 k (two 64-k chunks)
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sRing = base;
+  unsigned char* sZ = base + a.off_Z;
+  unsigned char* sStage = base + a.off_stage;  // rank 0: staging of W; rank 1: the W buffers
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + a.off_bar);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + kNumBars);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  volatile uint32_t* sent_slot = tmem_holder + 2;      // rank 1: W copies rank 0 issued (written by rank 0)
+  volatile uint32_t* consumed_slot = tmem_holder + 3;  // rank 1: W buffers whose arrival was waited for
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = cluster_rank();
+  const int cluster_id = blockIdx.x >> 1;
+  const int NB = a.ncd / 2;
+  const int U = NB * PL;
+  const int R = rank == 0 ? a.ring0 : a.ring1;
+  const uint32_t tmem_cols = rank == 0 ? a.tmem0 : a.tmem1;
+
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&bar[R0_D1FULL + s], 1);
+      mbar_init(&bar[R0_D1EMPTY + s], 4);
+      mbar_init(&bar[R0_B2FREE + s], 1);
+      mbar_init(&bar[R1_B2FULL + s], 1);
+      mbar_init(&bar[R1_B2USED + s], 1);
+      mbar_init(&bar[R1_D2FULL + s], 1);
+      mbar_init(&bar[R1_D2EMPTY + s], 4);
+    }
+    mbar_init(&bar[R0_ZDRAIN], 1);
+    mbar_init(&bar[B_EPI], 128);
+    mbar_init(&bar[B_DONE], 1);
+    for (int s = 0; s < kMaxRing; ++s) {
+      mbar_init(&bar[B_RING0 + s], 1);
+      mbar_init(&bar[B_RING0 + kMaxRing + s], 1);
+    }
+    *abort_flag = 0;
+    *sent_slot = 0;
+    *consumed_slot = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_holder)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // both CTAs' barriers initialised before any remote arrive or copy
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    atomicOr(a.status, ST_TIMEOUT);
+  };
+  auto wait = [&](int id, uint32_t parity, bool cluster_scope) -> bool {
+    const uint32_t addr = su32(&bar[id]);
+    const long long t0 = clock64();
+    while (true) {
+      if (cluster_scope ? mbar_try_cluster(addr, parity) : mbar_try(addr, parity)) return true;
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kTimeoutCycles) {
+        give_up();
+        return false;
+      }
+    }
+  };
+  auto bounded_drain = [&](int id, uint32_t parity) {
+    const uint32_t addr = su32(&bar[id]);
+    const long long t0 = clock64();
+    while (!mbar_try_cluster(addr, parity) && clock64() - t0 < kTimeoutCycles) {
+    }
+  };
+
+  const int sb = a.seg_ptr[cluster_id], se = a.seg_ptr[cluster_id + 1];
+  auto tiles_of = [&](int s) { return static_cast<int>((a.segs[s].row1 - a.segs[s].row0 + kBM - 1) / kBM); };
+  uint32_t total_tiles = 0;
+  for (int s = sb; s < se; ++s) total_tiles += static_cast<uint32_t>(tiles_of(s));
+
+  // TMA producer over the segments [s0, s1): every unit of every tile, in order.
+  // Returns the number of units issued so far (g continues from g_start).
+  auto produce = [&](int s0, int s1, uint32_t g, uint64_t policy) -> uint32_t {
+    for (int s = s0; s < s1; ++s) {
+      const Segment sg = a.segs[s];
+      const int nt = tiles_of(s);
+      for (int t = 0; t < nt; ++t)
+        for (int u = 0; u < U; ++u) {
+          const uint32_t slot = g % R;
+          if (!wait(B_RING0 + kMaxRing + slot, ((g / R) + 1) & 1, false)) return g;
+          mbar_expect_tx(&bar[B_RING0 + slot], kUnitBytes);
+          const int b = u / PL, pl = u % PL;
+          const int row = static_cast<int>(sg.row0) + t * kBM;
+          const CUtensorMap* map = pl ? &map1 : &map0;
+          for (int j = 0; j < 2; ++j) {
+            const uint32_t dst = su32(sRing + slot * kUnitBytes + j * kChunkBytes);
+            if (a.hints) tma_load_2d_hint(dst, map, 64 * (2 * b + j), row, &bar[B_RING0 + slot], policy);
+            else tma_load_2d(dst, map, 64 * (2 * b + j), row, &bar[B_RING0 + slot]);
+          }
+          ++g;
+        }
+    }
+    return g;
+  };
+  // After an abort: copies still in flight land before the CTA's shared memory goes.
+  auto drain_ring = [&](uint32_t g_end) {
+    for (uint32_t q = g_end > static_cast<uint32_t>(R) ? g_end - R : 0; q < g_end; ++q)
+      bounded_drain(B_RING0 + q % R, (q / R) & 1);
+  };
+
+  if (rank == 0) {
+    // ===================================================================== rank 0: W = A_t Z
+    constexpr uint32_t idesc1 = idesc_bf16(128, N, false, false);
+    const int DC = 64 * a.ncd;
+    uint32_t g_prod = 0, g_mma = 0, T_epi = 0, T_mma = 0, epi_phase = 0, sent = 0, run = 0;
+    int si = sb;
+    const uint64_t pol = a.hints ? l2_policy_evict_last() : 0;
+    while (si < se) {
+      // a run: consecutive segments of one partition share Z_i
+      const int part = a.segs[si].part;
+      int sj = si + 1;
+      while (sj < se && a.segs[sj].part == part) ++sj;
+      __syncthreads();  // every role finished the previous run (its MMAs retired: ZDRAIN)
+      if (*abort_flag) break;
+      if (run == 0 || a.z_stride != 0) {
+        const float* Zg = a.Z + a.z_stride * part;
+        for (int e = tid; e < DC * K; e += kThreads) {
+          const int c = e / K, j = e % K;
+          const float z = c < a.d ? Zg[static_cast<int64_t>(c) * K + j] : 0.f;
+          const uint16_t hi = bf16_bits(z);
+          const uint16_t lo = bf16_bits(z - bf16_val(hi));
+          *reinterpret_cast<uint16_t*>(sZ + sw128_off(j, c, N)) = hi;
+          *reinterpret_cast<uint16_t*>(sZ + sw128_off(K + j, c, N)) = lo;
+        }
+      }
+      fence_async_smem();
+      __syncthreads();
+
+      if (warp == 0 && lane == 0) {
+        g_prod = produce(si, sj, g_prod, pol);
+      } else if (warp == 1 && lane == 0) {
+        // ------------------------------------------------ MMA issuer, pass 1
+        bool ok = true;
+        for (int s = si; ok && s < sj; ++s) {
+          const int nt = tiles_of(s);
+          for (int t = 0; ok && t < nt; ++t, ++T_mma) {
+            const uint32_t buf = T_mma & 1;
+            if (!(ok = wait(R0_D1EMPTY + buf, ((T_mma >> 1) + 1) & 1, false))) break;
+            for (int u = 0; u < U; ++u, ++g_mma) {
+              const uint32_t slot = g_mma % R;
+              if (!(ok = wait(B_RING0 + slot, (g_mma / R) & 1, false))) break;
+              tc_fence_after();
+              const int b = u / PL;
+              const uint32_t aS = su32(sRing + slot * kUnitBytes);
+              const uint32_t bS = su32(sZ);
+#pragma unroll
+              for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                  const uint64_t ad = sdesc(aS + j * kChunkBytes + kk * 32, 16, 1024);
+                  const uint64_t bd = sdesc(bS + (2 * b + j) * N * 128 + kk * 32, 16, 1024);
+                  mma_bf16(tmem + buf * N, ad, bd, idesc1, (u | j | kk) != 0);
+                }
+              mma_commit(&bar[B_RING0 + kMaxRing + slot]);
+              if (u == U - 1) mma_commit(&bar[R0_D1FULL + buf]);
+            }
+          }
+        }
+        // every MMA of the run retired before the next run restages Z
+        mma_commit(&bar[R0_ZDRAIN]);
+        wait(R0_ZDRAIN, run & 1, false);
+      } else if (warp >= 4) {
+        // ------------------------------------------------ epilogue: D1 -> [W_hi | W_lo] -> rank 1
+        const int r = (warp - 4) * 32 + lane;
+        const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
+        bool ok = true;
+        auto epi_sync = [&]() -> bool {
+          mbar_arrive(&bar[B_EPI]);
+          return wait(B_EPI, (epi_phase++) & 1, false);
+        };
+        for (int s = si; ok && s < sj; ++s) {
+          const Segment sg = a.segs[s];
+          const int nt = tiles_of(s);
+          for (int t = 0; ok && t < nt; ++t, ++T_epi) {
+            const uint32_t buf = T_epi & 1;
+            if (!(ok = wait(R0_D1FULL + buf, (T_epi >> 1) & 1, false))) break;
+            tc_fence_after();
+            float w[K];
+#pragma unroll
+            for (int q = 0; q < N / 16; ++q) {
+              float v[16];
+              tmem_ld16(tmem + lane_base + buf * N + q * 16, v);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const int col = q * 16 + i;
+                if (col < K) w[col] = v[i];
+                else w[col - K] += v[i];
+              }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar[R0_D1EMPTY + buf]);
+            if (!(sg.row0 + static_cast<int64_t>(t) * kBM + r < sg.row1)) {
+#pragma unroll
+              for (int j = 0; j < K; ++j) w[j] = 0.f;
+            }
+            // staging[buf] was last read by the copy of tile T_epi - 2, which thread
+            // r == 0 waited for before joining the previous tile's barrier
+            unsigned char* stg = sStage + buf * B2BUF;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+              const uint16_t hi = bf16_bits(w[j]);
+              const uint16_t lo = bf16_bits(w[j] - bf16_val(hi));
+              *reinterpret_cast<uint16_t*>(stg + sw128_off(j, r, N)) = hi;
+              *reinterpret_cast<uint16_t*>(stg + sw128_off(K + j, r, N)) = lo;
+            }
+            fence_async_smem();
+            if (!(ok = epi_sync())) break;
+            if (r == 0) {
+              if (!(ok = wait(R0_B2FREE + buf, (T_epi >> 1) & 1, true))) break;
+              bulk_s2s_cluster(mapa(su32(stg), 1), su32(stg), B2BUF, mapa(su32(&bar[R1_B2FULL + buf]), 1));
+              bulk_commit();
+              bulk_wait_read0();
+              ++sent;
+            }
+          }
+        }
+      }
+      ++run;
+      si = sj;
+    }
+    if (warp == 0 && lane == 0) drain_ring(g_prod);
+    if (warp == 4 && lane == 0) st_cluster_u32(mapa(su32(const_cast<uint32_t*>(sent_slot)), 1), sent);
+  } else {
+    // ===================================================================== rank 1: Y += A_t^T W
+    constexpr uint32_t idesc2 = idesc_bf16(128, N, true, false);
+    if (warp == 0 && lane == 0) {
+      const uint32_t g_end = produce(sb, se, 0, a.hints ? l2_policy_evict_first() : 0);
+      drain_ring(g_end);
+    } else if (warp == 1 && lane == 0) {
+      // ------------------------------------------------ MMA issuer, pass 2
+      bool ok = true;
+      uint32_t g = 0, T = 0, consumed = 0;
+      for (int s = sb, pi = 0; ok && s < se; ++s, ++pi) {
+        const int pb = pi % a.nd2;
+        const uint32_t use = static_cast<uint32_t>(pi / a.nd2);
+        const int nt = tiles_of(s);
+        for (int t = 0; ok && t < nt; ++t, ++T) {
+          const uint32_t buf = T & 1;
+          for (int u = 0; u < U; ++u, ++g) {
+            const uint32_t slot = g % R;
+            if (!(ok = wait(B_RING0 + slot, (g / R) & 1, false))) break;
+            if (u == 0) {
+              if (!(ok = wait(R1_B2FULL + buf, (T >> 1) & 1, true))) break;
+              consumed = T + 1;
+              if (t == 0 && !(ok = wait(R1_D2EMPTY + pb, (use + 1) & 1, false))) break;
+            }
+            tc_fence_after();
+            const int b = u / PL, pl = u % PL;
+            const uint32_t aS = su32(sRing + slot * kUnitBytes);
+            const uint32_t bS = su32(sStage + buf * B2BUF);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+              // A^T: M = 128 columns (two 64-column chunks, LBO apart), K = 16 rows (two 8-row groups, SBO apart)
+              const uint64_t ad = sdesc(aS + kk * 2048, kChunkBytes, 1024);
+              const uint64_t bd = sdesc(bS + (kk >> 2) * N * 128 + (kk & 3) * 32, 16, 1024);
+              mma_bf16(tmem + (pb * NB + b) * N, ad, bd, idesc2, (t == 0 && pl == 0 && kk == 0) ? 0u : 1u);
+            }
+            mma_commit(&bar[B_RING0 + kMaxRing + slot]);
+            if (u == U - 1) {
+              mma_commit(&bar[R1_B2USED + buf]);
+              if (t == nt - 1) mma_commit(&bar[R1_D2FULL + pb]);
+            }
+          }
+        }
+      }
+      *consumed_slot = consumed;
+    } else if (warp == 2 && lane == 0) {
+      // ------------------------------------------------ W buffer recycler
+      for (uint32_t b = 0; b < 2 && b < total_tiles; ++b) {
+        mbar_expect_tx(&bar[R1_B2FULL + b], B2BUF);
+        mbar_arrive_remote(mapa(su32(&bar[R0_B2FREE + b]), 0));
+      }
+      for (uint32_t T = 0; T < total_tiles; ++T) {
+        const uint32_t buf = T & 1;
+        if (!wait(R1_B2USED + buf, (T >> 1) & 1, false)) break;
+        if (T + 2 < total_tiles) {
+          mbar_expect_tx(&bar[R1_B2FULL + buf], B2BUF);
+          mbar_arrive_remote(mapa(su32(&bar[R0_B2FREE + buf]), 0));
+        }
+      }
+    } else if (warp >= 4) {
+      // ------------------------------------------------ epilogue: Y slices -> P[slot]
+      for (int s = sb, pi = 0; s < se; ++s, ++pi) {
+        const int pb = pi % a.nd2;
+        const uint32_t use = static_cast<uint32_t>(pi / a.nd2);
+        if (!wait(R1_D2FULL + pb, use & 1, false)) break;
+        tc_fence_after();
+        float* Pd = a.P + static_cast<int64_t>(a.segs[s].slot) * a.d * K;
+        for (int b = 0; b < NB; ++b) {
+          float y[K];
+#pragma unroll
+          for (int q = 0; q < N / 16; ++q) {
+            float v[16];
+            tmem_ld16(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + (pb * NB + b) * N + q * 16, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int col = q * 16 + i;
+              if (col < K) y[col] = v[i];
+              else y[col - K] += v[i];
+            }
+          }
+          const int dcol = b * 128 + (warp & 3) * 32 + lane;
+          if (dcol < a.d) {
+            float4* dst = reinterpret_cast<float4*>(Pd + static_cast<int64_t>(dcol) * K);
+#pragma unroll
+            for (int j = 0; j < K; j += 4) dst[j / 4] = make_float4(y[j], y[j + 1], y[j + 2], y[j + 3]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar[R1_D2EMPTY + pb]);
+      }
+    }
+  }
+
+  // ---- teardown: MMAs retired, W copies addressed to rank 1 landed, then free TMEM
+  if (warp == 1 && lane == 0) mma_commit(&bar[B_DONE]);
+  __syncthreads();
+  if (warp == 0 && lane == 0) bounded_drain(B_DONE, 0);
+  __syncthreads();
+  cluster_sync_all();  // rank 0's sent count is visible to rank 1; no remote traffic starts after this
+  if (rank == 1 && tid == 0) {
+    const uint32_t sent = *sent_slot;
+    for (uint32_t T = *consumed_slot; T < sent; ++T) bounded_drain(R1_B2FULL + (T & 1), (T >> 1) & 1);
+  }
+  __syncthreads();
+  cluster_sync_all();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  }
+}
+
+template <int K, int PL>
+cudaLaunchConfig_t pair_config(unsigned grid, size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <int K, int PL>
+int pair_active_clusters(size_t smem) {
+  if (cudaFuncSetAttribute(step_pair_kernel<K, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = pair_config<K, PL>(2, smem, nullptr, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, step_pair_kernel<K, PL>, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int pair_active_for(int K, int planes, size_t smem) {
+  if (planes == 1)
+    return K == 8 ? pair_active_clusters<8, 1>(smem) : K == 16 ? pair_active_clusters<16, 1>(smem)
+                                                             : pair_active_clusters<32, 1>(smem);
+  return K == 8 ? pair_active_clusters<8, 2>(smem) : K == 16 ? pair_active_clusters<16, 2>(smem)
+                                                           : pair_active_clusters<32, 2>(smem);
+}
+
+template <int K, int PL>
+cudaError_t launch_pair_t(const TcsPlan& p, const PairArgs& a, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(step_pair_kernel<K, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(p.smem));
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = pair_config<K, PL>(static_cast<unsigned>(2 * p.nclusters), p.smem, s, attr);
+  const CUtensorMap* m0 = reinterpret_cast<const CUtensorMap*>(p.tmap[0]);
+  const CUtensorMap* m1 = reinterpret_cast<const CUtensorMap*>(p.tmap[PL > 1 ? 1 : 0]);
+  return cudaLaunchKernelEx(&cfg, step_pair_kernel<K, PL>, *m0, *m1, a);
+}
+
+}  // namespace
+
+bool pair_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan* p) {
+  if (planes != 1 && planes != 2) return false;
+  const int K = k <= 8 ? 8 : (k <= 16 ? 16 : 32);
+  const int N = 2 * K;
+  int ncd = (d + 63) / 64;
+  ncd += ncd & 1;
+  const int NB = ncd / 2;
+  if (NB * N > 512) return false;  // rank 1's Y slice must fit tensor memory
+  const uint32_t zbytes = static_cast<uint32_t>(ncd) * N * 128;
+  const uint32_t stage = 2u * (2u * N * 128);
+  const uint32_t bars = kNumBars * 8 + 16;
+  const int avail = kSmemLimit - 1024 - static_cast<int>(stage + bars);
+  int ring0 = (avail - static_cast<int>(zbytes)) / kUnitBytes;
+  int ring1 = avail / kUnitBytes;
+  if (ring0 > kMaxRing) ring0 = kMaxRing;
+  if (ring1 > kMaxRing) ring1 = kMaxRing;
+  if (tune.ring_units > 0) {
+    if (ring0 > tune.ring_units) ring0 = tune.ring_units;
+    if (ring1 > tune.ring_units) ring1 = tune.ring_units;
+  }
+  if (ring0 < 2 || ring1 < 2) return false;
+  p->pair = 1;
+  p->K = K;
+  p->planes = planes;
+  p->ncd = ncd;
+  p->cluster = 2;
+  p->ring = ring0;
+  p->ring1 = ring1;
+  p->lag = 0;
+  p->prefetch = 0;
+  p->hints = 1;  // rank 0 evict_last, rank 1 evict_first (measured best for the two-pass pattern)
+  // layout: ring region (rank 1 uses it all), Z (rank 0), W staging / W buffers, barriers
+  const uint32_t ring_region = static_cast<uint32_t>(ring1 > ring0 ? ring1 : ring0) * kUnitBytes;
+  p->off_B1 = static_cast<uint32_t>(ring0) * kUnitBytes;  // Z
+  p->off_B2 = ring_region > p->off_B1 + zbytes ? ring_region : p->off_B1 + zbytes;  // staging / W buffers
+  p->off_bar = p->off_B2 + stage;
+  p->off_W = p->off_Wrecv = 0;
+  p->smem = p->off_bar + bars + 1024;
+  if (p->smem > static_cast<size_t>(kSmemLimit)) return false;
+  uint32_t c0 = 32;
+  while (c0 < static_cast<uint32_t>(2 * N)) c0 *= 2;
+  p->tmem_cols = c0;
+  p->nd2 = 2 * NB * N <= 512 ? 2 : 1;
+  uint32_t c1 = 32;
+  while (c1 < static_cast<uint32_t>(p->nd2 * NB * N)) c1 *= 2;
+  p->tmem_cols1 = c1;
+  const int active = pair_active_for(K, planes, p->smem);
+  p->nclusters = sms / 2;
+  if (active > 0 && active < p->nclusters) p->nclusters = active;
+  return p->nclusters >= 1;
+}
+
+cudaError_t launch_step_pair(const TcsPlan& p, const Segment* segs, const int* seg_ptr, const float* Z,
+                             int64_t z_stride, float* P, int d, int* status, cudaStream_t s) {
+  PairArgs a;
+  a.segs = segs;
+  a.seg_ptr = seg_ptr;
+  a.Z = Z;
+  a.z_stride = z_stride;
+  a.P = P;
+  a.d = d;
+  a.status = status;
+  a.ncd = p.ncd;
+  a.ring0 = p.ring;
+  a.ring1 = p.ring1;
+  a.nd2 = p.nd2;
+  a.hints = p.hints;
+  a.off_Z = p.off_B1;
+  a.off_stage = p.off_B2;
+  a.off_bar = p.off_bar;
+  a.tmem0 = p.tmem_cols;
+  a.tmem1 = p.tmem_cols1;
+  if (p.planes == 1) {
+    if (p.K == 8) return launch_pair_t<8, 1>(p, a, s);
+    if (p.K == 16) return launch_pair_t<16, 1>(p, a, s);
+    return launch_pair_t<32, 1>(p, a, s);
+  }
+  if (p.K == 8) return launch_pair_t<8, 2>(p, a, s);
+  if (p.K == 16) return launch_pair_t<16, 2>(p, a, s);
+  return launch_pair_t<32, 2>(p, a, s);
+}
+
+}  // namespace lp

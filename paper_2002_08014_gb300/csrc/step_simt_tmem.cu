@@ -327,6 +327,7 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs 
   extern __shared__ __align__(16) float smt[];
   __shared__ uint32_t tmem_holder;
   __shared__ __align__(8) uint64_t full[3];
+  __shared__ int s_abort;  // set when a bounded wait gave up
   float* bufs = smt;                  // 3 tiles of R x 1024
   float* Wb = smt + 3 * kTile;        // 2 x (R x K)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -335,6 +336,7 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs 
 
   if (tid == 0) {
     for (int b = 0; b < 3; ++b) tc::mbar_init(&full[b], 1);
+    s_abort = 0;
     tc::fence_mbar_init();
   }
   if (warp == 0) {
@@ -354,14 +356,19 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs 
     for (int j = 0; j < kK / 2; ++j) y[q][j] = make_float2(0.f, 0.f);
 
   uint32_t g0 = 0;  // tiles of earlier segments: tile t of this one is the CTA's tile g0 + t
+  // CTA tiles whose copy was issued / whose wait succeeded (both in tile order);
+  // they differ at the end only after a wait gave up
+  uint32_t issued = 0, waited = 0;
+  bool aborted = false;
   int cur_part = -1;
   const int sb = a.seg_ptr[blockIdx.x], se = a.seg_ptr[blockIdx.x + 1];
-  for (int si = sb; si < se; ++si) {
+  for (int si = sb; si < se && !aborted; ++si) {
     const Segment sg = a.segs[si];
     const int ntiles = static_cast<int>((sg.row1 - sg.row0 + kR - 1) / kR);
     // tile t -> buffer t % 3 (called by every thread: thread 0 issues the copy,
     // all zero the rows past the segment)
     auto issue = [&](int t) {
+      issued = g0 + t + 1;
       const int b = (g0 + t) % 3;
       float* buf = bufs + b * kTile;
       const int64_t r0 = sg.row0 + int64_t(t) * kR;
@@ -384,10 +391,15 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs 
       const long long t0 = clock64();
       while (!tc::mbar_try(addr, parity)) {
         if (clock64() - t0 > tc::kTimeoutCycles) {
+          // give up: record it; every thread leaves the tile loop at its next
+          // check (after a barrier), no further copies are issued, and thread 0
+          // waits for the copies still in flight before the CTA exits
           if (a.status && lane == 0) atomicOr(a.status, ST_TIMEOUT);
-          break;
+          s_abort = 1;
+          return;
         }
       }
+      waited = g + 1;
     };
     // every buffer is free here: the previous segment ended with a barrier
     issue(0);
@@ -427,6 +439,10 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs 
     }
     __syncthreads();
     for (int t = 0; t < ntiles; ++t) {
+      if (s_abort) {  // read after a barrier: the same decision in every thread
+        aborted = true;
+        break;
+      }
       const bool next = t + 1 < ntiles;
       // tile t + 2 goes into the buffer tile t - 1 used (freed by the last barrier)
       if (t + 2 < ntiles) issue(t + 2);
@@ -445,6 +461,8 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs 
       }
       __syncthreads();  // W(t + 1) complete; tile t's buffer and W(t) free
     }
+    if (!aborted && s_abort) aborted = true;  // a wait in the segment's last tile gave up
+    if (aborted) break;
     g0 += ntiles;
     float* Pd = a.P + size_t(sg.slot) * kD * pld;
 #pragma unroll
@@ -456,6 +474,16 @@ __global__ void __launch_bounds__(kThr, 1) step_simt_tmem_d1024_kernel(StepArgs 
             make_float4(y[q][j].x, y[q][j].y, y[q][j + 1].x, y[q][j + 1].y);
 #pragma unroll
       for (int j = 0; j < kK / 2; ++j) y[q][j] = make_float2(0.f, 0.f);
+    }
+  }
+  // After a wait gave up: the copies issued but not seen to land must land
+  // before the CTA's shared memory is released (bounded again).
+  if (tid == 0) {
+    for (uint32_t g = waited; g < issued; ++g) {
+      const uint32_t addr = su32(&full[g % 3]);
+      const long long t0 = clock64();
+      while (!tc::mbar_try(addr, (g / 3) & 1) && clock64() - t0 < tc::kTimeoutCycles) {
+      }
     }
   }
   tc_sync();

@@ -16,11 +16,17 @@
 //     first call before any stream capture.
 //   * All calls share the one array and it keeps the last call's contents.
 //     Every byte a call reads is written earlier in the same call (the kernels
-//     overwrite the tables, partials and padded blocks in full), so nothing
-//     needs clearing, but calls whose work overlaps on the GPU race with each
-//     other: serialise them (one stream, or events).
+//     overwrite the tables, partials and padded blocks in full, and the status
+//     word at the array's start is cleared on the stream first), but calls
+//     whose work overlaps on the GPU race with each other: serialise them (one
+//     stream, or events).
+//   * The call returns before the GPU runs its work, so a bounded wait that
+//     gives up inside the step kernel (a stall of seconds) cannot become a
+//     status code: a last small kernel reads the status word and, if any bit
+//     is set, overwrites every entry of y with NaN.
 //   * Inputs and outputs stay the caller's: A (FP32, partitions back to back,
 //     row pitch d), Z and Y (FP64) are device pointers.
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -44,6 +50,14 @@ lp_status fail(lp_status st, const std::string& msg) {
 }
 
 size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+
+// y <- NaN everywhere when the step recorded a failure in the status word.
+__global__ void poison_on_status_kernel(const int* status, double* y, int64_t count) {
+  if (*status == 0) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = nan;
+}
 
 }  // namespace
 
@@ -134,12 +148,13 @@ extern "C" lp_status lp_power_step_static(const float* A, int m, const int64_t* 
     cur += up256(bytes);
     return p;
   };
-  const size_t need = up256(segs.size() * sizeof(Segment)) + up256((G + 1) * sizeof(int)) +
+  const size_t need = up256(sizeof(int)) + up256(segs.size() * sizeof(Segment)) + up256((G + 1) * sizeof(int)) +
                       up256((m + 1) * sizeof(int)) + up256(m * sizeof(float)) + up256(size_t(d) * K * 4) +
                       up256(size_t(nslots) * d * K * 4) + up256(size_t(m) * d * K * 4);
   if (need > kStaticScratchBytes)
     return fail(LP_ERR_INVALID, "problem needs " + std::to_string(need) + " bytes of scratch; the static array holds " +
                                     std::to_string(kStaticScratchBytes));
+  int* dStatus = reinterpret_cast<int*>(take(sizeof(int)));
   Segment* dSegs = reinterpret_cast<Segment*>(take(segs.size() * sizeof(Segment)));
   int* dSegPtr = reinterpret_cast<int*>(take((G + 1) * sizeof(int)));
   int* dSlotBegin = reinterpret_cast<int*>(take((m + 1) * sizeof(int)));
@@ -150,7 +165,8 @@ extern "C" lp_status lp_power_step_static(const float* A, int m, const int64_t* 
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int di = static_cast<int>(d);
-  if ((e = cudaMemcpyAsync(dSegs, segs.data(), segs.size() * sizeof(Segment), cudaMemcpyHostToDevice, s)) ||
+  if ((e = cudaMemsetAsync(dStatus, 0, sizeof(int), s)) ||
+      (e = cudaMemcpyAsync(dSegs, segs.data(), segs.size() * sizeof(Segment), cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(dSegPtr, seg_ptr.data(), seg_ptr.size() * sizeof(int), cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemcpyAsync(dSlotBegin, slot_begin.data(), slot_begin.size() * sizeof(int), cudaMemcpyHostToDevice,
                            s)) ||
@@ -168,8 +184,14 @@ extern "C" lp_status lp_power_step_static(const float* A, int m, const int64_t* 
   a.z_stride = 0;
   a.P = dP;
   a.grid = G;
+  a.status = dStatus;
   if ((e = lp::launch_step_simt(a, LP_F32, K, s)) || (e = lp::launch_reduce(dP, dSlotBegin, dInvS, m, di, K, dY, s, max_slots)) ||
       (e = lp::launch_unpack(dY, y, m, di, k, K, s)))
+    return fail(LP_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
+  const int64_t count = int64_t(m) * d * k;
+  poison_on_status_kernel<<<static_cast<unsigned>(std::min<int64_t>((count + 255) / 256, 1024)), 256, 0, s>>>(
+      dStatus, y, count);
+  if ((e = cudaGetLastError()) != cudaSuccess)
     return fail(LP_ERR_CUDA, std::string("launch failed: ") + cudaGetErrorString(e));
   // The host tables above are copied from pageable memory, so the copies have
   // completed (or been staged) by the time cudaMemcpyAsync returns.

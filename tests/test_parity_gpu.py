@@ -25,7 +25,7 @@ pytestmark = pytest.mark.gpu
 TC_STEP_TOL = 1e-5
 TC_SOLVE_TOL = 1e-4
 # Path codes of lp_stats.path.
-SIMT, TC_RESIDENT, TC_STREAM = 0, 1, 2
+SIMT, TC_RESIDENT, TC_STREAM, TC_PAIR = 0, 1, 2, 3
 
 
 def _decode_planes(hi, lo):
@@ -460,7 +460,7 @@ def test_autotune_picks_a_working_kernel(gpu_lib, dtype):
     if dtype == "f32":
         assert choice["path_code"] == SIMT
     else:
-        assert choice["path_code"] in (TC_RESIDENT, TC_STREAM) and choice["ms_per_step"] > 0
+        assert choice["path_code"] in (TC_RESIDENT, TC_STREAM, TC_PAIR) and choice["ms_per_step"] > 0
     ref = O.localpower(exact, 12, [3, 1], "opt", Y0)
     assert O.subspace_dist(Z, ref["Z"]) < (1e-6 if dtype == "f32" else TC_SOLVE_TOL)
 
