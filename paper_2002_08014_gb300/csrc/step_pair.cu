@@ -31,10 +31,15 @@
 // split hi/lo the products carry FP32-level accuracy on BF16 operands, and the
 // sums are formed in the same order as the single-SM streaming kernel's.
 //
-// Roles (256 threads per CTA): warp 0 lane 0 issues TMA; warp 1 lane 0 issues
-// MMAs; warps 4-7 (one per TMEM lane quadrant) run the epilogue; on rank 1,
-// warp 2 lane 0 recycles W buffers; on rank 0 all warps stage Z when the
-// partition changes.  Every wait is bounded: on expiry the CTA records
+// Roles (384 threads per CTA): warp 0 lane 0 issues TMA; lane 0 of warps 1-4
+// issue MMAs (four issuers: one thread issues a small-N MMA about every 55
+// cycles and much slower when it also polls barriers between MMAs, while four
+// threads in four warps keep the tensor pipe fed; rank 0's issuers take units
+// round-robin, each into its own partial D1 that the epilogue sums in issuer
+// order, rank 1's take 128-column blocks round-robin, each block its own D2);
+// warps 8-11 (one per TMEM lane quadrant) run the epilogue; on rank 1, warp 5
+// lane 0 recycles W buffers; on rank 0 all warps stage Z when the partition
+// changes.  Every wait is bounded: on expiry the CTA records
 // ST_TIMEOUT, stops issuing, waits (bounded) for its own copies in flight and
 // for W copies addressed to it, retires its MMAs, frees tensor memory and
 // returns; the partner's own bounded waits then expire the same way.
@@ -47,6 +52,11 @@ namespace {
 using namespace tc;
 
 constexpr int kUnitBytes = 2 * kChunkBytes;  // 128 rows x 128 columns of one BF16 plane
+constexpr int kPairThreads = 384;
+constexpr int kIssuers = 4;    // MMA-issuing threads: lane 0 of warps 1 .. kIssuers
+constexpr int kIssuers1 = 3;   // rank 1 uses at most three (its ring of six units splits 3 x 2)
+constexpr int kRecycler = 5;   // rank 1: warp of the W-buffer recycler
+constexpr int kEpiWarp0 = 8;   // warps 8-11: epilogue (warp % 4 = TMEM lane quadrant)
 constexpr int kMaxRing = 8;
 constexpr int kSmemLimit = 232448;
 
@@ -58,7 +68,7 @@ enum PairBar {
   R1_B2FULL = 7,     // [2] rank 1: W bytes landed (bulk copy from rank 0, counted in bytes)
   R1_B2USED = 9,     // [2] rank 1: MMA -> recycler, a tile's pass-2 MMAs retired
   R1_D2FULL = 11,    // [2] rank 1: MMA -> epilogue, a segment's Y slice complete
-  R1_D2EMPTY = 13,   // [2] rank 1: epilogue (4 warps) -> MMA, Y slice read out
+  R1_D2EMPTY = 13,   // [2] rank 1: epilogue (4 warps) -> MMA issuers, Y slice read out
   B_EPI = 15,        // the 128 epilogue threads (bounded barrier)
   B_DONE = 16,       // teardown: every MMA retired
   B_RING0 = 17       // FULL[s] = B_RING0 + s, EMPTY[s] = B_RING0 + kMaxRing + s
@@ -78,6 +88,7 @@ struct PairArgs {
   int ring1;  // rank 1 ring units
   int nd2;    // rank 1 Y-slice buffers in TMEM (1 or 2)
   int hints;  // 1: rank 0 loads evict_last, rank 1 loads evict_first
+  int prefetch;  // rank 0: units brought into L2 this far ahead of their load (0: none)
   uint32_t off_Z, off_stage, off_bar, tmem0, tmem1;
 };
 
@@ -89,7 +100,7 @@ __device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v
 }
 
 template <int K, int PL>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kPairThreads, 1)
     step_pair_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1, PairArgs a) {
   constexpr int N = 2 * K;
   constexpr uint32_t B2BUF = 2 * N * 128;  // [W_hi | W_lo]^T: N rows x 128 k (two 64-k chunks)
@@ -102,7 +113,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bar + kNumBars);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   volatile uint32_t* sent_slot = tmem_holder + 2;      // rank 1: W copies rank 0 issued (written by rank 0)
-  volatile uint32_t* consumed_slot = tmem_holder + 3;  // rank 1: W buffers whose arrival was waited for
+  volatile uint32_t* consumed_slot = tmem_holder + 4;  // rank 1, per issuer: W buffers whose arrival it waited for
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t rank = cluster_rank();
@@ -111,27 +122,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int U = NB * PL;
   const int R = rank == 0 ? a.ring0 : a.ring1;
   const uint32_t tmem_cols = rank == 0 ? a.tmem0 : a.tmem1;
+  // Active issuers: rank 0 deals units round-robin, rank 1 deals 128-column blocks.
+  // The ring's slots are dealt to the issuers as well: issuer h owns slots
+  // [h * RH, (h + 1) * RH) and consumes its units strictly in order, so no thread
+  // ever waits on a slot phase more than one past the slot's last completed
+  // phase (an mbarrier parity wait further ahead would succeed at once).
+  const int HE = rank == 0 ? min(min(U, kIssuers), R) : min(min(NB, kIssuers1), R);
+  const int RH = R / HE;
+  const int h = warp - 1;  // issuer index on warps 1 .. kIssuers
+  const bool issuer = lane == 0 && warp >= 1 && warp <= kIssuers;
+  auto issuer_of = [&](int u) { return rank == 0 ? u % HE : (u / PL) % HE; };
 
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&bar[R0_D1FULL + s], 1);
+      mbar_init(&bar[R0_D1FULL + s], HE);
       mbar_init(&bar[R0_D1EMPTY + s], 4);
       mbar_init(&bar[R0_B2FREE + s], 1);
       mbar_init(&bar[R1_B2FULL + s], 1);
-      mbar_init(&bar[R1_B2USED + s], 1);
-      mbar_init(&bar[R1_D2FULL + s], 1);
+      mbar_init(&bar[R1_B2USED + s], HE);
+      mbar_init(&bar[R1_D2FULL + s], HE);
       mbar_init(&bar[R1_D2EMPTY + s], 4);
     }
-    mbar_init(&bar[R0_ZDRAIN], 1);
+    mbar_init(&bar[R0_ZDRAIN], HE);
     mbar_init(&bar[B_EPI], 128);
-    mbar_init(&bar[B_DONE], 1);
+    mbar_init(&bar[B_DONE], kIssuers);
     for (int s = 0; s < kMaxRing; ++s) {
       mbar_init(&bar[B_RING0 + s], 1);
       mbar_init(&bar[B_RING0 + kMaxRing + s], 1);
     }
     *abort_flag = 0;
     *sent_slot = 0;
-    *consumed_slot = 0;
+    for (int i = 0; i < kIssuers; ++i) consumed_slot[i] = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -174,16 +195,31 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t total_tiles = 0;
   for (int s = sb; s < se; ++s) total_tiles += static_cast<uint32_t>(tiles_of(s));
 
-  // TMA producer over the segments [s0, s1): every unit of every tile, in order.
-  // Returns the number of units issued so far (g continues from g_start).
-  auto produce = [&](int s0, int s1, uint32_t g, uint64_t policy) -> uint32_t {
+  // TMA producer over the segments [s0, s1): every unit of every tile, in order,
+  // each into the next slot of the issuer that consumes it, optionally bringing
+  // the unit PF places ahead into L2 first.  pcnt[h] counts the units dealt to
+  // issuer h, fills[s] the fills of slot s.  Returns false after an abort.
+  uint32_t pcnt[kIssuers] = {0u, 0u, 0u, 0u};
+  uint32_t fills[kMaxRing] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  auto produce = [&](int s0, int s1, uint64_t policy, int PF) -> bool {
     for (int s = s0; s < s1; ++s) {
       const Segment sg = a.segs[s];
       const int nt = tiles_of(s);
+      auto prefetch_unit = [&](int q) {
+        const int t2 = q / U, u2 = q % U, b2 = u2 / PL, pl2 = u2 % PL;
+        for (int j = 0; j < 2; ++j)
+          tma_prefetch_2d(pl2 ? &map1 : &map0, 64 * (2 * b2 + j), static_cast<int>(sg.row0) + t2 * kBM);
+      };
+      for (int q = 0; q < PF && q < nt * U; ++q) prefetch_unit(q);
       for (int t = 0; t < nt; ++t)
         for (int u = 0; u < U; ++u) {
-          const uint32_t slot = g % R;
-          if (!wait(B_RING0 + kMaxRing + slot, ((g / R) + 1) & 1, false)) return g;
+          if (PF > 0 && t * U + u + PF < nt * U) prefetch_unit(t * U + u + PF);
+          const int hh = issuer_of(u);
+          const uint32_t k = pcnt[hh];
+          const uint32_t slot = static_cast<uint32_t>(hh * RH) + k % RH;
+          if (!wait(B_RING0 + kMaxRing + slot, ((k / RH) + 1) & 1, false)) return false;
+          pcnt[hh] = k + 1;
+          ++fills[slot];
           mbar_expect_tx(&bar[B_RING0 + slot], kUnitBytes);
           const int b = u / PL, pl = u % PL;
           const int row = static_cast<int>(sg.row0) + t * kBM;
@@ -193,22 +229,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (a.hints) tma_load_2d_hint(dst, map, 64 * (2 * b + j), row, &bar[B_RING0 + slot], policy);
             else tma_load_2d(dst, map, 64 * (2 * b + j), row, &bar[B_RING0 + slot]);
           }
-          ++g;
         }
     }
-    return g;
+    return true;
   };
-  // After an abort: copies still in flight land before the CTA's shared memory goes.
-  auto drain_ring = [&](uint32_t g_end) {
-    for (uint32_t q = g_end > static_cast<uint32_t>(R) ? g_end - R : 0; q < g_end; ++q)
-      bounded_drain(B_RING0 + q % R, (q / R) & 1);
+  // After an abort: copies still in flight land before the CTA's shared memory
+  // goes (the last fill of every slot; earlier fills were waited for by then).
+  auto drain_ring = [&]() {
+    for (int q = 0; q < HE * RH; ++q)
+      if (fills[q] > 0) bounded_drain(B_RING0 + q, (fills[q] - 1) & 1);
   };
 
   if (rank == 0) {
     // ===================================================================== rank 0: W = A_t Z
     constexpr uint32_t idesc1 = idesc_bf16(128, N, false, false);
     const int DC = 64 * a.ncd;
-    uint32_t g_prod = 0, g_mma = 0, T_epi = 0, T_mma = 0, epi_phase = 0, sent = 0, run = 0;
+    uint32_t c_mma = 0, T_epi = 0, T_mma = 0, epi_phase = 0, sent = 0, run = 0;
+    bool prod_ok = true;
     int si = sb;
     const uint64_t pol = a.hints ? l2_policy_evict_last() : 0;
     while (si < se) {
@@ -220,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (*abort_flag) break;
       if (run == 0 || a.z_stride != 0) {
         const float* Zg = a.Z + a.z_stride * part;
-        for (int e = tid; e < DC * K; e += kThreads) {
+        for (int e = tid; e < DC * K; e += kPairThreads) {
           const int c = e / K, j = e % K;
           const float z = c < a.d ? Zg[static_cast<int64_t>(c) * K + j] : 0.f;
           const uint16_t hi = bf16_bits(z);
@@ -233,18 +270,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncthreads();
 
       if (warp == 0 && lane == 0) {
-        g_prod = produce(si, sj, g_prod, pol);
-      } else if (warp == 1 && lane == 0) {
-        // ------------------------------------------------ MMA issuer, pass 1
+        if (prod_ok) prod_ok = produce(si, sj, pol, a.prefetch);
+      } else if (issuer && h < HE) {
+        // ------------------------------------------------ MMA issuers, pass 1: issuer h takes units
+        // u = h, h + HE, ... of every tile into its partial D1[buf][h]
+        const int u_last = h + ((U - 1 - h) / HE) * HE;
         bool ok = true;
         for (int s = si; ok && s < sj; ++s) {
           const int nt = tiles_of(s);
           for (int t = 0; ok && t < nt; ++t, ++T_mma) {
             const uint32_t buf = T_mma & 1;
             if (!(ok = wait(R0_D1EMPTY + buf, ((T_mma >> 1) + 1) & 1, false))) break;
-            for (int u = 0; u < U; ++u, ++g_mma) {
-              const uint32_t slot = g_mma % R;
-              if (!(ok = wait(B_RING0 + slot, (g_mma / R) & 1, false))) break;
+            for (int u = h; u < U; u += HE, ++c_mma) {
+              const uint32_t slot = static_cast<uint32_t>(h * RH) + c_mma % RH;
+              if (!(ok = wait(B_RING0 + slot, (c_mma / RH) & 1, false))) break;
               tc_fence_after();
               const int b = u / PL;
               const uint32_t aS = su32(sRing + slot * kUnitBytes);
@@ -255,19 +294,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int kk = 0; kk < 4; ++kk) {
                   const uint64_t ad = sdesc(aS + j * kChunkBytes + kk * 32, 16, 1024);
                   const uint64_t bd = sdesc(bS + (2 * b + j) * N * 128 + kk * 32, 16, 1024);
-                  mma_bf16(tmem + buf * N, ad, bd, idesc1, (u | j | kk) != 0);
+                  mma_bf16(tmem + (buf * kIssuers + h) * N, ad, bd, idesc1, (u != h || j != 0 || kk != 0) ? 1u : 0u);
                 }
               mma_commit(&bar[B_RING0 + kMaxRing + slot]);
-              if (u == U - 1) mma_commit(&bar[R0_D1FULL + buf]);
+              if (u == u_last) mma_commit(&bar[R0_D1FULL + buf]);
             }
           }
         }
         // every MMA of the run retired before the next run restages Z
         mma_commit(&bar[R0_ZDRAIN]);
         wait(R0_ZDRAIN, run & 1, false);
-      } else if (warp >= 4) {
+      } else if (warp >= kEpiWarp0) {
         // ------------------------------------------------ epilogue: D1 -> [W_hi | W_lo] -> rank 1
-        const int r = (warp - 4) * 32 + lane;
+        const int r = (warp - kEpiWarp0) * 32 + lane;
         const uint32_t lane_base = static_cast<uint32_t>((warp & 3) * 32) << 16;
         bool ok = true;
         auto epi_sync = [&]() -> bool {
@@ -281,16 +320,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t buf = T_epi & 1;
             if (!(ok = wait(R0_D1FULL + buf, (T_epi >> 1) & 1, false))) break;
             tc_fence_after();
+            // W = sum over the issuers' partials, each [hi part | lo part] (fixed order)
             float w[K];
 #pragma unroll
-            for (int q = 0; q < N / 16; ++q) {
-              float v[16];
-              tmem_ld16(tmem + lane_base + buf * N + q * 16, v);
+            for (int j = 0; j < K; ++j) w[j] = 0.f;
+            for (int hh = 0; hh < HE; ++hh) {
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                const int col = q * 16 + i;
-                if (col < K) w[col] = v[i];
-                else w[col - K] += v[i];
+              for (int q = 0; q < N / 16; ++q) {
+                float v[16];
+                tmem_ld16(tmem + lane_base + (buf * kIssuers + hh) * N + q * 16, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                  const int col = q * 16 + i;
+                  w[col < K ? col : col - K] += v[i];
+                }
               }
             }
             tc_fence_before();
@@ -325,28 +368,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       ++run;
       si = sj;
     }
-    if (warp == 0 && lane == 0) drain_ring(g_prod);
-    if (warp == 4 && lane == 0) st_cluster_u32(mapa(su32(const_cast<uint32_t*>(sent_slot)), 1), sent);
+    if (warp == 0 && lane == 0) drain_ring();
+    if (warp == kEpiWarp0 && lane == 0) st_cluster_u32(mapa(su32(const_cast<uint32_t*>(sent_slot)), 1), sent);
   } else {
     // ===================================================================== rank 1: Y += A_t^T W
     constexpr uint32_t idesc2 = idesc_bf16(128, N, true, false);
     if (warp == 0 && lane == 0) {
-      const uint32_t g_end = produce(sb, se, 0, a.hints ? l2_policy_evict_first() : 0);
-      drain_ring(g_end);
-    } else if (warp == 1 && lane == 0) {
-      // ------------------------------------------------ MMA issuer, pass 2
+      produce(sb, se, a.hints ? l2_policy_evict_first() : 0, 0);
+      drain_ring();
+    } else if (issuer && h < HE) {
+      // ------------------------------------------------ MMA issuers, pass 2: issuer h takes the
+      // 128-column blocks b = h, h + HE, ... (both planes of each), each into its own D2 slice
+      const int b_last = h + ((NB - 1 - h) / HE) * HE;
+      const int u_first = h * PL, u_last = b_last * PL + PL - 1;
       bool ok = true;
-      uint32_t g = 0, T = 0, consumed = 0;
+      uint32_t c = 0, T = 0, consumed = 0;
       for (int s = sb, pi = 0; ok && s < se; ++s, ++pi) {
         const int pb = pi % a.nd2;
         const uint32_t use = static_cast<uint32_t>(pi / a.nd2);
         const int nt = tiles_of(s);
         for (int t = 0; ok && t < nt; ++t, ++T) {
           const uint32_t buf = T & 1;
-          for (int u = 0; u < U; ++u, ++g) {
-            const uint32_t slot = g % R;
-            if (!(ok = wait(B_RING0 + slot, (g / R) & 1, false))) break;
-            if (u == 0) {
+          for (int u = u_first; u <= u_last; u = ((u % PL) == PL - 1) ? u + (HE - 1) * PL + 1 : u + 1, ++c) {
+            const uint32_t slot = static_cast<uint32_t>(h * RH) + c % RH;
+            if (!(ok = wait(B_RING0 + slot, (c / RH) & 1, false))) break;
+            if (u == u_first) {
               if (!(ok = wait(R1_B2FULL + buf, (T >> 1) & 1, true))) break;
               consumed = T + 1;
               if (t == 0 && !(ok = wait(R1_D2EMPTY + pb, (use + 1) & 1, false))) break;
@@ -363,15 +409,15 @@ __global__ void __launch_bounds__(kThreads, 1)
               mma_bf16(tmem + (pb * NB + b) * N, ad, bd, idesc2, (t == 0 && pl == 0 && kk == 0) ? 0u : 1u);
             }
             mma_commit(&bar[B_RING0 + kMaxRing + slot]);
-            if (u == U - 1) {
+            if (u == u_last) {
               mma_commit(&bar[R1_B2USED + buf]);
               if (t == nt - 1) mma_commit(&bar[R1_D2FULL + pb]);
             }
           }
         }
       }
-      *consumed_slot = consumed;
-    } else if (warp == 2 && lane == 0) {
+      consumed_slot[h] = consumed;
+    } else if (warp == kRecycler && lane == 0) {
       // ------------------------------------------------ W buffer recycler
       for (uint32_t b = 0; b < 2 && b < total_tiles; ++b) {
         mbar_expect_tx(&bar[R1_B2FULL + b], B2BUF);
@@ -385,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_arrive_remote(mapa(su32(&bar[R0_B2FREE + buf]), 0));
         }
       }
-    } else if (warp >= 4) {
+    } else if (warp >= kEpiWarp0) {
       // ------------------------------------------------ epilogue: Y slices -> P[slot]
       for (int s = sb, pi = 0; s < se; ++s, ++pi) {
         const int pb = pi % a.nd2;
@@ -421,14 +467,16 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   // ---- teardown: MMAs retired, W copies addressed to rank 1 landed, then free TMEM
-  if (warp == 1 && lane == 0) mma_commit(&bar[B_DONE]);
+  if (issuer) mma_commit(&bar[B_DONE]);  // every issuer's MMAs (none for an idle issuer)
   __syncthreads();
   if (warp == 0 && lane == 0) bounded_drain(B_DONE, 0);
   __syncthreads();
   cluster_sync_all();  // rank 0's sent count is visible to rank 1; no remote traffic starts after this
   if (rank == 1 && tid == 0) {
     const uint32_t sent = *sent_slot;
-    for (uint32_t T = *consumed_slot; T < sent; ++T) bounded_drain(R1_B2FULL + (T & 1), (T >> 1) & 1);
+    uint32_t consumed = consumed_slot[0];
+    for (int i = 1; i < HE; ++i) consumed = consumed_slot[i] < consumed ? consumed_slot[i] : consumed;
+    for (uint32_t T = consumed; T < sent; ++T) bounded_drain(R1_B2FULL + (T & 1), (T >> 1) & 1);
   }
   __syncthreads();
   cluster_sync_all();
@@ -442,7 +490,7 @@ template <int K, int PL>
 cudaLaunchConfig_t pair_config(unsigned grid, size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
-  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.blockDim = dim3(kPairThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -503,7 +551,7 @@ bool pair_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan
   if (NB * N > 512) return false;  // rank 1's Y slice must fit tensor memory
   const uint32_t zbytes = static_cast<uint32_t>(ncd) * N * 128;
   const uint32_t stage = 2u * (2u * N * 128);
-  const uint32_t bars = kNumBars * 8 + 16;
+  const uint32_t bars = kNumBars * 8 + 32;  // barriers, TMEM holder, abort flag, sent, consumed[kIssuers]
   const int avail = kSmemLimit - 1024 - static_cast<int>(stage + bars);
   int ring0 = (avail - static_cast<int>(zbytes)) / kUnitBytes;
   int ring1 = avail / kUnitBytes;
@@ -522,7 +570,7 @@ bool pair_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan
   p->ring = ring0;
   p->ring1 = ring1;
   p->lag = 0;
-  p->prefetch = 0;
+  p->prefetch = tune.prefetch_units > 0 ? tune.prefetch_units : 0;
   p->hints = 1;  // rank 0 evict_last, rank 1 evict_first (measured best for the two-pass pattern)
   // layout: ring region (rank 1 uses it all), Z (rank 0), W staging / W buffers, barriers
   const uint32_t ring_region = static_cast<uint32_t>(ring1 > ring0 ? ring1 : ring0) * kUnitBytes;
@@ -533,7 +581,8 @@ bool pair_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan
   p->smem = p->off_bar + bars + 1024;
   if (p->smem > static_cast<size_t>(kSmemLimit)) return false;
   uint32_t c0 = 32;
-  while (c0 < static_cast<uint32_t>(2 * N)) c0 *= 2;
+  while (c0 < static_cast<uint32_t>(2 * kIssuers * N)) c0 *= 2;  // D1[2][kIssuers]
+  if (c0 > 512) return false;
   p->tmem_cols = c0;
   p->nd2 = 2 * NB * N <= 512 ? 2 : 1;
   uint32_t c1 = 32;
@@ -560,6 +609,7 @@ cudaError_t launch_step_pair(const TcsPlan& p, const Segment* segs, const int* s
   a.ring1 = p.ring1;
   a.nd2 = p.nd2;
   a.hints = p.hints;
+  a.prefetch = p.prefetch;
   a.off_Z = p.off_B1;
   a.off_stage = p.off_B2;
   a.off_bar = p.off_bar;
