@@ -158,7 +158,7 @@ void dfree(lp_ctx* c, T*& p, size_t bytes) {
 
 enum Path { PATH_SIMT = 0, PATH_TC = 1, PATH_TCS = 2 };
 // What LP_KERNEL_DEFAULT means for the tensor-core step.
-constexpr int kDefaultTcKernel = LP_KERNEL_STREAM;
+constexpr int kDefaultTcKernel = LP_KERNEL_PAIR;
 // lp_stats::path code of the pass-split pair kernel (it shares PATH_TCS's tables).
 constexpr int kReportedPathPair = 3;
 

@@ -105,3 +105,22 @@ def test_pair_kernel_rejects_what_it_cannot_plan(gpu_lib):
         with pytest.raises(B.LPError) as e:
             lp.power_step(32, O.orth(np.random.default_rng(1).standard_normal((2048, 32))))
         assert e.value.status == B.LP_ERR_UNSUPPORTED
+
+
+def test_pair_kernel_is_deterministic_for_every_ring_depth(gpu_lib):
+    """Each issuer's accumulation chain and the epilogue's sum over issuers run in
+    a fixed order: a solve repeats bit for bit.  A smaller ring deals units to
+    fewer issuers (another summation order), within the same bar of the oracle."""
+    sizes = [3000, 2500, 1777]
+    stored, exact, _ = _parts(sizes, 512, 31, "bf16")
+    y0 = np.random.default_rng(32).standard_normal((512, 16))
+    sched = [2, 1]
+    ref = O.localpower(exact, 16, sched, "sign", y0)["Z"]
+    with B.LocalPower(stored, dtype="bf16") as lp:
+        for ring in (0, 2, 3):
+            B.lp_set_tuning(lp.ctx, ring_units=ring, kernel="pair")
+            Z1, _, st = lp.solve(16, sched, "sign", y0)
+            Z2, _, _ = lp.solve(16, sched, "sign", y0)
+            assert st["path"] == TC_PAIR
+            assert np.array_equal(Z1, Z2), ring
+            assert O.subspace_dist(Z1, ref) < TC_SOLVE_TOL, ring

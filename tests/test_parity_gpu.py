@@ -182,12 +182,12 @@ def test_fp32_workload_shape_decay_schedule(gpu_lib, agg):
 
 
 @pytest.mark.parametrize("dtype,flags,path", [
-    ("bf16", 0, TC_STREAM), ("bf16", B.LP_FLAG_TC_RESIDENT, TC_RESIDENT), ("bf16", B.LP_FLAG_SIMT, SIMT),
-    ("e4m3", 0, SIMT), ("f32_bf16x2", 0, TC_STREAM)])
+    ("bf16", 0, TC_PAIR), ("bf16", B.LP_FLAG_TC_RESIDENT, TC_RESIDENT), ("bf16", B.LP_FLAG_SIMT, SIMT),
+    ("e4m3", 0, SIMT), ("f32_bf16x2", 0, TC_PAIR)])
 def test_reduced_precision_storage_end_to_end(gpu_lib, dtype, flags, path):
     """BF16 / FP8-E4M3 / split-plane stored A: the oracle runs on the decoded
-    stored values.  BF16 and split planes run on the tensor cores (streaming
-    kernel unless the resident one or the SIMT kernel is asked for)."""
+    stored values.  BF16 and split planes run on the tensor cores (the pass-split
+    pair kernel by default, the resident one or the SIMT kernel on request)."""
     sizes = [900, 1100, 1000, 1000]
     stored, exact, scales = _parts(sizes, 200, 55, dtype, spikes=10)
     Y0 = synth.gaussian_start(200, 8, 56)
@@ -220,13 +220,24 @@ def test_tensor_core_step_shapes(gpu_lib, d, k, sizes):
         Y = B.lp_power_step(lp.ctx, k, Zs, False, len(sizes), d)
         for i, P in enumerate(exact):
             assert _relF(Y[i], O.local_step(P, Zs[i])) < TC_STEP_TOL, (i, _relF(Y[i], O.local_step(P, Zs[i])))
-        # the whole solve on both tensor-core kernels (and the SIMT kernel where it exists)
-        runs = [(0, TC_STREAM)]
+        # whether the pair kernel has a plan here decides what the default runs
+        B.lp_set_tuning(lp.ctx, kernel="pair")
+        try:
+            B.lp_power_step(lp.ctx, k, Zs, False, len(sizes), d)
+            default_path = TC_PAIR
+        except B.LPError as e:
+            assert e.status == B.LP_ERR_UNSUPPORTED
+            default_path = TC_STREAM
+        # the whole solve on every tensor-core kernel (and the SIMT kernel where it exists)
+        runs = [("default", 0, default_path), ("stream", 0, TC_STREAM)]
+        if default_path == TC_PAIR:
+            runs.append(("pair", 0, TC_PAIR))
         if d <= 2048:
-            runs.append((B.LP_FLAG_TC_RESIDENT, TC_RESIDENT))
+            runs.append(("default", B.LP_FLAG_TC_RESIDENT, TC_RESIDENT))
         if d <= 1024:
-            runs.append((B.LP_FLAG_SIMT, SIMT))
-        for flags, path in runs:
+            runs.append(("default", B.LP_FLAG_SIMT, SIMT))
+        for kern, flags, path in runs:
+            B.lp_set_tuning(lp.ctx, kernel=kern)
             B.lp_solve(lp.ctx, k, sched, "opt", Y0, 0, flags)
             Z, _, st = lp.result(k)
             assert st["path"] == path
@@ -259,7 +270,7 @@ def test_split_plane_storage(gpu_lib, d, k, sizes):
         for i, P in enumerate(exact):
             assert _relF(Y[i], O.local_step(P, Zs[i])) < TC_STEP_TOL, (i, _relF(Y[i], O.local_step(P, Zs[i])))
         Z, _, st = lp.solve(k, sched, "sign", Y0)
-        assert st["path"] == TC_STREAM
+        assert st["path"] in (TC_PAIR, TC_STREAM)
         with pytest.raises(B.LPError) as e:  # no SIMT kernel reads split planes
             B.lp_solve(lp.ctx, k, sched, "sign", Y0, 0, B.LP_FLAG_SIMT)
         assert e.value.status == B.LP_ERR_UNSUPPORTED
@@ -425,7 +436,7 @@ def test_tuning_changes_speed_not_results(gpu_lib):
     outs = []
     with B.LocalPower(stored, dtype="bf16") as lp:
         for ring, lag, pf, hint in [(0, 0, 0, 0), (2, 1, 0, 0), (3, 4, 0, 1), (0, 2, 4, 1), (5, 3, 8, 0)]:
-            B.lp_set_tuning(lp.ctx, ring, lag, pf, hint)
+            B.lp_set_tuning(lp.ctx, ring, lag, pf, hint, kernel="stream")
             Z, _, st = lp.solve(16, sched, "sign", Y0)
             assert st["path"] == TC_STREAM
             outs.append(Z)
@@ -439,7 +450,7 @@ def test_tuning_changes_speed_not_results(gpu_lib):
     assert O.subspace_dist(outs[0], ref["Z"]) < TC_SOLVE_TOL
     # narrower column slices (a cluster splits d): another summation order, same result to the bar
     with B.LocalPower(stored, dtype="bf16") as lp:
-        B.lp_set_tuning(lp.ctx, slice_cols=128)
+        B.lp_set_tuning(lp.ctx, slice_cols=128, kernel="stream")
         Zs, _, st = lp.solve(16, sched, "sign", Y0)
         assert st["path"] == TC_STREAM
         with pytest.raises(B.LPError) as e:
