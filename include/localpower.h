@@ -145,6 +145,21 @@ lp_status lp_solve(lp_ctx* ctx, int k, const int* p_schedule, int T, lp_aggregat
                    const double* y0, int refine_rounds, unsigned flags);
 
 /*
+ * lp_solve_seeded: lp_solve with the start block Y_0 drawn by the library from
+ * `seed` instead of passed in (Alg. 1 starts from a random orthonormal basis;
+ * Z_0 = orth(Y_0) as in lp_solve).  Y_0's d x k entries (row-major) are N(0,1)
+ * draws from a counter-based generator: SplitMix64 (Steele, Lea & Flood, OOPSLA
+ * 2014) evaluated at counters seed + (c + 1) * 0x9E3779B97F4A7C15, the top 53
+ * bits as a uniform u in [0, 1), and Box-Muller on consecutive pairs: counters
+ * 2q, 2q + 1 give r = sqrt(-2 ln(1 - u_2q)), theta = 2 pi u_2q+1, entry 2q =
+ * r cos(theta) and entry 2q + 1 = r sin(theta).  The same seed gives the same
+ * start on every machine up to the host's last-digit rounding of log, cos and
+ * sin.  Same arguments, asynchrony and errors as lp_solve otherwise.
+ */
+lp_status lp_solve_seeded(lp_ctx* ctx, int k, const int* p_schedule, int T, lp_aggregator agg, uint64_t seed,
+                          int refine_rounds, unsigned flags);
+
+/*
  * lp_result: wait for the last solve and copy its output to host memory.
  *   z_out      d x k row-major FP64: Z_T = orth(Y_T) (Alg. 1 output), or with
  *              LP_FLAG_RITZ the Ritz vectors ordered by descending Ritz value.
@@ -171,6 +186,13 @@ typedef struct lp_tuning {
                               * plane, 512 for two); smaller slices split d over a cluster and
                               * shorten the distance between a unit's HBM read and its L2 re-read */
     int32_t kernel;          /* LP_KERNEL_DEFAULT, LP_KERNEL_STREAM or LP_KERNEL_PAIR          */
+    int32_t test_stall_cycles; /* test hook, 0 in normal use.  > 0: the pair kernel's HBM-pass
+                              * producer, after its first ring fill, waits on a barrier that
+                              * nothing completes, with this many SM clock cycles as the limit
+                              * instead of the ~2 s of every other wait; the wait runs out, the
+                              * kernel records the timeout, drains its copies and MMAs and
+                              * returns, and the solve reports LP_ERR_TIMEOUT.  The context
+                              * stays usable (reset the field and solve again).               */
 } lp_tuning;
 
 /* Tensor-core step kernels selectable through lp_tuning::kernel.
@@ -375,6 +397,8 @@ void lp_batch_destroy(lp_batch* b);
  *          else m consecutive d x k blocks (Z_1, ..., Z_m).
  *   y_out  m consecutive d x k FP64 blocks.
  *   space  where z and y_out live.
+ * Synchronises the context's stream; LP_ERR_TIMEOUT if a bounded device wait
+ * gave up (y_out is then not the product).
  */
 lp_status lp_power_step(lp_ctx* ctx, int k, const double* z, int z_shared, double* y_out, lp_ptr_space space);
 

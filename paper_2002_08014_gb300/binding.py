@@ -26,7 +26,7 @@ DTYPE = {"f32": LP_F32, "bf16": LP_BF16, "e4m3": LP_FP8_E4M3, "f32_bf16x2": LP_F
 PATHS = {0: "simt", 1: "tc_resident", 2: "tc_streaming", 3: "tc_pair"}
 
 # Every symbol the header declares, in declaration order.
-EXPORTS = ["lp_create", "lp_load_partitions", "lp_solve", "lp_result", "lp_destroy", "lp_last_error",
+EXPORTS = ["lp_create", "lp_load_partitions", "lp_solve", "lp_solve_seeded", "lp_result", "lp_destroy", "lp_last_error",
            "lp_set_tuning", "lp_autotune", "lp_trace", "lp_eta", "lp_server_create", "lp_server_submit", "lp_server_progress",
            "lp_server_result", "lp_server_query", "lp_server_error", "lp_server_destroy", "lp_batch_create",
            "lp_batch_add", "lp_batch_autotune", "lp_batch_solve", "lp_batch_result", "lp_batch_size", "lp_batch_error",
@@ -45,7 +45,8 @@ class lp_stats(C.Structure):
 
 class lp_tuning(C.Structure):
     _fields_ = [("ring_units", C.c_int32), ("lag_units", C.c_int32), ("prefetch_units", C.c_int32),
-                ("cache_hints", C.c_int32), ("slice_cols", C.c_int32), ("kernel", C.c_int32)]
+                ("cache_hints", C.c_int32), ("slice_cols", C.c_int32), ("kernel", C.c_int32),
+                ("test_stall_cycles", C.c_int32)]
 
 
 class lp_request(C.Structure):
@@ -90,6 +91,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
     L.lp_create.argtypes = [C.POINTER(P), I, C.c_size_t, P]
     L.lp_load_partitions.argtypes = [P, I, C.POINTER(I64), I64, I, C.POINTER(P), C.POINTER(P), I]
     L.lp_solve.argtypes = [P, I, C.POINTER(I), I, I, P, I, U]
+    L.lp_solve_seeded.argtypes = [P, I, C.POINTER(I), I, I, C.c_uint64, I, U]
     L.lp_result.argtypes = [P, P, P, C.POINTER(lp_stats)]
     L.lp_destroy.argtypes = [P]
     L.lp_destroy.restype = None
@@ -172,14 +174,15 @@ KERNELS = {"default": 0, "stream": 1, "pair": 2}
 
 
 def lp_set_tuning(ctx, ring_units: int = 0, lag_units: int = 0, prefetch_units: int = 0, cache_hints: int = 0,
-                  reset: bool = False, slice_cols: int = 0, kernel: str = "default") -> None:
+                  reset: bool = False, slice_cols: int = 0, kernel: str = "default",
+                  test_stall_cycles: int = 0) -> None:
     """Tuning of the tensor-core step (zeros keep the defaults; reset=True passes NULL);
     kernel is "default", "stream" or "pair" (LP_KERNEL_*)."""
     L = load()
     if reset:
         _check(ctx, L.lp_set_tuning(ctx, None))
         return
-    t = lp_tuning(ring_units, lag_units, prefetch_units, cache_hints, slice_cols, KERNELS[kernel])
+    t = lp_tuning(ring_units, lag_units, prefetch_units, cache_hints, slice_cols, KERNELS[kernel], test_stall_cycles)
     _check(ctx, L.lp_set_tuning(ctx, C.byref(t)))
 
 
@@ -255,6 +258,15 @@ def lp_solve(ctx, k: int, p_schedule, agg: str, y0: np.ndarray, refine_rounds: i
     y0c = np.ascontiguousarray(y0, dtype=np.float64)
     _check(ctx, L.lp_solve(ctx, int(k), sched.ctypes.data_as(C.POINTER(C.c_int)) if T else None, T, AGG[agg],
                            C.c_void_p(y0c.ctypes.data), int(refine_rounds), int(flags)))
+
+
+def lp_solve_seeded(ctx, k: int, p_schedule, agg: str, seed: int, refine_rounds: int = 0, flags: int = 0) -> None:
+    """lp_solve with Y_0 drawn by the library from `seed` (SplitMix64 + Box-Muller)."""
+    L = load()
+    sched = np.ascontiguousarray(np.asarray(p_schedule, dtype=np.int32))
+    T = int(sched.shape[0])
+    _check(ctx, L.lp_solve_seeded(ctx, int(k), sched.ctypes.data_as(C.POINTER(C.c_int)) if T else None, T, AGG[agg],
+                                  C.c_uint64(int(seed)), int(refine_rounds), int(flags)))
 
 
 def lp_result(ctx, d: int, k: int):

@@ -866,7 +866,8 @@ lp_status lp_set_tuning(lp_ctx* c, const lp_tuning* t) {
   lp::TcsTuning nt;
   if (t) {
     if (t->ring_units < 0 || t->lag_units < 0 || t->prefetch_units < 0 || t->cache_hints < 0 || t->slice_cols < 0 ||
-        (t->slice_cols != 0 && t->slice_cols % 128 != 0) || t->kernel < 0 || t->kernel > LP_KERNEL_PAIR)
+        (t->slice_cols != 0 && t->slice_cols % 128 != 0) || t->kernel < 0 || t->kernel > LP_KERNEL_PAIR ||
+        t->test_stall_cycles < 0)
       return fail(c, LP_ERR_INVALID,
                   "tuning fields must be >= 0, slice_cols a multiple of 128, kernel one of LP_KERNEL_*");
     nt.ring_units = t->ring_units;
@@ -875,6 +876,7 @@ lp_status lp_set_tuning(lp_ctx* c, const lp_tuning* t) {
     nt.cache_hints = t->cache_hints;
     nt.slice_cols = t->slice_cols;
     nt.kernel = t->kernel;
+    nt.test_stall_cycles = t->test_stall_cycles;
   }
   c->tuning = nt;
   c->prefer_resident = false;
@@ -965,6 +967,7 @@ lp_status lp_autotune(lp_ctx* c, int k, lp_tuning* chosen, int* path_out, double
     chosen->cache_hints = win.t.cache_hints;
     chosen->slice_cols = win.t.slice_cols;
     chosen->kernel = win.t.kernel;
+    chosen->test_stall_cycles = 0;
   }
   if (path_out) *path_out = win_path;
   if (best_ms) *best_ms = best;
@@ -1020,6 +1023,42 @@ static void solve_mark(lp_ctx* c, int k, int rounds, unsigned flags) {
   c->stats.m = c->m;
   c->stats.path = reported_path(c);
   c->solved = true;
+}
+
+// Y_0 for lp_solve_seeded: N(0,1) entries from a counter-based generator,
+// SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014) on counters seed + (c + 1) * golden gamma, the top 53
+// bits as a uniform in [0, 1), and the Box-Muller transform on consecutive pairs
+// (counters 2q and 2q + 1 give entries 2q (cosine) and 2q + 1 (sine) of the
+// row-major d x k block).
+static uint64_t splitmix64_at(uint64_t seed, uint64_t counter) {
+  uint64_t z = seed + (counter + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static void draw_start(uint64_t seed, size_t count, std::vector<double>& y) {
+  y.resize(count);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (size_t q = 0; 2 * q < count; ++q) {
+    const double u1 = static_cast<double>(splitmix64_at(seed, 2 * q) >> 11) * 0x1.0p-53;
+    const double u2 = static_cast<double>(splitmix64_at(seed, 2 * q + 1) >> 11) * 0x1.0p-53;
+    const double r = std::sqrt(-2.0 * std::log1p(-u1));  // 1 - u1 lies in (0, 1]
+    y[2 * q] = r * std::cos(two_pi * u2);
+    if (2 * q + 1 < count) y[2 * q + 1] = r * std::sin(two_pi * u2);
+  }
+}
+
+lp_status lp_solve_seeded(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, uint64_t seed,
+                          int refine_rounds, unsigned flags) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  if (c->m == 0) return fail(c, LP_ERR_STATE, "no partitions loaded");
+  if (k < 1 || k > LP_MAX_K) return fail(c, LP_ERR_INVALID, "k must be in [1, 32]");
+  std::vector<double> y0;
+  draw_start(seed, size_t(c->d) * size_t(k), y0);
+  return lp_solve(c, k, p_schedule, T, agg, y0.data(), refine_rounds, flags);
 }
 
 lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, const double* y0,
@@ -1119,10 +1158,11 @@ lp_status lp_result(lp_ctx* c, double* z_out, double* sigma_out, lp_stats* stats
     else std::memset(sigma_out, 0, size_t(c->k) * 8);
   }
   if (stats) *stats = c->stats;
+  if (status & lp::ST_TIMEOUT)  // first: a wait that gave up leaves the later steps garbage
+    return fail(c, LP_ERR_TIMEOUT, "device wait timed out");
   if (status & lp::ST_CHOL) return fail(c, LP_ERR_NUMERIC, "Cholesky breakdown (non-positive or non-finite pivot)");
   if (status & lp::ST_NONFINITE) return fail(c, LP_ERR_NUMERIC, "non-finite iterate");
   if (status & lp::ST_JACOBI) return fail(c, LP_ERR_NUMERIC, "Jacobi iteration did not converge or singular block");
-  if (status & lp::ST_TIMEOUT) return fail(c, LP_ERR_TIMEOUT, "device wait timed out");
   return LP_OK;
 }
 
@@ -1151,7 +1191,10 @@ lp_status lp_power_step(lp_ctx* c, int k, const double* z, int z_shared, double*
   if ((st = check_launch(c, lp::launch_unpack(c->dYl, dst, c->m, d, k, K, c->stream), "unpack"))) return st;
   if (space == LP_HOST)
     LP_CUDA(cudaMemcpyAsync(y_out, dst, size_t(c->m) * d * k * 8, cudaMemcpyDeviceToHost, c->stream));
+  int status = 0;
+  LP_CUDA(cudaMemcpyAsync(&status, c->dStatus, 4, cudaMemcpyDeviceToHost, c->stream));
   LP_CUDA(cudaStreamSynchronize(c->stream));
+  if (status & lp::ST_TIMEOUT) return fail(c, LP_ERR_TIMEOUT, "device wait timed out in the power step");
   return LP_OK;
 }
 
@@ -1222,7 +1265,8 @@ lp_status lp_eta(lp_ctx* c, double* eta, double* norms) {
   st = run();
   release();
   if (st) return st;
-  if (status & lp::ST_TIMEOUT) return fail(c, LP_ERR_TIMEOUT, "device wait timed out");
+  if (status & lp::ST_TIMEOUT)  // first: a wait that gave up leaves the later steps garbage
+    return fail(c, LP_ERR_TIMEOUT, "device wait timed out");
   double worst = 0.0;
   for (int i = 0; i <= m; ++i)
     if (!std::isfinite(out[i])) return fail(c, LP_ERR_NUMERIC, "non-finite matrix norm");

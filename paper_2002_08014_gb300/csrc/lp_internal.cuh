@@ -86,12 +86,14 @@ struct TcsPlan {
   int ring1 = 0;       // rank 1 ring units
   int nd2 = 0;         // rank 1 Y-slice buffers in tensor memory
   uint32_t tmem_cols1 = 0;
+  long long stall = 0;  // test hook (lp_tuning::test_stall_cycles)
   alignas(64) unsigned char tmap[2][128];  // CUtensorMaps of the planes
 };
 // Tuning of the streaming kernel (lp_tuning without the C names); zeros are defaults.
 struct TcsTuning {
   int ring_units = 0, lag_units = 0, prefetch_units = 0, cache_hints = 0, slice_cols = 0;
   int kernel = 0;  // LP_KERNEL_* of lp_tuning
+  long long test_stall_cycles = 0;  // lp_tuning::test_stall_cycles
 };
 // Fills the geometry for (d, k, planes).  False when the shape has no streaming kernel.
 bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan* p);

@@ -71,7 +71,8 @@ enum PairBar {
   R1_D2EMPTY = 13,   // [2] rank 1: epilogue (4 warps) -> MMA issuers, Y slice read out
   B_EPI = 15,        // the 128 epilogue threads (bounded barrier)
   B_DONE = 16,       // teardown: every MMA retired
-  B_RING0 = 17       // FULL[s] = B_RING0 + s, EMPTY[s] = B_RING0 + kMaxRing + s
+  B_NEVER = 17,      // completed by nothing: the test hook's wait (LP test_stall_cycles)
+  B_RING0 = 18       // FULL[s] = B_RING0 + s, EMPTY[s] = B_RING0 + kMaxRing + s
 };
 constexpr int kNumBars = B_RING0 + 2 * kMaxRing;
 
@@ -89,6 +90,7 @@ struct PairArgs {
   int nd2;    // rank 1 Y-slice buffers in TMEM (1 or 2)
   int hints;  // 1: rank 0 loads evict_last, rank 1 loads evict_first
   int prefetch;  // rank 0: units brought into L2 this far ahead of their load (0: none)
+  long long stall;  // test hook: > 0 makes rank 0's producer wait this many cycles on B_NEVER
   uint32_t off_Z, off_stage, off_bar, tmem0, tmem1;
 };
 
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     mbar_init(&bar[R0_ZDRAIN], HE);
     mbar_init(&bar[B_EPI], 128);
     mbar_init(&bar[B_DONE], kIssuers);
+    mbar_init(&bar[B_NEVER], 1);
     for (int s = 0; s < kMaxRing; ++s) {
       mbar_init(&bar[B_RING0 + s], 1);
       mbar_init(&bar[B_RING0 + kMaxRing + s], 1);
@@ -167,8 +170,11 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
+  // A CTA that gives up also raises its partner's flag (both CTAs live until the
+  // teardown's cluster barrier), so the partner stops at its next wait.
   auto give_up = [&]() {
     *abort_flag = 1;
+    st_cluster_u32(mapa(su32(const_cast<int*>(abort_flag)), rank ^ 1u), 1u);
     atomicOr(a.status, ST_TIMEOUT);
   };
   auto wait = [&](int id, uint32_t parity, bool cluster_scope) -> bool {
@@ -200,6 +206,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   // the unit PF places ahead into L2 first.  pcnt[h] counts the units dealt to
   // issuer h, fills[s] the fills of slot s.  Returns false after an abort.
   uint32_t pcnt[kIssuers] = {0u, 0u, 0u, 0u};
+  uint32_t issued_total = 0;
   uint32_t fills[kMaxRing] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
   auto produce = [&](int s0, int s1, uint64_t policy, int PF) -> bool {
     for (int s = s0; s < s1; ++s) {
@@ -221,6 +228,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
           pcnt[hh] = k + 1;
           ++fills[slot];
           mbar_expect_tx(&bar[B_RING0 + slot], kUnitBytes);
+          issued_total += 1;
           const int b = u / PL, pl = u % PL;
           const int row = static_cast<int>(sg.row0) + t * kBM;
           const CUtensorMap* map = pl ? &map1 : &map0;
@@ -228,6 +236,17 @@ __global__ void __launch_bounds__(kPairThreads, 1)
             const uint32_t dst = su32(sRing + slot * kUnitBytes + j * kChunkBytes);
             if (a.hints) tma_load_2d_hint(dst, map, 64 * (2 * b + j), row, &bar[B_RING0 + slot], policy);
             else tma_load_2d(dst, map, 64 * (2 * b + j), row, &bar[B_RING0 + slot]);
+          }
+          // Test hook: after rank 0's first ring fill (copies in flight, MMAs started),
+          // a wait that nothing can complete runs out its short limit and aborts.
+          if (a.stall > 0 && rank == 0 && issued_total == static_cast<uint32_t>(R)) {
+            const long long t0 = clock64();
+            while (!mbar_try(su32(&bar[B_NEVER]), 0)) {
+              if (clock64() - t0 > a.stall) {
+                give_up();
+                return false;
+              }
+            }
           }
         }
     }
@@ -571,6 +590,7 @@ bool pair_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan
   p->ring1 = ring1;
   p->lag = 0;
   p->prefetch = tune.prefetch_units > 0 ? tune.prefetch_units : 0;
+  p->stall = tune.test_stall_cycles;
   p->hints = 1;  // rank 0 evict_last, rank 1 evict_first (measured best for the two-pass pattern)
   // layout: ring region (rank 1 uses it all), Z (rank 0), W staging / W buffers, barriers
   const uint32_t ring_region = static_cast<uint32_t>(ring1 > ring0 ? ring1 : ring0) * kUnitBytes;
@@ -610,6 +630,7 @@ cudaError_t launch_step_pair(const TcsPlan& p, const Segment* segs, const int* s
   a.nd2 = p.nd2;
   a.hints = p.hints;
   a.prefetch = p.prefetch;
+  a.stall = p.stall;
   a.off_Z = p.off_B1;
   a.off_stage = p.off_B2;
   a.off_bar = p.off_bar;

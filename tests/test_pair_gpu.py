@@ -124,3 +124,27 @@ def test_pair_kernel_is_deterministic_for_every_ring_depth(gpu_lib):
             assert st["path"] == TC_PAIR
             assert np.array_equal(Z1, Z2), ring
             assert O.subspace_dist(Z1, ref) < TC_SOLVE_TOL, ring
+
+
+def test_pair_kernel_timeout_reports_and_the_context_recovers(gpu_lib):
+    """Failure detection without a GPU fault: the test hook makes rank 0's
+    producer wait, after its first ring fill, on a barrier that nothing
+    completes, with a limit of 200,000 cycles.  The wait runs out, the kernel
+    raises both ranks' abort flags, drains its copies and MMAs and returns; the
+    solve reports LP_ERR_TIMEOUT, and the next solve on the same context (hook
+    off) matches the oracle."""
+    sizes = [256, 256]              # 4 tiles: 4 CTA pairs of 8 ring units each
+    d, k = 1024, 16
+    stored, exact, _ = _parts(sizes, d, 9, "bf16")
+    y0 = np.random.default_rng(10).standard_normal((d, k))
+    sched = [2, 1]
+    ref = O.localpower(exact, k, sched, "sign", y0)["Z"]
+    with B.LocalPower(stored, dtype="bf16") as lp:
+        B.lp_set_tuning(lp.ctx, kernel="pair", test_stall_cycles=200_000)
+        with pytest.raises(B.LPError) as e:
+            lp.solve(k, sched, "sign", y0)
+        assert e.value.status == B.LP_ERR_TIMEOUT
+        B.lp_set_tuning(lp.ctx, kernel="pair")
+        Z, _, st = lp.solve(k, sched, "sign", y0)
+        assert st["path"] == TC_PAIR
+    assert O.subspace_dist(Z, ref) < TC_SOLVE_TOL

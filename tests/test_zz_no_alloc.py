@@ -20,10 +20,12 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def test_static_scratch_step_matches_context_step_twice(gpu_lib):
+@pytest.mark.parametrize("sizes,d,k", [
+    ([700, 333, 1000, 59], 256, 16),
+    ([5000, 3333, 4100, 777], 1024, 16),   # the d = 1,024 pipelined kernel (bulk copies on bounded waits)
+])
+def test_static_scratch_step_matches_context_step_twice(gpu_lib, sizes, d, k):
     torch = pytest.importorskip("torch")
-    sizes = [700, 333, 1000, 59]
-    d, k = 256, 16
     A = synth.spiked_rows(sum(sizes), d, 4.0 * 0.8 ** np.arange(1, 9), 0.3, 77, threads=4)
     parts = synth.split_rows(A, sizes)
     dev = torch.device("cuda", 0)
@@ -40,6 +42,7 @@ def test_static_scratch_step_matches_context_step_twice(gpu_lib):
                 B.lp_power_step_static(A_dev, sizes, k, z_dev, y_dev, stream=stream)
             stream.synchronize()
             Y = y_dev.cpu().numpy()
+            assert np.isfinite(Y).all()   # a wait that gave up would have set y to NaN
             for i in range(len(sizes)):
                 assert _rel(Y[i], ref[i]) < 2e-6, (call, i, _rel(Y[i], ref[i]))
 
