@@ -189,7 +189,8 @@ def run_reference(args):
 # columns, lag); other configurations report traffic as unknown.
 DRAM_RATIO = {(0, 0, 0, 0, 0): 1081.1 / 1073.7,    # SIMT FP32, Z_i in TMEM (n = 262,144)
               (2, 1, 1, 0, 1): 2094.9 / 2048.0,    # streaming tcgen05, BF16, as autotuned (n = 1,000,000)
-              (2, 2, 1, 512, 1): 4496.9 / 4096.0}  # streaming tcgen05, hi/lo planes, as autotuned (n = 1,000,000)
+              (2, 2, 1, 512, 1): 4496.9 / 4096.0,  # streaming tcgen05, hi/lo planes, as autotuned (n = 1,000,000)
+              (3, 2, 0, 0, 0): 2120.4 / 2048.0}    # pass-split pair tcgen05, hi/lo planes (n = 500,000)
 
 
 def _traffic(path, planes, tuning, launch_bytes, d=1024, k=16):

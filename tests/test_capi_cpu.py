@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2002_08014_gb300 import binding, build
@@ -48,3 +49,16 @@ def test_no_gpu_is_a_loud_error_not_a_fallback():
     with pytest.raises(binding.LPError) as e:
         binding.lp_create(0)
     assert e.value.status == binding.LP_ERR_CUDA
+
+
+def test_seeded_start_generator_follows_splitmix64():
+    """The test-side generator behind lp_solve_seeded's start block: SplitMix64's
+    published first outputs for state 0, and Box-Muller draws with mean ~0 and
+    variance ~1."""
+    from tests.seeded_start import seeded_start, splitmix64_at
+    assert splitmix64_at(0, 0) == 0xE220A8397B1DCDAF
+    assert splitmix64_at(0, 1) == 0x6E789E6AA1B965F4
+    y = seeded_start(12345, 200, 50)
+    assert abs(y.mean()) < 0.05 and abs(y.var() - 1.0) < 0.05
+    assert np.array_equal(y, seeded_start(12345, 200, 50))
+    assert not np.array_equal(y, seeded_start(12346, 200, 50))

@@ -518,3 +518,22 @@ def test_trace_and_residual_error_match_oracle(gpu_lib, agg):
         else:
             assert entry["rho"] > 1e-4          # the local bases really differ
             assert abs(rho[t] - entry["rho"]) <= 1e-4 * entry["rho"] + 1e-7, (t, rho[t], entry["rho"])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_seeded_solve_matches_oracle_from_the_same_start(gpu_lib, dtype):
+    """lp_solve_seeded draws Y_0 itself (SplitMix64 + Box-Muller); the oracle runs
+    from the start block the test side generates from the same definition, and
+    lp_solve given that block gives the same result as the seeded call."""
+    from tests.seeded_start import seeded_start
+    sizes = [700, 900, 650]
+    stored, exact, _ = _parts(sizes, 160, 81, dtype)
+    seed, k, sched = 2002_08014, 8, [4, 2, 1, 1]
+    Y0 = seeded_start(seed, 160, k)
+    ref = O.localpower(exact, k, sched, "sign", Y0)["Z"]
+    with B.LocalPower(stored, dtype=dtype) as lp:
+        B.lp_solve_seeded(lp.ctx, k, sched, "sign", seed)
+        Zs, _, _ = lp.result(k)
+        Zg, _, _ = lp.solve(k, sched, "sign", Y0)
+    assert O.subspace_dist(Zs, ref) < (1e-6 if dtype == "f32" else TC_SOLVE_TOL)
+    assert O.subspace_dist(Zs, Zg) < 1e-9
