@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(OUT_DIR, LIB_NAME)
 
 SOURCES = ["lp_capi.cu", "lp_server.cu", "step_simt.cu", "step_tc.cu", "step_tcs.cu", "small_kernels.cu",
            "step_static.cu", "eta.cu", "step_simt_tmem.cu",
-           "step_pair.cu"]
+           "step_pair.cu", "step_tcs8.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
           "-I", INCLUDE, "-I", CSRC]

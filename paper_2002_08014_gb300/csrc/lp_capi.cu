@@ -39,6 +39,7 @@ struct lp_ctx {
   void* dA = nullptr;
   size_t dA_bytes = 0;
   float* dScales = nullptr;
+  float smax2 = 1.f;  // FP8: the largest squared row scale (the tensor-core kernel's W scale)
   int base = 0;
 
   // step-kernel schedule
@@ -375,6 +376,9 @@ lp_status launch_step(lp_ctx* c, int K, const float* Z, int64_t z_stride, bool t
   if (c->path == PATH_TCS && c->tcs_cur->pair)
     e = lp::launch_step_pair(*c->tcs_cur, c->dSegsTcs, c->dSegPtrTcs, Z, z_stride, c->dP, static_cast<int>(c->d),
                              c->dStatus, c->stream);
+  else if (c->path == PATH_TCS && c->tcs_cur->fp8)
+    e = lp::launch_step_tcs8(*c->tcs_cur, c->dSegsTcs, c->dSegPtrTcs, Z, z_stride, c->dP, static_cast<int>(c->d),
+                             c->dScales, c->smax2, c->dStatus, c->stream);
   else if (c->path == PATH_TCS)
     e = lp::launch_step_tcs(*c->tcs_cur, c->dSegsTcs, c->dSegPtrTcs, Z, z_stride, c->dP, static_cast<int>(c->d),
                             c->dStatus, c->stream);
@@ -635,6 +639,13 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
       LP_CUDA(cudaMemcpyAsync(c->dScales + c->row_off[i], row_scales[i], size_t(rows[i]) * 4, kind, c->stream));
   }
   LP_CUDA(cudaStreamSynchronize(c->stream));
+  if (dtype == LP_FP8_E4M3) {  // S = max_r s_r^2 for the tensor-core kernel's W scale
+    std::vector<float> sc(static_cast<size_t>(n));
+    LP_CUDA(cudaMemcpy(sc.data(), c->dScales, size_t(n) * 4, cudaMemcpyDeviceToHost));
+    float mx = 0.f;
+    for (float v : sc) mx = std::max(mx, std::fabs(v));
+    c->smax2 = mx > 0.f && std::isfinite(mx * mx) ? mx * mx : 1.f;
+  }
   return LP_OK;
 }
 
@@ -689,7 +700,7 @@ static lp_status validate_k(lp_ctx* c, int k) {
   if (k > smin)
     return fail(c, LP_ERR_INVALID, "k exceeds the smallest partition's row count (its local Y_i would be rank deficient)");
   const int K = kcap_of(k);
-  if (c->planes == 0 && simt_launches(static_cast<int>(c->d), c->ld, c->dtype, K) == 0)
+  if (c->planes == 0 && c->dtype != LP_FP8_E4M3 && simt_launches(static_cast<int>(c->d), c->ld, c->dtype, K) == 0)
     return fail(c, LP_ERR_UNSUPPORTED, "no step kernel for d=" + std::to_string(c->d) + ", k=" + std::to_string(k));
   return LP_OK;
 }
@@ -705,17 +716,27 @@ static lp_status ensure_tcs(lp_ctx* c, int k) {
     c->tcs_state[idx] = -1;
     p = lp::TcsPlan{};
     bool planned = false;
-    const int want = c->tuning.kernel == LP_KERNEL_DEFAULT ? kDefaultTcKernel : c->tuning.kernel;
-    if (want == LP_KERNEL_PAIR) planned = lp::pair_plan(static_cast<int>(c->d), K, c->planes, c->sms, c->tuning, &p);
-    if (!planned && c->tuning.kernel != LP_KERNEL_PAIR) {
-      p = lp::TcsPlan{};
-      planned = lp::tcs_plan(static_cast<int>(c->d), K, c->planes, c->sms, c->tuning, &p);
+    if (c->dtype == LP_FP8_E4M3) {  // one kernel reads FP8 codes on the tensor cores
+      if (c->tuning.kernel == LP_KERNEL_PAIR)
+        return fail(c, LP_ERR_UNSUPPORTED, "the pair kernel does not read FP8 codes");
+      planned = lp::tcs8_plan(static_cast<int>(c->d), K, c->sms, c->tuning, &p);
+      if (!planned)
+        return fail(c, LP_ERR_UNSUPPORTED, "no FP8 tensor-core plan for d=" + std::to_string(c->d));
+      LP_CUDA(lp::tcs8_encode_map(c->dA, c->n, static_cast<int>(c->d), c->ld, &p));
+    } else {
+      const int want = c->tuning.kernel == LP_KERNEL_DEFAULT ? kDefaultTcKernel : c->tuning.kernel;
+      if (want == LP_KERNEL_PAIR)
+        planned = lp::pair_plan(static_cast<int>(c->d), K, c->planes, c->sms, c->tuning, &p);
+      if (!planned && c->tuning.kernel != LP_KERNEL_PAIR) {
+        p = lp::TcsPlan{};
+        planned = lp::tcs_plan(static_cast<int>(c->d), K, c->planes, c->sms, c->tuning, &p);
+      }
+      if (!planned)
+        return fail(c, LP_ERR_UNSUPPORTED, "no streaming tensor-core plan for d=" + std::to_string(c->d));
+      const uint16_t* hi = static_cast<const uint16_t*>(c->dA);
+      const uint16_t* lo = c->planes == 2 ? hi + size_t(c->n) * c->ld : nullptr;
+      LP_CUDA(lp::tcs_encode_maps(hi, lo, c->n, static_cast<int>(c->d), c->ld, &p));
     }
-    if (!planned)
-      return fail(c, LP_ERR_UNSUPPORTED, "no streaming tensor-core plan for d=" + std::to_string(c->d));
-    const uint16_t* hi = static_cast<const uint16_t*>(c->dA);
-    const uint16_t* lo = c->planes == 2 ? hi + size_t(c->n) * c->ld : nullptr;
-    LP_CUDA(lp::tcs_encode_maps(hi, lo, c->n, static_cast<int>(c->d), c->ld, &p));
     c->tcs_state[idx] = 1;
   }
   if (c->tcs_state[idx] < 0)
@@ -755,6 +776,12 @@ static lp_status ensure_tcs(lp_ctx* c, int k) {
 // other dtypes use the SIMT FP32 kernel.
 static lp_status select_path(lp_ctx* c, int k, unsigned flags) {
   c->path = PATH_SIMT;
+  if (c->dtype == LP_FP8_E4M3 && !(flags & LP_FLAG_SIMT)) {
+    const lp_status st = ensure_tcs(c, k);
+    if (st == LP_OK) c->path = PATH_TCS;
+    else if (st != LP_ERR_UNSUPPORTED || c->tuning.kernel != LP_KERNEL_DEFAULT) return st;
+    c->err.clear();
+  }
   if (c->planes > 0 && !(flags & LP_FLAG_SIMT)) {
     const bool resident = ((flags & LP_FLAG_TC_RESIDENT) || c->prefer_resident) && c->dtype == LP_BF16;
     if (!resident) {
@@ -900,6 +927,17 @@ lp_status lp_autotune(lp_ctx* c, int k, lp_tuning* chosen, int* path_out, double
     bool resident;
   };
   std::vector<Cand> cands;
+  if (c->dtype == LP_FP8_E4M3) {
+    for (int slice : {0, 256})
+      for (int lag : {2, 4}) {
+        Cand cd;
+        cd.t.kernel = LP_KERNEL_STREAM;
+        cd.t.lag_units = lag;
+        cd.t.slice_cols = slice;
+        cd.resident = false;
+        cands.push_back(cd);
+      }
+  }
   if (c->planes > 0) {
     {
       Cand cd;
@@ -1211,7 +1249,7 @@ lp_status lp_eta(lp_ctx* c, double* eta, double* norms) {
   // orthonormalisation follows, so partitions with fewer rows than kb are fine.
   const int K = c->Kcap > 0 ? c->Kcap : kcap_of(std::min(16, d));
   const int kb = std::min(K, d);
-  if (c->planes == 0 && simt_launches(d, c->ld, c->dtype, K) == 0)
+  if (c->planes == 0 && c->dtype != LP_FP8_E4M3 && simt_launches(d, c->ld, c->dtype, K) == 0)
     return fail(c, LP_ERR_UNSUPPORTED, "no step kernel for d=" + std::to_string(d));
   lp_status st;
   if ((st = select_path(c, kb, 0))) return st;

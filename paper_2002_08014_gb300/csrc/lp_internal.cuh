@@ -87,6 +87,10 @@ struct TcsPlan {
   int nd2 = 0;         // rank 1 Y-slice buffers in tensor memory
   uint32_t tmem_cols1 = 0;
   long long stall = 0;  // test hook (lp_tuning::test_stall_cycles)
+  // FP8-E4M3 streaming kernel (step_tcs8.cu): codes staged by TMA, widened to FP16
+  int fp8 = 0;         // 1: this plan is for step_tcs8_kernel
+  int stage = 0;       // staging ring units (16 KB of codes each)
+  uint32_t off_stage = 0;
   alignas(64) unsigned char tmap[2][128];  // CUtensorMaps of the planes
 };
 // Tuning of the streaming kernel (lp_tuning without the C names); zeros are defaults.
@@ -105,6 +109,13 @@ cudaError_t launch_step_tcs(const TcsPlan& p, const Segment* segs, const int* se
 // the two CTAs of a cluster.  False when the shape has no plan (d > 1024 at
 // k > 16, d > 2048, or a ring under two units).
 bool pair_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan* p);
+// FP8-E4M3 codes with FP32 row scales on the tensor cores (streaming form; the
+// codes are widened to FP16 in shared memory).  False when the shape has no plan.
+bool tcs8_plan(int d, int k, int sms, const TcsTuning& tune, TcsPlan* p);
+cudaError_t tcs8_encode_map(const void* codes, int64_t n, int d, int64_t ld, TcsPlan* p);
+cudaError_t launch_step_tcs8(const TcsPlan& p, const Segment* segs, const int* seg_ptr, const float* Z,
+                             int64_t z_stride, float* P, int d, const float* scales, float smax2, int* status,
+                             cudaStream_t s);
 cudaError_t launch_step_pair(const TcsPlan& p, const Segment* segs, const int* seg_ptr, const float* Z,
                              int64_t z_stride, float* P, int d, int* status, cudaStream_t s);
 // FP32 rows (pitch src_ld) -> hi = RNE_bf16(a), lo = RNE_bf16(a - hi) planes (pitch ld,

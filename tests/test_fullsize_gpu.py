@@ -84,16 +84,25 @@ def test_fp32_workload_whole_solve_matches_oracle(gpu_lib, fp32_workload, agg):
         assert dist < FP32_SOLVE_TOL, (dtype, dist)
 
 
-def test_precision_workload_subset_whole_solve(gpu_lib):
+@pytest.mark.parametrize("dtype", ["bf16", "e4m3"])
+def test_precision_workload_subset_whole_solve(gpu_lib, dtype):
     A, _, Y0 = synth.make_config_data("lowprec", n=8 * 31_250, m=8, threads=16)
     sizes = [31_250] * 8
-    bits = [synth.f32_to_bf16_bits(p) for p in synth.split_rows(A, sizes)]
+    parts = synth.split_rows(A, sizes)
     del A
+    if dtype == "bf16":
+        stored = [synth.f32_to_bf16_bits(p) for p in parts]
+        exact, scales = [("bf16", b) for b in stored], None
+    else:
+        stored, scales = map(list, zip(*[synth.f32_to_e4m3_rowscaled(p) for p in parts]))
+        exact = [("e4m3", c, s) for c, s in zip(stored, scales)]
+    del parts
     sched = synth.config_schedule("lowprec")        # p = 4 x 30, then 3 rounds at p = 1
-    ref = O.localpower([("bf16", b) for b in bits], 32, sched, "sign", Y0)["Z"]
-    with B.LocalPower(bits, dtype="bf16") as lp:
+    ref = O.localpower(exact, 32, sched, "sign", Y0)["Z"]
+    with B.LocalPower(stored, dtype=dtype, row_scales=scales) as lp:
         B.lp_autotune(lp.ctx, 32)
         Z, _, st = lp.solve(32, sched[:30], "sign", Y0, refine_rounds=3)
     dist = O.subspace_dist(Z, ref)
-    print(f"precision workload, 8 of 128 partitions: dist to the oracle's solve {dist:.3e} (path {st['path']})")
+    print(f"precision workload ({dtype}), 8 of 128 partitions: dist to the oracle's solve {dist:.3e} "
+          f"(path {st['path']})")
     assert dist < TC_SOLVE_TOL, dist

@@ -77,7 +77,7 @@ def test_power_step_matches_oracle(gpu_lib, dtype, sizes, d, k):
     stored, exact, scales = _parts(sizes, d, 100 + d + k, dtype)
     rng = np.random.default_rng(1)
     Z = O.orth(rng.standard_normal((d, k)))
-    tol = TC_STEP_TOL if dtype in ("bf16", "f32_bf16x2") else 2e-6
+    tol = TC_STEP_TOL if dtype in ("bf16", "f32_bf16x2", "e4m3") else 2e-6
     with B.LocalPower(stored, dtype=dtype, row_scales=scales) as lp:
         Y = lp.power_step(k, Z, shared=True)
         for i, P in enumerate(exact):
@@ -183,7 +183,7 @@ def test_fp32_workload_shape_decay_schedule(gpu_lib, agg):
 
 @pytest.mark.parametrize("dtype,flags,path", [
     ("bf16", 0, TC_PAIR), ("bf16", B.LP_FLAG_TC_RESIDENT, TC_RESIDENT), ("bf16", B.LP_FLAG_SIMT, SIMT),
-    ("e4m3", 0, SIMT), ("f32_bf16x2", 0, TC_PAIR)])
+    ("e4m3", 0, TC_STREAM), ("e4m3", B.LP_FLAG_SIMT, SIMT), ("f32_bf16x2", 0, TC_PAIR)])
 def test_reduced_precision_storage_end_to_end(gpu_lib, dtype, flags, path):
     """BF16 / FP8-E4M3 / split-plane stored A: the oracle runs on the decoded
     stored values.  BF16 and split planes run on the tensor cores (the pass-split
