@@ -89,6 +89,7 @@ struct TcsPlan {
   long long stall = 0;  // test hook (lp_tuning::test_stall_cycles)
   // FP8-E4M3 streaming kernel (step_tcs8.cu): codes staged by TMA, widened to FP16
   int fp8 = 0;         // 1: this plan is for step_tcs8_kernel
+  int issuers = 1;     // streaming kernels: MMA-issuing threads (own partial D1 and ring slots each)
   int stage = 0;       // staging ring units (16 KB of codes each)
   uint32_t off_stage = 0;
   alignas(64) unsigned char tmap[2][128];  // CUtensorMaps of the planes

@@ -20,9 +20,13 @@
 // hi/lo split keeps ~16 significant bits) and W split the same way, the
 // products carry FP32-level accuracy on BF16 tensor-core operands.
 //
-// Roles (256 threads): warp 0 lane 0 issues TMA; warp 1 lane 0 issues MMAs;
-// warps 4-7 (one per TMEM lane quadrant) run the epilogue; all warps stage Z
-// at segment starts.  Every wait is bounded: on expiry the kernel records
+// Roles (256 threads): warp 0 lane 0 issues TMA; lane 0 of warps 1 and 2 issue
+// MMAs (two issuers: one thread issues a small-N MMA only every ~55 cycles, and
+// every ~100 when it polls barriers between MMAs), each owning alternate
+// 128-column blocks (both planes of a block) with its own partial D1 (the
+// epilogue sums the two in issuer order) and its own part of the ring, so that
+// it consumes its slots strictly in order; warps 4-7 (one per TMEM lane
+// quadrant) run the epilogue; all warps stage Z at segment starts.  Every wait is bounded: on expiry the kernel records
 // ST_TIMEOUT, stops issuing, waits (bounded) for its own copies in flight,
 // frees tensor memory and returns.
 #include "lp_internal.cuh"
@@ -51,6 +55,7 @@ struct TcsArgs {
   int ncd;   // 64-column chunks in this CTA's slice (even)
   int ring;  // ring units
   int lag;   // first-pass units of tile t+1 issued before the second pass of tile t starts
+  int issuers;  // MMA-issuing threads (1 or 2), each with its own partial D1
   int prefetch;  // first-pass units brought into L2 ahead of their load (0: none)
   int hints;     // 1: first-pass loads evict_last, second-pass loads evict_first
   uint32_t off_B1, off_B2, off_W, off_Wrecv, off_bar, tmem_cols;
@@ -97,18 +102,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int NB = a.ncd / 2;
   const int U = NB * PL;
   const int LAG = a.lag;
+  // Issuer h owns blocks b = h, h + HE, ... and ring slots [ring_base(h),
+  // ring_base(h) + ring_len(h)) (R dealt as evenly as it goes: 3 = 2 + 1).
+  const int HE = a.issuers < NB ? a.issuers : NB;
+  auto ring_len = [&](int hh) { return R / HE + (hh < R % HE ? 1 : 0); };
+  auto ring_base = [&](int hh) { return hh * (R / HE) + (hh < R % HE ? hh : R % HE); };
+  const int h = warp - 1;
+  const bool issuer = lane == 0 && (warp == 1 || warp == 2);
 
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&bar[S_D1FULL0 + s], 1);
+      mbar_init(&bar[S_D1FULL0 + s], HE);
       mbar_init(&bar[S_D1EMPTY0 + s], 4);
       mbar_init(&bar[S_B2FULL0 + s], kBM);
-      mbar_init(&bar[S_B2FREE0 + s], 1);
+      mbar_init(&bar[S_B2FREE0 + s], HE);
     }
-    mbar_init(&bar[S_D2FULL], 1);
+    mbar_init(&bar[S_D2FULL], HE);
     mbar_init(&bar[S_REDFULL], 1);
     mbar_init(&bar[S_WFULL], 1);
-    mbar_init(&bar[S_DONE], 1);
+    mbar_init(&bar[S_DONE], 2);  // both issuer threads commit (an idle one at once)
     mbar_init(&bar[S_EPI], 128);  // barrier of the four epilogue warps (bounded waits)
     for (int s = 0; s < R; ++s) {
       mbar_init(&bar[S_RING0 + s], 1);
@@ -152,7 +164,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int sb = a.seg_ptr[cluster_id], se = a.seg_ptr[cluster_id + 1];
   uint32_t T = 0;  // tiles before this segment (same in every CTA of the cluster)
   uint32_t epi_phase = 0;  // uses of the epilogue barrier so far (epilogue threads)
-  uint32_t G = 0;  // ring units before this segment
+  uint32_t pcnt[2] = {0u, 0u};  // producer: units dealt to each issuer so far
+  uint32_t fills[kMaxRing] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};  // producer: fills of each slot
+  uint32_t c_own = 0;           // issuer: own units consumed so far
   for (int si = sb; si < se; ++si) {
     const Segment sg = a.segs[si];
     const int ntiles = static_cast<int>((sg.row1 - sg.row0 + kBM - 1) / kBM);
@@ -187,10 +201,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < 2; ++j)
           tma_prefetch_2d(pl2 ? &map1 : &map0, c0 + 64 * (2 * b2 + j), static_cast<int>(sg.row0) + t2 * kBM);
       }
-      uint32_t g = G;
       for_each_unit(ntiles, U, LAG, [&](bool second, int t, int u) -> bool {
-        const uint32_t s = g % R;
-        if (!wait(S_RING0 + R + s, ((g / R) + 1) & 1, false)) return false;
+        // the next slot of the issuer that consumes this unit
+        const int hh = (u / PL) % HE;
+        const uint32_t k = pcnt[hh], RH = static_cast<uint32_t>(ring_len(hh));
+        const uint32_t s = static_cast<uint32_t>(ring_base(hh)) + k % RH;
+        if (!wait(S_RING0 + R + s, ((k / RH) + 1) & 1, false)) return false;
+        pcnt[hh] = k + 1;
+        ++fills[s];
         mbar_expect_tx(&bar[S_RING0 + s], kUnitBytes);
         const int b = u / PL, pl = u % PL;
         const int row = static_cast<int>(sg.row0) + t * kBM;
@@ -210,24 +228,29 @@ __global__ void __launch_bounds__(kThreads, 1)
               tma_prefetch_2d(pl2 ? &map1 : &map0, c0 + 64 * (2 * b2 + j), static_cast<int>(sg.row0) + t2 * kBM);
           }
         }
-        ++g;
         return true;
       });
-      // Copies still in flight (only after an abort) land before the CTA exits.
-      const uint32_t g_end = g;
-      for (uint32_t q = g_end > static_cast<uint32_t>(R) ? g_end - R : 0; q < g_end; ++q) {
-        const uint32_t addr = su32(&bar[S_RING0 + q % R]);
+      // Copies still in flight (only after an abort) land before the CTA exits:
+      // the last fill of every slot (earlier fills were waited for by then).
+      for (int q = 0; q < R; ++q) {
+        if (fills[q] == 0) continue;
+        const uint32_t addr = su32(&bar[S_RING0 + q]);
         const long long t0 = clock64();
-        while (!mbar_try(addr, (q / R) & 1) && clock64() - t0 < kTimeoutCycles) {
+        while (!mbar_try(addr, (fills[q] - 1) & 1) && clock64() - t0 < kTimeoutCycles) {
         }
       }
-    } else if (warp == 1 && lane == 0) {
-      // ------------------------------------------------------------ MMA issuer
-      uint32_t g = G;
+    } else if (issuer && h < HE) {
+      // ------------------------------------------------------------ MMA issuers
+      // issuer h: units of blocks b = h, h + HE, ... in the shared unit order
+      const int b_last = h + ((NB - 1 - h) / HE) * HE;
+      const int u_first = h * PL, u_last = b_last * PL + PL - 1;
+      const uint32_t RH = static_cast<uint32_t>(ring_len(h)), rb = static_cast<uint32_t>(ring_base(h));
       for_each_unit(ntiles, U, LAG, [&](bool second, int t, int u) -> bool {
-        const uint32_t s = g % R, Tg = T + t, buf = Tg & 1;
-        if (!wait(S_RING0 + s, (g / R) & 1, false)) return false;
-        if (u == 0) {
+        if ((u / PL) % HE != h) return true;
+        const uint32_t s = rb + c_own % RH, Tg = T + t, buf = Tg & 1;
+        if (!wait(S_RING0 + s, (c_own / RH) & 1, false)) return false;
+        ++c_own;
+        if (u == u_first) {
           if (!second && !wait(S_D1EMPTY0 + buf, ((Tg >> 1) + 1) & 1, false)) return false;
           if (second && !wait(S_B2FULL0 + buf, (Tg >> 1) & 1, false)) return false;
         }
@@ -242,10 +265,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kk = 0; kk < 4; ++kk) {
               const uint64_t ad = sdesc(aS + j * kChunkBytes + kk * 32, 16, 1024);
               const uint64_t bd = sdesc(bS + (2 * b + j) * N * 128 + kk * 32, 16, 1024);
-              mma_bf16(tmem + buf * N, ad, bd, idesc1, (u | j | kk) != 0);
+              mma_bf16(tmem + (buf * HE + h) * N, ad, bd, idesc1, (u != u_first || j != 0 || kk != 0) ? 1u : 0u);
             }
           mma_commit(&bar[S_RING0 + R + s]);
-          if (u == U - 1) mma_commit(&bar[S_D1FULL0 + buf]);
+          if (u == u_last) mma_commit(&bar[S_D1FULL0 + buf]);
         } else {
           const uint32_t bS = su32(sB2 + buf * B2BUF);
 #pragma unroll
@@ -253,12 +276,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             // A^T: M = 128 columns (two 64-column chunks, LBO apart), K = 16 rows (two 8-row groups, SBO apart)
             const uint64_t ad = sdesc(aS + kk * 2048, kChunkBytes, 1024);
             const uint64_t bd = sdesc(bS + (kk >> 2) * N * 128 + (kk & 3) * 32, 16, 1024);
-            mma_bf16(tmem + 2 * N + b * N, ad, bd, idesc2, (t == 0 && pl == 0 && kk == 0) ? 0u : 1u);
+            mma_bf16(tmem + 2 * HE * N + b * N, ad, bd, idesc2, (t == 0 && pl == 0 && kk == 0) ? 0u : 1u);
           }
           mma_commit(&bar[S_RING0 + R + s]);
-          if (u == U - 1) mma_commit(&bar[S_B2FREE0 + buf]);
+          if (u == u_last) mma_commit(&bar[S_B2FREE0 + buf]);
         }
-        ++g;
         return true;
       });
       mma_commit(&bar[S_D2FULL]);
@@ -277,16 +299,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t Tg = T + t, buf = Tg & 1;
         if (!(ok = wait(S_D1FULL0 + buf, (Tg >> 1) & 1, false))) break;
         tc_fence_after();
+        // W = the issuers' partials, each [hi part | lo part], summed in a fixed order
         float w[K];
 #pragma unroll
-        for (int q = 0; q < N / 16; ++q) {
-          float v[16];
-          tmem_ld16(tmem + lane_base + buf * N + q * 16, v);
+        for (int j = 0; j < K; ++j) w[j] = 0.f;
+        for (int hh = 0; hh < HE; ++hh) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int col = q * 16 + i;
-            if (col < K) w[col] = v[i];
-            else w[col - K] += v[i];
+          for (int q = 0; q < N / 16; ++q) {
+            float v[16];
+            tmem_ld16(tmem + lane_base + (buf * HE + hh) * N + q * 16, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int col = q * 16 + i;
+              w[col < K ? col : col - K] += v[i];
+            }
           }
         }
         tc_fence_before();
@@ -374,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int q = 0; q < N / 16; ++q) {
             float v[16];
-            tmem_ld16(tmem + lane_base + 2 * N + b * N + q * 16, v);
+            tmem_ld16(tmem + lane_base + 2 * HE * N + b * N + q * 16, v);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
               const int col = q * 16 + i;
@@ -393,11 +419,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     T += ntiles;
-    G += 2u * static_cast<uint32_t>(ntiles) * static_cast<uint32_t>(U);
   }
 
   // ---- teardown: all MMAs retired, no remote traffic in flight, then free TMEM
-  if (warp == 1 && lane == 0) mma_commit(&bar[S_DONE]);
+  if (issuer) mma_commit(&bar[S_DONE]);
   __syncthreads();
   if (warp == 0) {
     const uint32_t addr = su32(&bar[S_DONE]);
@@ -516,7 +541,12 @@ bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan*
   p->off_Wrecv = p->off_W + W;
   p->off_bar = p->off_Wrecv + W;
   p->smem = p->off_bar + (S_RING0 + 2 * ring) * 8 + 16 + 1024;
-  const uint32_t used = static_cast<uint32_t>(2 * N + (ncd / 2) * N);
+  // two issuers (two partial D1 per buffer) when tensor memory holds them
+  const int NBp = ncd / 2;
+  // (independent of the ring depth, which must only reorder loads: any ring of two
+  // or more units deals each issuer at least one slot)
+  p->issuers = (4 * N + NBp * N <= 512 && NBp >= 2) ? 2 : 1;
+  const uint32_t used = static_cast<uint32_t>(2 * p->issuers * N + NBp * N);
   uint32_t cols = 32;
   while (cols < used) cols *= 2;
   if (cols > 512) return false;
@@ -567,6 +597,7 @@ cudaError_t launch_step_tcs(const TcsPlan& p, const Segment* segs, const int* se
   a.ncd = p.ncd;
   a.ring = p.ring;
   a.lag = p.lag;
+  a.issuers = p.issuers;
   a.prefetch = p.prefetch;
   a.hints = p.hints;
   a.off_B1 = p.off_B1;
