@@ -263,12 +263,19 @@ def run_lowprec(args):
     hbm_peak, _, peak_src = _peaks()
     lpb = B.LocalPower(bits, dtype="bf16", device=local, stream=stream)
     choice = B.lp_autotune(lpb.ctx, k)
+    # the workload's arithmetic: FP32 accumulation, the k x k work in FP64 (LP_FLAG_KXK_FP64)
     for _ in range(args.warmup):
-        lpb.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
+        lpb.submit(k, sched, args.agg, Y0, ritz=True, timing=True, kxk_fp64=True)
         lpb.result(k)
     ms, stats, Z, sig, clk = _timed(torch, dist, world, dev, stream, lpb, k, sched, args.agg, args.steps,
-                                    Clocks(local))
+                                    Clocks(local), kxk_fp64=True)
     s = _summary(world, args.steps, ms, stats, 2, c)
+    # the same solves with the k x k work in FP32, for the cost of the FP64 k x k work
+    for _ in range(max(1, args.warmup // 2)):
+        lpb.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
+        lpb.result(k)
+    ms32, stats32, Z32, _, _ = _timed(torch, dist, world, dev, stream, lpb, k, sched, args.agg, args.steps)
+    s32 = _summary(world, args.steps, ms32, stats32, 2, c)
     lpb.close()
     gbs_k = s["launch_bytes"] / (s["step_ms"] / 1e3) / 1e9
     line = {"metric": METRIC, "value": s["gbs"], "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -281,6 +288,9 @@ def run_lowprec(args):
                          "traffic": None, "launch_ms": s["step_ms"], "peak_source": f"{peak_src} HBM copy bandwidth"}}
     line["orthonormality"] = float(np.abs(Z.T @ Z - np.eye(k)).max())
     line["sigma_top3"] = [float(x) for x in sig[:3]]
+    line["kxk"] = {"precision": "fp64 (Gram/Cholesky of CholQR2, Procrustes SVD, Ritz eigen-solve)",
+                   "fp32_kxk_solves_per_s": s32["solves_per_s"], "fp32_kxk_ms_per_solve": s32["ms_per_solve"],
+                   "fp64_cost_frac": (s["ms_per_solve"] - s32["ms_per_solve"]) / s["ms_per_solve"]}
 
     # the same matrix as FP8-E4M3 codes with one FP32 scale per row (tensor cores: codes widened to FP16)
     fp8 = None
@@ -289,10 +299,10 @@ def run_lowprec(args):
         lp8 = B.LocalPower(list(codes), dtype="e4m3", row_scales=list(scales), device=local, stream=stream)
         choice8 = B.lp_autotune(lp8.ctx, k)
         for _ in range(args.warmup):
-            lp8.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
+            lp8.submit(k, sched, args.agg, Y0, ritz=True, timing=True, kxk_fp64=True)
             lp8.result(k)
         ms8, st8, Z8, sig8, clk8 = _timed(torch, dist, world, dev, stream, lp8, k, sched, args.agg, args.steps,
-                                          Clocks(local))
+                                          Clocks(local), kxk_fp64=True)
         s8 = _summary(world, args.steps, ms8, st8, 1, c)
         lp8.close()
         gbs8 = (s8["launch_bytes"] + 4.0 * c["n"]) / (s8["step_ms"] / 1e3) / 1e9
@@ -317,6 +327,7 @@ def run_lowprec(args):
         Vf, _ = _truth(parts, c)
         line["accuracy"] = {"dist_to_eigh_topk_bf16_problem": oracle.subspace_dist(oracle.orth(Z), Vb),
                             "dist_to_eigh_topk_fp32_problem": oracle.subspace_dist(oracle.orth(Z), Vf),
+                            "dist_to_eigh_topk_bf16_problem_fp32_kxk": oracle.subspace_dist(oracle.orth(Z32), Vb),
                             "quantisation_shift": oracle.subspace_dist(Vb, Vf),
                             "host_fp64_seconds": time.perf_counter() - t0}
         if fp8 and "error" not in fp8:
@@ -722,7 +733,7 @@ def run_kernels(args):
     print(json.dumps({"workload": "kernels", "n": n, "d": d, "k": k, "m": m, "results": out}))
 
 
-def _timed(torch, dist, world, dev, stream, lp, k, sched, agg, steps, clocks=None):
+def _timed(torch, dist, world, dev, stream, lp, k, sched, agg, steps, clocks=None, kxk_fp64=False):
     """K back-to-back solves on the library's stream, bracketed by a barrier and a
     device synchronize; CUDA events on that stream.  Returns (ms, stats, Z, sigma, clocks)."""
     def barrier():
@@ -737,7 +748,7 @@ def _timed(torch, dist, world, dev, stream, lp, k, sched, agg, steps, clocks=Non
     ev0.record(stream)
     stats, Z, sig = [], None, None
     for _ in range(steps):
-        lp.submit(k, sched, agg, _timed.y0, ritz=True, timing=True)
+        lp.submit(k, sched, agg, _timed.y0, ritz=True, timing=True, kxk_fp64=kxk_fp64)
         Z, sig, st = lp.result(k)
         stats.append(st)
     ev1.record(stream)

@@ -74,6 +74,13 @@ typedef enum lp_ptr_space { LP_HOST = 0, LP_DEVICE = 1 } lp_ptr_space;
 #define LP_FLAG_TC_RESIDENT 8u  /* BF16 data: use the tensor-core step that keeps each tile in shared
                                  * memory for both contractions (cluster-split d) instead of the
                                  * streaming one; ignored for other dtypes */
+#define LP_FLAG_KXK_FP64 64u /* the k x k work in FP64: the Gram matrix of CholQR2 (each FP32
+                              * product summed in FP64) and its Cholesky factor, the k x k SVD
+                              * of the Procrustes alignment (eq. (3)) and the eigen-solve of
+                              * the final Rayleigh-Ritz step.  Without it these are FP32, with
+                              * an FP64 Cholesky only where an FP32 pivot is too small; the
+                              * d x k work (steps, triangular solves, averaging) is FP32
+                              * either way.                                                   */
 
 typedef struct lp_ctx lp_ctx;
 
@@ -407,19 +414,21 @@ lp_status lp_power_step(lp_ctx* ctx, int k, const double* z, int z_shared, doubl
  * passes of Gram, Cholesky and triangular solve; eq. (1)'s orth, whose column
  * space is that of a Householder QR).  FP64 row-major in and out (`space`).
  * A block whose Gram matrix is not numerically positive definite yields
- * LP_ERR_NUMERIC.
+ * LP_ERR_NUMERIC.  flags: 0, or LP_FLAG_KXK_FP64 for the FP64 Gram and Cholesky.
  */
-lp_status lp_orth(lp_ctx* ctx, int batch, int64_t d, int k, const double* y, double* z, lp_ptr_space space);
+lp_status lp_orth(lp_ctx* ctx, int batch, int64_t d, int k, const double* y, double* z, lp_ptr_space space,
+                  unsigned flags);
 
 /*
  * lp_align_aggregate: Y = sum_i w_i Y_i D_i with D_b = I and D_i from `agg`
  * computed between Z_i and Z_b (eqs. (3)-(4); Alg. 1 aggregation).
  *   ys, zs   m consecutive d x k FP64 blocks each; w: m weights; base: b.
  *   y_out    d x k FP64; d_out (may be NULL) m consecutive k x k FP64 D_i.
+ *   flags    0, or LP_FLAG_KXK_FP64 for the Procrustes SVD in FP64.
  */
 lp_status lp_align_aggregate(lp_ctx* ctx, int m, int64_t d, int k, lp_aggregator agg, int base,
                              const double* w, const double* ys, const double* zs,
-                             double* y_out, double* d_out, lp_ptr_space space);
+                             double* y_out, double* d_out, lp_ptr_space space, unsigned flags);
 
 /* ----------------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this call exists

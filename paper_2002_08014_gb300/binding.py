@@ -19,6 +19,7 @@ LP_F32, LP_BF16, LP_FP8_E4M3, LP_F32_BF16X2 = 0, 1, 2, 3
 LP_AGG_IDENTITY, LP_AGG_SIGN, LP_AGG_OPT = 0, 1, 2
 LP_HOST, LP_DEVICE = 0, 1
 LP_FLAG_RITZ, LP_FLAG_TIMING, LP_FLAG_SIMT, LP_FLAG_TC_RESIDENT, LP_FLAG_NO_GRAPH, LP_FLAG_TRACE = 1, 2, 4, 8, 16, 32
+LP_FLAG_KXK_FP64 = 64
 LP_MAX_K = 32
 
 AGG = {"identity": LP_AGG_IDENTITY, "sign": LP_AGG_SIGN, "opt": LP_AGG_OPT}
@@ -98,8 +99,8 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
     L.lp_last_error.argtypes = [P]
     L.lp_last_error.restype = C.c_char_p
     L.lp_power_step.argtypes = [P, I, P, I, P, I]
-    L.lp_orth.argtypes = [P, I, I64, I, P, P, I]
-    L.lp_align_aggregate.argtypes = [P, I, I64, I, I, I, P, P, P, P, P, I]
+    L.lp_orth.argtypes = [P, I, I64, I, P, P, I, C.c_uint]
+    L.lp_align_aggregate.argtypes = [P, I, I64, I, I, I, P, P, P, P, P, I, C.c_uint]
     L.lp_power_step_static.argtypes = [P, I, C.POINTER(I64), I64, I, P, P, P]
     L.lp_set_tuning.argtypes = [P, C.POINTER(lp_tuning)]
     L.lp_trace.argtypes = [P, P, P]
@@ -298,8 +299,9 @@ def lp_power_step(ctx, k: int, z, z_shared: bool, m: int, d: int, out=None):
     return out
 
 
-def lp_orth(ctx, Y):
-    """Z_b = orth(Y_b) for a (batch, d, k) FP64 array (host) or tensor (device)."""
+def lp_orth(ctx, Y, kxk_fp64: bool = False):
+    """Z_b = orth(Y_b) for a (batch, d, k) FP64 array (host) or tensor (device);
+    kxk_fp64: the Gram and Cholesky in FP64 (LP_FLAG_KXK_FP64)."""
     L = load()
     b, d, k = Y.shape
     yp, sp, keep = _ptr(Y, np.float64)
@@ -309,12 +311,13 @@ def lp_orth(ctx, Y):
     else:
         Z = np.empty((b, d, k), dtype=np.float64)
     zp, _, keep2 = _ptr(Z, np.float64)
-    _check(ctx, L.lp_orth(ctx, int(b), int(d), int(k), yp, zp, sp))
+    _check(ctx, L.lp_orth(ctx, int(b), int(d), int(k), yp, zp, sp, LP_FLAG_KXK_FP64 if kxk_fp64 else 0))
     return Z
 
 
-def lp_align_aggregate(ctx, agg: str, base: int, w, Ys, Zs):
-    """(Y d x k, D (m, k, k)) for host FP64 inputs Ys, Zs of shape (m, d, k)."""
+def lp_align_aggregate(ctx, agg: str, base: int, w, Ys, Zs, kxk_fp64: bool = False):
+    """(Y d x k, D (m, k, k)) for host FP64 inputs Ys, Zs of shape (m, d, k);
+    kxk_fp64: the Procrustes SVD in FP64 (LP_FLAG_KXK_FP64)."""
     L = load()
     m, d, k = Ys.shape
     Ys = np.ascontiguousarray(Ys, dtype=np.float64)
@@ -324,7 +327,8 @@ def lp_align_aggregate(ctx, agg: str, base: int, w, Ys, Zs):
     D = np.empty((m, k, k), dtype=np.float64)
     _check(ctx, L.lp_align_aggregate(ctx, int(m), int(d), int(k), AGG[agg], int(base), C.c_void_p(w.ctypes.data),
                                      C.c_void_p(Ys.ctypes.data), C.c_void_p(Zs.ctypes.data),
-                                     C.c_void_p(Y.ctypes.data), C.c_void_p(D.ctypes.data), LP_HOST))
+                                     C.c_void_p(Y.ctypes.data), C.c_void_p(D.ctypes.data), LP_HOST,
+                                     LP_FLAG_KXK_FP64 if kxk_fp64 else 0))
     return Y, D
 
 
@@ -362,13 +366,17 @@ class LocalPower:
         self.d = int(parts[0].shape[1])
         self.sizes = [int(p.shape[0]) for p in parts]
 
-    def solve(self, k: int, schedule, agg: str, y0, refine_rounds: int = 0, ritz: bool = False, timing: bool = False):
-        flags = (LP_FLAG_RITZ if ritz else 0) | (LP_FLAG_TIMING if timing else 0)
+    def solve(self, k: int, schedule, agg: str, y0, refine_rounds: int = 0, ritz: bool = False, timing: bool = False,
+              kxk_fp64: bool = False):
+        flags = ((LP_FLAG_RITZ if ritz else 0) | (LP_FLAG_TIMING if timing else 0)
+                 | (LP_FLAG_KXK_FP64 if kxk_fp64 else 0))
         lp_solve(self.ctx, k, schedule, agg, y0, refine_rounds, flags)
         return lp_result(self.ctx, self.d, k)
 
-    def submit(self, k: int, schedule, agg: str, y0, refine_rounds: int = 0, ritz: bool = False, timing: bool = False):
-        flags = (LP_FLAG_RITZ if ritz else 0) | (LP_FLAG_TIMING if timing else 0)
+    def submit(self, k: int, schedule, agg: str, y0, refine_rounds: int = 0, ritz: bool = False, timing: bool = False,
+               kxk_fp64: bool = False):
+        flags = ((LP_FLAG_RITZ if ritz else 0) | (LP_FLAG_TIMING if timing else 0)
+                 | (LP_FLAG_KXK_FP64 if kxk_fp64 else 0))
         lp_solve(self.ctx, k, schedule, agg, y0, refine_rounds, flags)
 
     def result(self, k: int):

@@ -814,21 +814,21 @@ static lp_status select_path(lp_ctx* c, int k, unsigned flags) {
 // The launch sequence of one solve (Alg. 1 in rounds, then Ritz or unpack), on
 // the context's stream; lp_solve runs it eagerly or captures it into a graph.
 static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator agg, int refine_rounds,
-                            bool timing, const double* dy0, bool trace) {
+                            bool timing, const double* dy0, bool trace, bool kxk64) {
   const int d = static_cast<int>(c->d);
   const int m = c->m;
   const int K = kcap_of(k);
   lp_status st;
   LP_CUDA(cudaMemsetAsync(c->dStatus, 0, 4, c->stream));
   if ((st = check_launch(c, lp::launch_pack(dy0, c->dY, 1, d, k, K, c->stream), "pack"))) return st;
-  if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream), "orth"))) return st;
+  if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream, kxk64), "orth"))) return st;
 
   const int rounds = T + refine_rounds;
   const int64_t zs = int64_t(d) * K;
   for (int t = 0; t < rounds; ++t) {
     const int p = t < T ? p_schedule[t] : 1;
     for (int j = 0; j < p; ++j) {
-      if (j > 0 && (st = check_launch(c, lp::launch_cholqr2(c->dYl, c->dZl, m, d, k, K, c->dStatus, c->stream),
+      if (j > 0 && (st = check_launch(c, lp::launch_cholqr2(c->dYl, c->dZl, m, d, k, K, c->dStatus, c->stream, kxk64),
                                       "local orth")))
         return st;
       if ((st = launch_step(c, K, j == 0 ? c->dZ : c->dZl, j == 0 ? 0 : zs, timing))) return st;
@@ -842,7 +842,7 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
     if (align) {
       // The last basis each partition multiplied this round is Z_i (orth of its previous Y_i).
       if ((st = check_launch(c, lp::launch_align(c->dZl, zs, c->dZl + zs * c->base, m, d, k, K, c->base, agg, c->dG,
-                                                 c->dStatus, c->stream),
+                                                 c->dStatus, c->stream, kxk64),
                              "align")))
         return st;
     }
@@ -850,7 +850,7 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
                                                    m, d, K, c->dY, c->stream),
                            "aggregate")))
       return st;
-    if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream), "orth")))
+    if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream, kxk64), "orth")))
       return st;
     if (trace) {
       LP_CUDA(cudaMemcpyAsync(c->dTraceZ + size_t(t) * d * K, c->dZ, size_t(d) * K * 4, cudaMemcpyDeviceToDevice,
@@ -877,7 +877,7 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
     // the partials buffer is free again after the reduction: it holds the Ritz scratch
     if (lp::ritz_scratch_bytes(d, K) > state_sizes(c, K).P) return fail(c, LP_ERR_INVALID, "Ritz scratch too small");
     if ((st = check_launch(c, lp::launch_ritz(c->dZ, c->dMZ, d, k, K, double(c->n), c->dZout, c->dSigma,
-                                              reinterpret_cast<double*>(c->dP), c->dStatus, c->stream),
+                                              reinterpret_cast<double*>(c->dP), c->dStatus, c->stream, kxk64),
                            "ritz")))
       return st;
     c->stats.kernel_launches += 2;  // launch_ritz runs three kernels
@@ -1121,7 +1121,8 @@ lp_status lp_solve(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggregator
     }
     std::memset(&c->stats, 0, sizeof(c->stats));
     c->step_ev_used = 0;
-    st = solve_body(c, k, p_schedule, T, agg, refine_rounds, timing, dy0, (flags & LP_FLAG_TRACE) != 0);
+    st = solve_body(c, k, p_schedule, T, agg, refine_rounds, timing, dy0, (flags & LP_FLAG_TRACE) != 0,
+                    (flags & LP_FLAG_KXK_FP64) != 0);
     if (use_graph) {
       cudaGraph_t g = nullptr;
       const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
@@ -1352,7 +1353,8 @@ lp_status to_device(lp_ctx* c, Scratch& s, const double* src, size_t count, lp_p
 
 extern "C" {
 
-lp_status lp_orth(lp_ctx* c, int batch, int64_t d, int k, const double* y, double* z, lp_ptr_space space) {
+lp_status lp_orth(lp_ctx* c, int batch, int64_t d, int k, const double* y, double* z, lp_ptr_space space,
+                  unsigned flags) {
   if (!c) return LP_ERR_INVALID;
   c->err.clear();
   if (batch < 1 || d < 1 || k < 1 || k > LP_MAX_K || k > d || !y || !z)
@@ -1372,7 +1374,8 @@ lp_status lp_orth(lp_ctx* c, int batch, int64_t d, int k, const double* y, doubl
   else if ((st = s.get(&dz, blk * k * 8))) return st;
   LP_CUDA(cudaMemsetAsync(c->dStatus, 0, 4, c->stream));
   if ((st = check_launch(c, lp::launch_pack(dy, Y, batch, static_cast<int>(d), k, K, c->stream), "pack"))) return st;
-  if ((st = check_launch(c, lp::launch_cholqr2(Y, Z, batch, static_cast<int>(d), k, K, c->dStatus, c->stream),
+  if ((st = check_launch(c, lp::launch_cholqr2(Y, Z, batch, static_cast<int>(d), k, K, c->dStatus, c->stream,
+                                               (flags & LP_FLAG_KXK_FP64) != 0),
                          "orth")))
     return st;
   if ((st = check_launch(c, lp::launch_unpack(Z, dz, batch, static_cast<int>(d), k, K, c->stream), "unpack")))
@@ -1386,7 +1389,8 @@ lp_status lp_orth(lp_ctx* c, int batch, int64_t d, int k, const double* y, doubl
 }
 
 lp_status lp_align_aggregate(lp_ctx* c, int m, int64_t d, int k, lp_aggregator agg, int base, const double* w,
-                             const double* ys, const double* zs, double* y_out, double* d_out, lp_ptr_space space) {
+                             const double* ys, const double* zs, double* y_out, double* d_out, lp_ptr_space space,
+                             unsigned flags) {
   if (!c) return LP_ERR_INVALID;
   c->err.clear();
   if (m < 1 || d < 1 || k < 1 || k > LP_MAX_K || k > d || base < 0 || base >= m || !w || !ys || !zs || !y_out)
@@ -1416,7 +1420,8 @@ lp_status lp_align_aggregate(lp_ctx* c, int m, int64_t d, int k, lp_aggregator a
     return st;
   const bool align = agg != LP_AGG_IDENTITY;
   if (align && (st = check_launch(c, lp::launch_align(Zl, int64_t(d) * K, Zl + int64_t(d) * K * base, m, di, k, K, base,
-                                                      agg, G, c->dStatus, c->stream),
+                                                      agg, G, c->dStatus, c->stream,
+                                                      (flags & LP_FLAG_KXK_FP64) != 0),
                                   "align")))
     return st;
   if ((st = check_launch(c, lp::launch_aggregate(Yl, W, align ? G : nullptr, agg == LP_AGG_SIGN ? 1 : 0, m, di, K, Y,
@@ -1460,7 +1465,7 @@ lp_status lp::batch_enqueue(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
   c->step_ev_used = 0;
   LP_CUDA(record_event(c->ev0, c->stream));
   const lp_status st = solve_body(c, k, p_schedule, T, agg, refine_rounds, (flags & LP_FLAG_TIMING) != 0, c->dStage,
-                                  (flags & LP_FLAG_TRACE) != 0);
+                                  (flags & LP_FLAG_TRACE) != 0, (flags & LP_FLAG_KXK_FP64) != 0);
   if (st) return st;
   LP_CUDA(record_event(c->ev1, c->stream));
   *captured = c->stats;

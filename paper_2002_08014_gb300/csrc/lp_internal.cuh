@@ -153,18 +153,21 @@ inline void set_no_context_error(const std::string& msg) { set_no_context_error(
 // slots any partition has) picks how many threads share one output.
 cudaError_t launch_reduce(const float* P, const int* slot_begin, const float* scale, int m, int d, int K,
                           float* Y, cudaStream_t s, int max_slots);
-// Z_b = orth(Y_b) (CholQR2, FP32 data, FP64 k x k factors), batch blocks of d x K.
-cudaError_t launch_cholqr2(const float* Y, float* Z, int batch, int d, int k, int K, int* status, cudaStream_t s);
-// G_i = aligning matrices (K x K, FP32) for agg in {SIGN, OPT}; base gets I.
+// Z_b = orth(Y_b) (CholQR2 on FP32 data), batch blocks of d x K.  kxk_fp64: the k x k
+// Gram and Cholesky in FP64; else FP32 with an FP64 Cholesky when a pivot is too small.
+cudaError_t launch_cholqr2(const float* Y, float* Z, int batch, int d, int k, int K, int* status, cudaStream_t s,
+                           bool kxk_fp64);
+// G_i = aligning matrices (K x K, FP32) for agg in {SIGN, OPT}; base gets I.  kxk_fp64:
+// the k x k Procrustes SVD in FP64, else FP32.
 cudaError_t launch_align(const float* Zl, int64_t z_stride, const float* Zb, int m, int d, int k, int K, int base,
-                         lp_aggregator agg, float* G, int* status, cudaStream_t s);
+                         lp_aggregator agg, float* G, int* status, cudaStream_t s, bool kxk_fp64);
 // Y = sum_i w_i Y_i G_i  (G == nullptr: identity; diag_only: G_i diagonal)
 cudaError_t launch_aggregate(const float* Yl, const float* w, const float* G, int diag_only, int m, int d, int K,
                              float* Y, cudaStream_t s);
-// Ritz: H = Z^T MZ (FP64), eig (FP64 Jacobi), Zout = Z W (FP64), sigma = sqrt(n lambda).
-// Three launches; `scratch` holds ritz_scratch_bytes(d, K) bytes.
+// Ritz: H = Z^T MZ (FP64 sums), eig by Jacobi (FP64 when kxk_fp64, else FP32), Zout = Z W
+// (FP64), sigma = sqrt(n lambda).  Three launches; `scratch` holds ritz_scratch_bytes(d, K) bytes.
 cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, double n, double* Zout, double* sigma,
-                        double* scratch, int* status, cudaStream_t s);
+                        double* scratch, int* status, cudaStream_t s, bool kxk_fp64);
 size_t ritz_scratch_bytes(int d, int K);
 // out[i] = ||Z_i G_i - Z_b||_2 (Def. 3), G_i the aligner (nullptr: none; diag_only: sign-fixing); out[base] = 0.
 cudaError_t launch_rho(const float* Zl, int64_t z_stride, const float* Zb, const float* G, int diag_only, int base,

@@ -6,11 +6,13 @@
 //   ritz       Rayleigh-Ritz on span(Z): ordered basis and sigma_j = sqrt(n lambda_j)
 //   split      FP32 rows -> hi / lo BF16 planes (load time)
 //   rho        residual error of Def. 3 per partition (traced solves)
-// Precision: the d-sized work (Gram, solves, averaging) and the k x k Jacobi
-// SVD / eigen-solves are FP32; the Cholesky factor is FP32 when its pivots allow
-// (else FP64); the Ritz matrix H and the sign-fix inner products that decide D_i
-// are accumulated in FP64.  GB300's FP64 pipe is a small fraction of its FP32
-// pipe, and these k x k steps are serial latency on every round.
+// Precision, by default: the d-sized work (Gram, solves, averaging) and the k x k
+// Jacobi SVD / eigen-solves are FP32; the Cholesky factor is FP32 when its pivots
+// allow (else FP64); the Ritz matrix H and the sign-fix inner products that
+// decide D_i are accumulated in FP64.  GB300's FP64 pipe is a small fraction of
+// its FP32 pipe, and these k x k steps are serial latency on every round.  With
+// LP_FLAG_KXK_FP64 the k x k work is FP64 throughout: the CholQR2 Gram (summed in
+// FP64) and its Cholesky, the Procrustes SVD and the Ritz eigen-solve.
 #include <algorithm>
 #include <cfloat>
 
@@ -125,47 +127,68 @@ __device__ __forceinline__ float warp_sumf(float v) {
   return v;
 }
 
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Thresholds of the Jacobi sweeps per precision: a pair (p, q) is rotated while
+// |c_p . c_q| > tol ||c_p|| ||c_q|| (tol a few units of the type's rounding
+// error times k, so the last sweep only sees rounding noise below it); `tiny`
+// skips pairs whose product underflows; beyond `huge` t = 1 / (2 |zeta|) avoids
+// squaring zeta.
+template <typename T> struct JacobiLimits;
+template <> struct JacobiLimits<float> {
+  static constexpr float tol = 1e-6f, tiny = 1e-35f, huge = 1e15f;
+};
+template <> struct JacobiLimits<double> {
+  static constexpr double tol = 1e-13, tiny = 1e-300, huge = 1e150;
+};
+
 // One-sided (Hestenes) Jacobi on the k x k matrix C (stride K, in shared memory),
-// accumulating the rotations in V, in FP32: on return C's columns are mutually
-// orthogonal, C_in V = C_out, so C_in = U Sigma V^T with sigma_j = ||C_out[:, j]||
-// and U[:, j] = C_out[:, j] / sigma_j.  FP32 because GB300's FP64 pipe is a small
-// fraction of its FP32 pipe and these k x k problems sit on serial critical
-// paths; the aligners and Ritz values it yields stay within 1e-7 of FP64
-// factorisations (CPU simulation on the FP32 workload's spectrum).  Returns false
-// if the sweep limit was hit.
-__device__ bool warp_jacobi_f32(float* C, float* V, int k, int K) {
+// accumulating the rotations in V, in precision T: on return C's columns are
+// mutually orthogonal, C_in V = C_out, so C_in = U Sigma V^T with
+// sigma_j = ||C_out[:, j]|| and U[:, j] = C_out[:, j] / sigma_j.  FP32 by
+// default because GB300's FP64 pipe is a small fraction of its FP32 pipe and
+// these k x k problems sit on serial critical paths (the aligners and Ritz
+// values stay within 1e-7 of FP64 factorisations on the FP32 workload's
+// spectrum); FP64 under LP_FLAG_KXK_FP64.  Returns false if the sweep limit was hit.
+template <typename T>
+__device__ bool warp_jacobi(T* C, T* V, int k, int K) {
+  using L = JacobiLimits<T>;
   const int lane = threadIdx.x & 31;
   for (int r = lane; r < k; r += 32)
-    for (int j = 0; j < k; ++j) V[r * K + j] = (r == j) ? 1.f : 0.f;
+    for (int j = 0; j < k; ++j) V[r * K + j] = (r == j) ? T(1) : T(0);
   __syncwarp();
-  const float tol = 1e-6f;
   for (int sweep = 0; sweep < 40; ++sweep) {
     int rotated = 0;
     for (int p = 0; p < k - 1; ++p) {
       for (int q = p + 1; q < k; ++q) {
-        float a = 0.f, b = 0.f, g = 0.f;
+        T a = 0, b = 0, g = 0;
         if (lane < k) {
-          const float cp = C[lane * K + p], cq = C[lane * K + q];
+          const T cp = C[lane * K + p], cq = C[lane * K + q];
           a = cp * cp;
           b = cq * cq;
           g = cp * cq;
         }
-        a = warp_sumf(a);
-        b = warp_sumf(b);
-        g = warp_sumf(g);
-        if (fabsf(g) > tol * sqrtf(a * b) && fabsf(g) > 1e-35f) {
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (fabs(g) > L::tol * sqrt(a * b) && fabs(g) > L::tiny) {
           rotated = 1;
           // zeta = (b - a) / 2g, t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2)
-          const float zeta = (b - a) / (2.f * g);
-          const float az = fabsf(zeta);
-          const float t = (zeta >= 0.f ? 1.f : -1.f) / (az > 1e15f ? 2.f * az : az + sqrtf(1.f + zeta * zeta));
-          const float c = 1.f / sqrtf(1.f + t * t);
-          const float sn = c * t;
+          const T zeta = (b - a) / (T(2) * g);
+          const T az = fabs(zeta);
+          const T t = (zeta >= T(0) ? T(1) : T(-1)) / (az > L::huge ? T(2) * az : az + sqrt(T(1) + zeta * zeta));
+          const T c = T(1) / sqrt(T(1) + t * t);
+          const T sn = c * t;
           if (lane < k) {
-            const float cp = C[lane * K + p], cq = C[lane * K + q];
+            const T cp = C[lane * K + p], cq = C[lane * K + q];
             C[lane * K + p] = c * cp - sn * cq;
             C[lane * K + q] = sn * cp + c * cq;
-            const float vp = V[lane * K + p], vq = V[lane * K + q];
+            const T vp = V[lane * K + p], vq = V[lane * K + q];
             V[lane * K + p] = c * vp - sn * vq;
             V[lane * K + q] = sn * vp + c * vq;
           }
@@ -241,6 +264,64 @@ __device__ void gram_fp32(const float* Y, int d, float* red, double* G) {
     }
     for (; q < S; ++q) s0 += red[(q * NBB + bb) * 16 + el];
     G[e] = static_cast<double>((s0 + s1) + (s2 + s3));
+  }
+  __syncthreads();
+}
+
+// G = Y^T Y in FP64 (LP_FLAG_KXK_FP64): the upper triangle of 4 x 4 blocks, one
+// per thread of a row slice; each FP32 product is exact in FP64 (two 24-bit
+// significands need 48 of its 53 bits) and is summed in FP64 over the slice's
+// rows; the slices are added in slice order and the lower triangle mirrored.
+template <int K>
+__device__ void gram_fp64(const float* Y, int d, double* red, double* G) {
+  constexpr int NB = K / 4, NBU = NB * (NB + 1) / 2, S = kT / NBU;
+  const int t = threadIdx.x;
+  const int blk = t % NBU, sl = t / NBU;
+  int bi = 0, rem = blk;
+  while (rem >= NB - bi) {
+    rem -= NB - bi;
+    ++bi;
+  }
+  const int bj = bi + rem;
+  if (sl < S) {
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    constexpr int U = 4;
+    for (int r0 = sl; r0 < d; r0 += S * U) {
+      float4 u[U], v[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int r = r0 + q * S;
+        u[q] = r < d ? *reinterpret_cast<const float4*>(Y + int64_t(r) * K + 4 * bi) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[q] = r < d ? *reinterpret_cast<const float4*>(Y + int64_t(r) * K + 4 * bj) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const double uu[4] = {u[q].x, u[q].y, u[q].z, u[q].w}, vv[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(uu[a], vv[b], acc[a][b]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) red[(sl * NBU + blk) * 16 + 4 * a + b] = acc[a][b];
+  }
+  __syncthreads();
+  for (int e = t; e < K * K; e += kT) {
+    const int i = e / K, j = e % K;
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    const int ba = a / 4, bb = b / 4;
+    const int idx = ba * NB - ba * (ba - 1) / 2 + (bb - ba);
+    const int el = 4 * (a % 4) + b % 4;
+    double sum = 0.0;
+    for (int q = 0; q < S; ++q) sum += red[(q * NBU + idx) * 16 + el];
+    G[e] = sum;
   }
   __syncthreads();
 }
@@ -373,18 +454,29 @@ __device__ void forward_rows(const float* Yin, float* Zout, const float* Lf, con
 
 // Z = orth(Y) of one d x K block by the CTA.  Y and Z may be written earlier in
 // the same kernel (the fused reduction writes Y; the second pass reads Z).
-template <int K>
+// F64: Gram and Cholesky in FP64 (LP_FLAG_KXK_FP64); else the FP32 Gram and
+// FP32 Cholesky with the FP64 factorisation as fallback.  The d x k forward
+// substitution is FP32 either way.
+template <int K, bool F64>
 __device__ void cholqr2_block(const float* Y, float* Z, int d, int k, int* status) {
   __shared__ __align__(16) double G[K * K];
   __shared__ __align__(16) float Lf[K * K];
   __shared__ float invd[K];
-  __shared__ __align__(16) float red[kT * 16];
+  __shared__ __align__(16) unsigned char red[(F64 ? 8 : 4) * kT * 16];
   for (int pass = 0; pass < 2; ++pass) {
     const float* src = pass == 0 ? Y : Z;
-    gram_fp32<K>(src, d, red, G);
-    if (threadIdx.x < 32 && !warp_cholesky_f32<K>(G, Lf, invd, k)) {
-      const bool ok = warp_cholesky_rl<K>(G, Lf, invd, k);
-      if (!ok && threadIdx.x == 0) atomicOr(status, ST_CHOL);
+    if (F64) {
+      gram_fp64<K>(src, d, reinterpret_cast<double*>(red), G);
+      if (threadIdx.x < 32) {
+        const bool ok = warp_cholesky_rl<K>(G, Lf, invd, k);
+        if (!ok && threadIdx.x == 0) atomicOr(status, ST_CHOL);
+      }
+    } else {
+      gram_fp32<K>(src, d, reinterpret_cast<float*>(red), G);
+      if (threadIdx.x < 32 && !warp_cholesky_f32<K>(G, Lf, invd, k)) {
+        const bool ok = warp_cholesky_rl<K>(G, Lf, invd, k);
+        if (!ok && threadIdx.x == 0) atomicOr(status, ST_CHOL);
+      }
     }
     __syncthreads();
     forward_rows<K>(src, Z, Lf, invd, d, k);
@@ -392,10 +484,10 @@ __device__ void cholqr2_block(const float* Y, float* Z, int d, int k, int* statu
   }
 }
 
-template <int K>
+template <int K, bool F64>
 __global__ void __launch_bounds__(kT) cholqr2_kernel(const float* __restrict__ Yall, float* __restrict__ Zall, int d,
                                                      int k, int* status) {
-  cholqr2_block<K>(Yall + int64_t(blockIdx.x) * d * K, Zall + int64_t(blockIdx.x) * d * K, d, k, status);
+  cholqr2_block<K, F64>(Yall + int64_t(blockIdx.x) * d * K, Zall + int64_t(blockIdx.x) * d * K, d, k, status);
 }
 
 
@@ -403,7 +495,7 @@ __global__ void __launch_bounds__(kT) cholqr2_kernel(const float* __restrict__ Y
 // One CTA per partition.  G_i (K x K float, row-major) = D_i (sign) or O_i (OPT).
 __global__ void __launch_bounds__(kT) align_kernel(const float* __restrict__ Zl, int64_t z_stride,
                                                    const float* __restrict__ Zb, int d, int k, int K, int base,
-                                                   int opt, float* __restrict__ Gout, int* status) {
+                                                   int opt, int f64, float* __restrict__ Gout, int* status) {
   extern __shared__ __align__(16) unsigned char sm[];
   double* C = reinterpret_cast<double*>(sm);   // K*K
   double* V = C + K * K;                        // K*K
@@ -460,13 +552,33 @@ __global__ void __launch_bounds__(kT) align_kernel(const float* __restrict__ Zl,
     }
     __syncthreads();
   }
-  if (t < 32) {
+  if (t < 32 && f64) {
+    // k x k Procrustes SVD in FP64 (LP_FLAG_KXK_FP64): C = U Sigma V^T, O = U V^T
+    const bool ok = warp_jacobi<double>(C, V, k, K);
+    if (!ok && t == 0) atomicOr(status, ST_JACOBI);
+    for (int j = 0; j < k; ++j) {
+      double nrm = 0.0;
+      if (t < k) nrm = C[t * K + j] * C[t * K + j];
+      nrm = warp_sum(nrm);
+      const double inv = nrm > 1e-300 ? 1.0 / sqrt(nrm) : 0.0;
+      if (t < k) C[t * K + j] *= inv;
+      if (!(nrm > 1e-300) && t == 0) atomicOr(status, ST_JACOBI);
+    }
+    __syncwarp();
+    for (int e = t; e < K * K; e += 32) {
+      const int a = e / K, b = e % K;
+      double sum = 0.0;
+      if (a < k && b < k)
+        for (int j = 0; j < k; ++j) sum = fma(C[a * K + j], V[b * K + j], sum);
+      Gi[e] = static_cast<float>(sum);
+    }
+  } else if (t < 32) {
     // FP32 copies in the V area (2 K*K floats fit in K*K doubles)
     float* Cf = reinterpret_cast<float*>(V);
     float* Vf = Cf + K * K;
     for (int e = t; e < K * K; e += 32) Cf[e] = static_cast<float>(C[e]);
     __syncwarp();
-    const bool ok = warp_jacobi_f32(Cf, Vf, k, K);
+    const bool ok = warp_jacobi<float>(Cf, Vf, k, K);
     if (!ok && t == 0) atomicOr(status, ST_JACOBI);
     // U[:, j] = C[:, j] / sigma_j ; O = U V^T
     for (int j = 0; j < k; ++j) {
@@ -552,7 +664,7 @@ __global__ void __launch_bounds__(kT) rho_kernel(const float* __restrict__ Zl, i
     float* Vf = Cf + K * K;
     for (int e = t; e < K * K; e += 32) Cf[e] = static_cast<float>(C[e]);
     __syncwarp();
-    const bool ok = warp_jacobi_f32(Cf, Vf, k, K);
+    const bool ok = warp_jacobi<float>(Cf, Vf, k, K);
     if (!ok && t == 0) atomicOr(status, ST_JACOBI);
     float top = 0.f;
     for (int j = 0; j < k; ++j) {
@@ -594,7 +706,8 @@ __global__ void aggregate_kernel(const float* __restrict__ Yl, const float* __re
 // ---------------------------------------------------------------- Ritz
 // H = Z^T (M Z) in FP64, split over row slices: block g adds the products of
 // its rows (staged in shared memory) into Hpart[g]; ritz_solve adds the slices
-// in slice order (deterministic), symmetrises, diagonalises (FP64 Jacobi),
+// in slice order (deterministic), symmetrises, diagonalises (Jacobi: FP32, or
+// FP64 under LP_FLAG_KXK_FP64),
 // orders by descending Ritz value and writes sigma and the reordered V;
 // ritz_rotate forms Zout = Z V row by row.
 constexpr int kRitzRows = 64;  // rows per slice
@@ -621,7 +734,7 @@ __global__ void __launch_bounds__(kT) ritz_partial_kernel(const float* __restric
 }
 
 __global__ void __launch_bounds__(kT) ritz_solve_kernel(const double* __restrict__ Hpart, int slices, int k, int K,
-                                                        double n, double* __restrict__ Vo,
+                                                        double n, int f64, double* __restrict__ Vo,
                                                         double* __restrict__ sigma, int* status) {
   extern __shared__ __align__(16) unsigned char sm[];
   double* H = reinterpret_cast<double*>(sm);  // K*K
@@ -646,19 +759,31 @@ __global__ void __launch_bounds__(kT) ritz_solve_kernel(const double* __restrict
       }
     }
     __syncwarp();
-    // H is symmetric positive semidefinite: its one-sided Jacobi SVD is its eigendecomposition
-    // (FP32 copies in the V area).
-    float* Hf = reinterpret_cast<float*>(V);
-    float* Vf = Hf + K * K;
-    for (int e = t; e < K * K; e += 32) Hf[e] = static_cast<float>(H[e]);
-    __syncwarp();
-    const bool ok = warp_jacobi_f32(Hf, Vf, k, K);
-    if (!ok && t == 0) atomicOr(status, ST_JACOBI);
-    for (int j = 0; j < k; ++j) {
-      float v = 0.f;
-      if (t < k) v = Hf[t * K + j] * Hf[t * K + j];
-      v = warp_sumf(v);
-      if (t == 0) lam[j] = v > 0.f ? sqrt(static_cast<double>(v)) : 0.0;
+    // H is symmetric positive semidefinite: its one-sided Jacobi SVD is its
+    // eigendecomposition, in FP64 under LP_FLAG_KXK_FP64, else on FP32 copies in
+    // the V area.
+    if (f64) {
+      const bool ok = warp_jacobi<double>(H, V, k, K);
+      if (!ok && t == 0) atomicOr(status, ST_JACOBI);
+      for (int j = 0; j < k; ++j) {
+        double v = 0.0;
+        if (t < k) v = H[t * K + j] * H[t * K + j];
+        v = warp_sum(v);
+        if (t == 0) lam[j] = v > 0.0 ? sqrt(v) : 0.0;
+      }
+    } else {
+      float* Hf = reinterpret_cast<float*>(V);
+      float* Vf = Hf + K * K;
+      for (int e = t; e < K * K; e += 32) Hf[e] = static_cast<float>(H[e]);
+      __syncwarp();
+      const bool ok = warp_jacobi<float>(Hf, Vf, k, K);
+      if (!ok && t == 0) atomicOr(status, ST_JACOBI);
+      for (int j = 0; j < k; ++j) {
+        float v = 0.f;
+        if (t < k) v = Hf[t * K + j] * Hf[t * K + j];
+        v = warp_sumf(v);
+        if (t == 0) lam[j] = v > 0.f ? sqrt(static_cast<double>(v)) : 0.0;
+      }
     }
     __syncwarp();
     if (t == 0) {
@@ -677,7 +802,9 @@ __global__ void __launch_bounds__(kT) ritz_solve_kernel(const double* __restrict
   __syncthreads();
   for (int e = t; e < K * K; e += kT) {
     const int l = e / K, j = e % K;
-    Vo[e] = j < k ? static_cast<double>(reinterpret_cast<const float*>(V)[K * K + l * K + order[j]]) : 0.0;
+    Vo[e] = j >= k ? 0.0
+                   : f64 ? V[l * K + order[j]]
+                         : static_cast<double>(reinterpret_cast<const float*>(V)[K * K + l * K + order[j]]);
   }
 }
 
@@ -735,19 +862,24 @@ cudaError_t launch_reduce(const float* P, const int* slot_begin, const float* sc
   return cudaGetLastError();
 }
 
-cudaError_t launch_cholqr2(const float* Y, float* Z, int batch, int d, int k, int K, int* status, cudaStream_t s) {
-  switch (K) {
-    case 8: cholqr2_kernel<8><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
-    case 16: cholqr2_kernel<16><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
-    case 32: cholqr2_kernel<32><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
+cudaError_t launch_cholqr2(const float* Y, float* Z, int batch, int d, int k, int K, int* status, cudaStream_t s,
+                           bool kxk_fp64) {
+  switch (K * 2 + (kxk_fp64 ? 1 : 0)) {
+    case 16: cholqr2_kernel<8, false><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
+    case 17: cholqr2_kernel<8, true><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
+    case 32: cholqr2_kernel<16, false><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
+    case 33: cholqr2_kernel<16, true><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
+    case 64: cholqr2_kernel<32, false><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
+    case 65: cholqr2_kernel<32, true><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_align(const float* Zl, int64_t z_stride, const float* Zb, int m, int d, int k, int K, int base,
-                         lp_aggregator agg, float* G, int* status, cudaStream_t s) {
-  align_kernel<<<m, kT, align_smem(K), s>>>(Zl, z_stride, Zb, d, k, K, base, agg == LP_AGG_OPT ? 1 : 0, G, status);
+                         lp_aggregator agg, float* G, int* status, cudaStream_t s, bool kxk_fp64) {
+  align_kernel<<<m, kT, align_smem(K), s>>>(Zl, z_stride, Zb, d, k, K, base, agg == LP_AGG_OPT ? 1 : 0,
+                                            kxk_fp64 ? 1 : 0, G, status);
   return cudaGetLastError();
 }
 
@@ -759,7 +891,7 @@ cudaError_t launch_aggregate(const float* Yl, const float* w, const float* G, in
 }
 
 cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, double n, double* Zout, double* sigma,
-                        double* scratch, int* status, cudaStream_t s) {
+                        double* scratch, int* status, cudaStream_t s, bool kxk_fp64) {
   const int slices = (d + kRitzRows - 1) / kRitzRows;
   double* Hpart = scratch;
   double* Vo = scratch + size_t(slices) * K * K;
@@ -767,7 +899,7 @@ cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, do
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t sm = size_t(2) * K * K * 8 + size_t(K) * 8 + size_t(K) * 4 + 16;
-  ritz_solve_kernel<<<1, kT, sm, s>>>(Hpart, slices, k, K, n, Vo, sigma, status);
+  ritz_solve_kernel<<<1, kT, sm, s>>>(Hpart, slices, k, K, n, kxk_fp64 ? 1 : 0, Vo, sigma, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int64_t total = int64_t(d) * k;
   ritz_rotate_kernel<<<static_cast<unsigned>((total + kT - 1) / kT), kT, 0, s>>>(Z, Vo, d, k, K, Zout);

@@ -7,10 +7,11 @@ C ABI, in the launch configurations the benchmark times.
     FP32 data as hi/lo BF16 planes on the tensor cores); then the whole 50-round
     solve (160 local steps) against the oracle's own whole solve, both
     aggregators, both paths, at the FP32 bar of 1e-6 in subspace distance.
-  * Precision workload (d = 2,048, k = 32, BF16, p = 4 x 30 + 3 refinement
-    rounds): the whole solve on 8 of its 128 partitions (31,250 rows each, the
-    workload's partition size; the oracle would need 65 GB for all 128) against
-    the oracle on the decoded BF16 values, at the reduced-precision bar of 1e-4.
+  * Precision workload (d = 2,048, k = 32, BF16 or FP8-E4M3, p = 4 x 30 + 3
+    refinement rounds): the whole solve on 8 of its 128 partitions (31,250 rows
+    each, the workload's partition size; the oracle would need 65 GB for all
+    128) against the oracle on the decoded values, at the reduced-precision bar
+    of 1e-4, with the k x k work in FP64 (as the workload states) and in FP32.
 
 These tests take minutes (the oracle's whole FP32-workload solve is ~160 FP64
 passes over 8 GB)."""
@@ -84,8 +85,8 @@ def test_fp32_workload_whole_solve_matches_oracle(gpu_lib, fp32_workload, agg):
         assert dist < FP32_SOLVE_TOL, (dtype, dist)
 
 
-@pytest.mark.parametrize("dtype", ["bf16", "e4m3"])
-def test_precision_workload_subset_whole_solve(gpu_lib, dtype):
+@pytest.mark.parametrize("dtype,agg", [("bf16", "sign"), ("bf16", "opt"), ("e4m3", "sign")])
+def test_precision_workload_subset_whole_solve(gpu_lib, dtype, agg):
     A, _, Y0 = synth.make_config_data("lowprec", n=8 * 31_250, m=8, threads=16)
     sizes = [31_250] * 8
     parts = synth.split_rows(A, sizes)
@@ -98,11 +99,13 @@ def test_precision_workload_subset_whole_solve(gpu_lib, dtype):
         exact = [("e4m3", c, s) for c, s in zip(stored, scales)]
     del parts
     sched = synth.config_schedule("lowprec")        # p = 4 x 30, then 3 rounds at p = 1
-    ref = O.localpower(exact, 32, sched, "sign", Y0)["Z"]
+    ref = O.localpower(exact, 32, sched, agg, Y0)["Z"]
     with B.LocalPower(stored, dtype=dtype, row_scales=scales) as lp:
         B.lp_autotune(lp.ctx, 32)
-        Z, _, st = lp.solve(32, sched[:30], "sign", Y0, refine_rounds=3)
-    dist = O.subspace_dist(Z, ref)
-    print(f"precision workload ({dtype}), 8 of 128 partitions: dist to the oracle's solve {dist:.3e} "
-          f"(path {st['path']})")
-    assert dist < TC_SOLVE_TOL, dist
+        # the workload's k x k arithmetic (FP64 Gram/Cholesky and Procrustes SVD), then the default
+        Z64, _, st = lp.solve(32, sched[:30], agg, Y0, refine_rounds=3, kxk_fp64=True)
+        Z32, _, _ = lp.solve(32, sched[:30], agg, Y0, refine_rounds=3)
+    d64, d32 = O.subspace_dist(Z64, ref), O.subspace_dist(Z32, ref)
+    print(f"precision workload ({dtype}, {agg}), 8 of 128 partitions: dist to the oracle's solve "
+          f"{d64:.3e} with FP64 k x k, {d32:.3e} with FP32 k x k (path {st['path']})")
+    assert d64 < TC_SOLVE_TOL and d32 < TC_SOLVE_TOL, (d64, d32)
