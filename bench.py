@@ -421,9 +421,11 @@ def _width_pools(torch, local, seed, pool_rows):
 def run_batching(args):
     """Batching: independent instances (n log-uniform [2e3, 2e5], d log-uniform
     [64, 1024] rounded to the pool widths, m [4, 32], k in {4, 8, 16, 32}; BF16;
-    p = 4, T = 30) loaded once into a batch, step kernels chosen per instance by
-    the autotuner, and every solve run by one CUDA graph launch.  Beside it: the
-    same instances solved one after another (each its own replayed graph)."""
+    p = 4, T = 30) loaded once into a batch; instances of one (d, k) form a group
+    whose every step kind is one launch over all of them, with the group's step
+    kernel chosen by the autotuner; every solve of the whole batch is one CUDA
+    graph launch.  Beside it: the same instances solved one after another (each
+    its own replayed graph)."""
     import torch
 
     import oracle
@@ -470,11 +472,17 @@ def run_batching(args):
             ms.append((time.perf_counter() - t0) * 1e3)
         clk = clocks.stop()
         outs = [bt.result(i) for i in range(len(inst))]
+        n_groups = bt.groups()
         a_bytes = sum(o[2]["a_bytes"] for o in outs)
-        launches = sum(o[2]["kernel_launches"] for o in outs)
+        # instances of one group (here: one (d, k), every other parameter is shared)
+        # report their group's launches; count each group once
+        group_of = {}
+        for r, o in zip(inst, outs):
+            group_of[(r["d"], r["k"])] = (o[2]["kernel_launches"], KERNELS[o[2]["path"]])
+        launches = sum(v[0] for v in group_of.values())
         paths = {}
-        for o in outs:
-            paths[KERNELS[o[2]["path"]]] = paths.get(KERNELS[o[2]["path"]], 0) + 1
+        for _, pth in group_of.values():
+            paths[pth] = paths.get(pth, 0) + 1
     # the same instances one after another, each with its own context and replayed graph
     seq_ms = None
     try:
@@ -504,13 +512,14 @@ def run_batching(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"LocalPower batching: {len(inst)} independent BF16 instances, n log-uniform "
                                    f"[2e3, 2e5], d log-uniform [64, 1024] rounded to 9 widths, m [4, 32], k in "
-                                   f"{{4, 8, 16, 32}}, p=4 x30 rounds, one graph launch per step",
-                       "instances": len(inst), "a_bytes_per_step": a_bytes,
+                                   f"{{4, 8, 16, 32}}, p=4 x30 rounds, one graph launch per step (instances "
+                                   f"of one (d, k) merged into a group: each step kind one launch per group)",
+                       "instances": len(inst), "groups": n_groups, "a_bytes_per_step": a_bytes,
                        "l2": "instances' A from 2.7 GB of device pools (larger than L2)"},
             "solves_per_s": len(inst) / (best / 1e3), "latency_ms": {"p50": float(np.percentile(ms, 50)),
                                                                     "p99": float(np.percentile(ms, 99)),
                                                                     "samples": len(ms)},
-            "kernel_launches_per_step": launches, "step_kernels_chosen": paths,
+            "kernel_launches_per_step": launches, "step_kernels_chosen_per_group": paths,
             "autotune_s": t_tune, "first_solve_with_capture_s": t_cap,
             "sequential_ms": seq_ms,
             "speedup_vs_sequential": (seq_ms / best) if isinstance(seq_ms, float) else None,

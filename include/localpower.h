@@ -356,25 +356,38 @@ void lp_server_destroy(lp_server* s);
 /* ----------------------------------------------------------------------------
  * Batch runner: many independent instances (the same lp_request description,
  * each its own shapes, schedule and dtype) loaded once and solved together by
- * one CUDA graph launch.  The paper has no counterpart.  The graph holds every
- * instance's whole solve as an independent branch; it is captured on the first
- * lp_batch_solve and replayed by later ones until instances are added or
- * re-tuned.  One thread drives a batch at a time.
+ * one CUDA graph launch.  The paper has no counterpart.  Instances that share
+ * the width d, the storage dtype, k, the schedule, the aggregator and the flags
+ * form a group: their partitions are copied back to back into one group
+ * context, and each step kind of the solve (the fused power step, the
+ * reduction, the local and global CholQR2, the alignment, the aggregation) is
+ * one launch over all of the group's instances; the step kernel is persistent
+ * (one CTA or CTA pair per SM walking the row pieces of every partition of
+ * every instance).  The graph holds each group's whole solve as an independent
+ * branch; it is captured on the first lp_batch_solve and replayed by later ones
+ * until instances are added or re-tuned.  An instance's result depends on the
+ * other instances of its group only through rounding (the row pieces follow the
+ * group's rows), and replays reproduce it bit for bit.  A device error or a
+ * numerical failure (LP_ERR_NUMERIC) in one instance is reported by every
+ * instance of its group.  One thread drives a batch at a time.
  * ------------------------------------------------------------------------- */
 typedef struct lp_batch lp_batch;
 
 /* lp_batch_create: an empty batch on `device`; instances are admitted while
- * the sum of their device-memory estimates stays within hbm_budget_bytes
- * (0 = no bound). */
+ * the sum of twice their device-memory estimates (each instance's data is held
+ * as loaded and again in its group) stays within hbm_budget_bytes (0 = no
+ * bound). */
 lp_status lp_batch_create(lp_batch** out, int device, size_t hbm_budget_bytes);
 
 /* lp_batch_add: load one instance (its partitions are copied to the device now;
  * the caller's buffers may be reused after the call); *index receives its
- * position.  LP_ERR_INVALID for malformed requests, LP_ERR_OOM over budget. */
+ * position.  LP_ERR_INVALID for malformed requests (LP_FLAG_TRACE included),
+ * LP_ERR_OOM over budget. */
 lp_status lp_batch_add(lp_batch* b, const lp_request* req, int* index);
 
-/* lp_batch_autotune: lp_autotune for every instance (the step kernel and its
- * tuning chosen by timing, per instance). */
+/* lp_batch_autotune: form the groups now and lp_autotune each group's context
+ * (the step kernel and its tuning chosen by timing on the group's own data);
+ * groups formed later, after more instances are added, are tuned too. */
 lp_status lp_batch_autotune(lp_batch* b);
 
 /* lp_batch_solve: every instance's solve, asynchronously, as one graph launch. */
@@ -385,6 +398,10 @@ lp_status lp_batch_result(lp_batch* b, int index, double* z_out, double* sigma_o
 
 /* lp_batch_size: number of instances (0 for NULL). */
 int lp_batch_size(const lp_batch* b);
+
+/* lp_batch_groups: number of groups the instances form (0 before the first
+ * lp_batch_solve or lp_batch_autotune after an lp_batch_add, and for NULL). */
+int lp_batch_groups(const lp_batch* b);
 
 /* lp_batch_error: text of the last failure on the batch ("" if none). */
 const char* lp_batch_error(const lp_batch* b);

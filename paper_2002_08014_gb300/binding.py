@@ -30,8 +30,8 @@ PATHS = {0: "simt", 1: "tc_resident", 2: "tc_streaming", 3: "tc_pair"}
 EXPORTS = ["lp_create", "lp_load_partitions", "lp_solve", "lp_solve_seeded", "lp_result", "lp_destroy", "lp_last_error",
            "lp_set_tuning", "lp_autotune", "lp_trace", "lp_eta", "lp_server_create", "lp_server_submit", "lp_server_progress",
            "lp_server_result", "lp_server_query", "lp_server_error", "lp_server_destroy", "lp_batch_create",
-           "lp_batch_add", "lp_batch_autotune", "lp_batch_solve", "lp_batch_result", "lp_batch_size", "lp_batch_error",
-           "lp_batch_destroy", "lp_power_step", "lp_orth", "lp_align_aggregate", "lp_power_step_static"]
+           "lp_batch_add", "lp_batch_autotune", "lp_batch_solve", "lp_batch_result", "lp_batch_size",
+           "lp_batch_groups", "lp_batch_error", "lp_batch_destroy", "lp_power_step", "lp_orth", "lp_align_aggregate", "lp_power_step_static"]
 
 
 class lp_stats(C.Structure):
@@ -121,6 +121,7 @@ def load(path: str | None = None, build_if_missing: bool = True) -> C.CDLL:
     L.lp_batch_solve.argtypes = [P]
     L.lp_batch_result.argtypes = [P, I, P, P, C.POINTER(lp_stats)]
     L.lp_batch_size.argtypes = [P]
+    L.lp_batch_groups.argtypes = [P]
     L.lp_batch_error.argtypes = [P]
     L.lp_batch_error.restype = C.c_char_p
     L.lp_batch_destroy.argtypes = [P]
@@ -542,6 +543,11 @@ class Batch:
 
     def __len__(self):
         return int(load().lp_batch_size(self.h))
+
+    def groups(self) -> int:
+        """Groups the instances form (instances sharing d, dtype, k, schedule,
+        aggregator and flags; 0 until the next solve or autotune)."""
+        return int(load().lp_batch_groups(self.h))
 
     def close(self):
         if self.h:

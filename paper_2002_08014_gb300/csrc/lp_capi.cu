@@ -76,6 +76,17 @@ struct lp_ctx {
   lp::TcsTuning tuning;
   bool prefer_resident = false;  // set by lp_autotune for LP_BF16 data
 
+  // Independent problems sharing this context's partitions (the batch runner's
+  // groups): problem q owns partitions [prob_begin[q], prob_begin[q + 1]), has
+  // its own start block, bases, weights s_i / n_q, aggregate and result.  An
+  // ordinary context is one problem.
+  int nprob = 1;
+  std::vector<int> prob_begin;
+  std::vector<int64_t> prob_n;
+  int* dPartProb = nullptr;   // partition -> problem
+  int* dPartBase = nullptr;   // partition -> its problem's base partition
+  int* dProbBegin = nullptr;  // nprob + 1 partition offsets
+
   // per-round records (LP_FLAG_TRACE): Z_t blocks and per-partition residuals
   float* dTraceZ = nullptr;
   double* dTraceRho = nullptr;
@@ -200,7 +211,7 @@ StateSizes state_sizes(const lp_ctx* c, int K) {
   StateSizes s;
   s.P = size_t(max_segments(c->sms, c->m, c->n)) * c->d * K * 4;
   s.Yl = size_t(c->m) * c->d * K * 4;
-  s.Y = size_t(c->d) * K * 4;
+  s.Y = size_t(c->nprob) * c->d * K * 4;
   s.G = size_t(c->m) * K * K * 4;
   s.stage = size_t(c->m) * c->d * K * 8;
   return s;
@@ -216,8 +227,8 @@ void free_state(lp_ctx* c) {
   dfree(c, c->dZ, s.Y);
   dfree(c, c->dMZ, s.Y);
   dfree(c, c->dG, s.G);
-  dfree(c, c->dZout, size_t(c->d) * LP_MAX_K * 8);
-  dfree(c, c->dSigma, LP_MAX_K * 8);
+  dfree(c, c->dZout, size_t(c->nprob) * c->d * LP_MAX_K * 8);
+  dfree(c, c->dSigma, size_t(c->nprob) * LP_MAX_K * 8);
   dfree(c, c->dStage, c->stage_bytes);
   c->stage_bytes = 0;
   c->Kcap = 0;
@@ -235,8 +246,8 @@ lp_status ensure_state(lp_ctx* c, int K) {
   lp_status st;
   if ((st = dalloc(c, &c->dP, s.P)) || (st = dalloc(c, &c->dYl, s.Yl)) || (st = dalloc(c, &c->dZl, s.Yl)) ||
       (st = dalloc(c, &c->dY, s.Y)) || (st = dalloc(c, &c->dZ, s.Y)) || (st = dalloc(c, &c->dMZ, s.Y)) ||
-      (st = dalloc(c, &c->dG, s.G)) || (st = dalloc(c, &c->dZout, size_t(c->d) * LP_MAX_K * 8)) ||
-      (st = dalloc(c, &c->dSigma, LP_MAX_K * 8)) || (st = dalloc(c, &c->dStage, s.stage))) {
+      (st = dalloc(c, &c->dG, s.G)) || (st = dalloc(c, &c->dZout, size_t(c->nprob) * c->d * LP_MAX_K * 8)) ||
+      (st = dalloc(c, &c->dSigma, size_t(c->nprob) * LP_MAX_K * 8)) || (st = dalloc(c, &c->dStage, s.stage))) {
     c->Kcap = K;  // free what was allocated
     free_state(c);
     return st;
@@ -262,6 +273,12 @@ void free_partitions(lp_ctx* c) {
   dfree(c, c->dSegPtrTcs, (size_t(c->sms) + 1) * 4);
   dfree(c, c->dSlotBeginTcs, (size_t(c->m) + 1) * 4);
   free_state(c);
+  dfree(c, c->dPartProb, size_t(c->m) * 4);
+  dfree(c, c->dPartBase, size_t(c->m) * 4);
+  dfree(c, c->dProbBegin, (size_t(c->nprob) + 1) * 4);
+  c->nprob = 1;
+  c->prob_begin.clear();
+  c->prob_n.clear();
   c->nslots_tc = 0;
   c->tc_ready = false;
   c->nslots_tcs = 0;
@@ -471,25 +488,11 @@ lp_status lp_load_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, l
 
 }  // extern "C"
 
-lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int64_t pitch, lp_dtype dtype,
-                           const void* const* parts, const float* const* row_scales, lp_ptr_space space) {
-  if (!c) return LP_ERR_INVALID;
-  c->err.clear();
-  if (pitch < d) return fail(c, LP_ERR_INVALID, "row pitch below d");
-  if (m < 1 || !rows || !parts) return fail(c, LP_ERR_INVALID, "need m >= 1 and non-NULL rows/parts");
-  if (d < 1 || d > (1 << 20)) return fail(c, LP_ERR_INVALID, "d out of range");
-  if (dtype != LP_F32 && dtype != LP_BF16 && dtype != LP_FP8_E4M3 && dtype != LP_F32_BF16X2)
-    return fail(c, LP_ERR_INVALID, "unknown dtype");
-  if (space != LP_HOST && space != LP_DEVICE) return fail(c, LP_ERR_INVALID, "unknown pointer space");
-  if (dtype == LP_FP8_E4M3 && !row_scales) return fail(c, LP_ERR_INVALID, "FP8 partitions need row_scales");
-  int64_t n = 0;
-  for (int i = 0; i < m; ++i) {
-    if (rows[i] < 1) return fail(c, LP_ERR_INVALID, "partition " + std::to_string(i) + " has no rows");
-    if (!parts[i]) return fail(c, LP_ERR_INVALID, "partition " + std::to_string(i) + " pointer is NULL");
-    if (dtype == LP_FP8_E4M3 && !row_scales[i])
-      return fail(c, LP_ERR_INVALID, "partition " + std::to_string(i) + " scales pointer is NULL");
-    n += rows[i];
-  }
+// Buffers, segment tables, plans and weights for m partitions of the given row
+// counts (n in total), or - for the same shapes as loaded now - the existing ones
+// (*reused).  The caller then copies the data into c->dA (and c->dScales).
+static lp_status setup_partitions(lp_ctx* c, int m, const int64_t* rows, int64_t d, lp_dtype dtype, int64_t n,
+                                  bool* reused) {
   LP_CUDA(cudaSetDevice(c->device));
   LP_CUDA(cudaStreamSynchronize(c->stream));
   // New data of the same shapes (m, rows, d, dtype) go into the existing buffers:
@@ -590,6 +593,38 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
   // the host vectors above are pageable: the copies must finish before they go
   LP_CUDA(cudaStreamSynchronize(c->stream));
   }
+  if (c->nprob == 1) {
+    c->prob_begin = {0, m};
+    c->prob_n = {n};
+  }
+  *reused = reuse;
+  return LP_OK;
+}
+
+lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int64_t pitch, lp_dtype dtype,
+                           const void* const* parts, const float* const* row_scales, lp_ptr_space space) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  if (pitch < d) return fail(c, LP_ERR_INVALID, "row pitch below d");
+  if (m < 1 || !rows || !parts) return fail(c, LP_ERR_INVALID, "need m >= 1 and non-NULL rows/parts");
+  if (d < 1 || d > (1 << 20)) return fail(c, LP_ERR_INVALID, "d out of range");
+  if (dtype != LP_F32 && dtype != LP_BF16 && dtype != LP_FP8_E4M3 && dtype != LP_F32_BF16X2)
+    return fail(c, LP_ERR_INVALID, "unknown dtype");
+  if (space != LP_HOST && space != LP_DEVICE) return fail(c, LP_ERR_INVALID, "unknown pointer space");
+  if (dtype == LP_FP8_E4M3 && !row_scales) return fail(c, LP_ERR_INVALID, "FP8 partitions need row_scales");
+  int64_t n = 0;
+  for (int i = 0; i < m; ++i) {
+    if (rows[i] < 1) return fail(c, LP_ERR_INVALID, "partition " + std::to_string(i) + " has no rows");
+    if (!parts[i]) return fail(c, LP_ERR_INVALID, "partition " + std::to_string(i) + " pointer is NULL");
+    if (dtype == LP_FP8_E4M3 && !row_scales[i])
+      return fail(c, LP_ERR_INVALID, "partition " + std::to_string(i) + " scales pointer is NULL");
+    n += rows[i];
+  }
+  bool reuse = false;
+  lp_status st = setup_partitions(c, m, rows, d, dtype, n, &reuse);
+  if (st) return st;
+  const bool split = dtype == LP_F32_BF16X2;
+  const size_t eb = plane_bytes(dtype);
   const cudaMemcpyKind kind = space == LP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   if (split) {
     // FP32 -> hi / lo planes on the device; host data go through a bounded FP32 staging buffer.
@@ -646,6 +681,96 @@ lp_status lp::load_pitched(lp_ctx* c, int m, const int64_t* rows, int64_t d, int
     for (float v : sc) mx = std::max(mx, std::fabs(v));
     c->smax2 = mx > 0.f && std::isfinite(mx * mx) ? mx * mx : 1.f;
   }
+  return LP_OK;
+}
+
+lp_status lp::load_merged(lp_ctx* c, lp_ctx* const* src, int nsrc) {
+  if (!c || !src || nsrc < 1) return LP_ERR_INVALID;
+  c->err.clear();
+  const lp_ctx* s0 = src[0];
+  std::vector<int64_t> rows;
+  int64_t n = 0;
+  for (int j = 0; j < nsrc; ++j) {
+    const lp_ctx* sj = src[j];
+    if (!sj || sj->m == 0 || sj->d != s0->d || sj->dtype != s0->dtype || sj->ld != s0->ld || sj->nprob != 1 ||
+        sj->device != c->device)
+      return fail(c, LP_ERR_INVALID, "merged contexts must hold loaded partitions of one width, type and device");
+    rows.insert(rows.end(), sj->rows.begin(), sj->rows.end());
+    n += sj->n;
+  }
+  LP_CUDA(cudaSetDevice(c->device));
+  for (int j = 0; j < nsrc; ++j) LP_CUDA(cudaStreamSynchronize(src[j]->stream));
+  bool reuse = false;
+  lp_status st = setup_partitions(c, static_cast<int>(rows.size()), rows.data(), s0->d, s0->dtype, n, &reuse);
+  if (st) return st;
+  // the stored rows (padding columns included) plane by plane: plane p of a
+  // context with N rows starts N * ld elements after plane p - 1
+  const size_t eb = plane_bytes(s0->dtype), row_bytes = size_t(c->ld) * eb;
+  const int nplanes = s0->dtype == LP_F32_BF16X2 ? 2 : 1;
+  int64_t off = 0;
+  float smax2 = 0.f;
+  for (int j = 0; j < nsrc; ++j) {
+    const lp_ctx* sj = src[j];
+    for (int pl = 0; pl < nplanes; ++pl)
+      LP_CUDA(cudaMemcpyAsync(static_cast<char*>(c->dA) + (size_t(pl) * n + off) * row_bytes,
+                              static_cast<const char*>(sj->dA) + size_t(pl) * sj->n * row_bytes,
+                              size_t(sj->n) * row_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (s0->dtype == LP_FP8_E4M3) {
+      LP_CUDA(cudaMemcpyAsync(c->dScales + off, sj->dScales, size_t(sj->n) * 4, cudaMemcpyDeviceToDevice, c->stream));
+      smax2 = std::max(smax2, sj->smax2);
+    }
+    off += sj->n;
+  }
+  if (s0->dtype == LP_FP8_E4M3) c->smax2 = smax2 > 0.f ? smax2 : 1.f;
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  std::vector<int> begin(nsrc + 1, 0);
+  for (int j = 0; j < nsrc; ++j) begin[j + 1] = begin[j] + src[j]->m;
+  return lp::set_problems(c, nsrc, begin.data());
+}
+
+lp_status lp::set_problems(lp_ctx* c, int nprob, const int* part_begin) {
+  if (!c) return LP_ERR_INVALID;
+  if (c->m == 0) return fail(c, LP_ERR_STATE, "no partitions loaded");
+  if (nprob < 1 || !part_begin || part_begin[0] != 0 || part_begin[nprob] != c->m)
+    return fail(c, LP_ERR_INVALID, "problem ranges must cover the partitions");
+  for (int q = 0; q < nprob; ++q)
+    if (part_begin[q + 1] <= part_begin[q]) return fail(c, LP_ERR_INVALID, "every problem needs a partition");
+  LP_CUDA(cudaSetDevice(c->device));
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  // the solve buffers are sized by the problem count
+  drop_graph(c);
+  free_state(c);
+  dfree(c, c->dPartProb, size_t(c->m) * 4);
+  dfree(c, c->dPartBase, size_t(c->m) * 4);
+  dfree(c, c->dProbBegin, (size_t(c->nprob) + 1) * 4);
+  c->nprob = nprob;
+  c->prob_begin.assign(part_begin, part_begin + nprob + 1);
+  c->prob_n.assign(nprob, 0);
+  std::vector<int> part_prob(c->m), part_base(c->m);
+  std::vector<float> w(c->m);
+  for (int q = 0; q < nprob; ++q) {
+    int b = part_begin[q];
+    for (int i = part_begin[q]; i < part_begin[q + 1]; ++i) {
+      c->prob_n[q] += c->rows[i];
+      if (c->rows[i] > c->rows[b]) b = i;  // the first largest partition, as for one problem
+    }
+    for (int i = part_begin[q]; i < part_begin[q + 1]; ++i) {
+      part_prob[i] = q;
+      part_base[i] = b;
+      w[i] = static_cast<float>(double(c->rows[i]) / double(c->prob_n[q]));
+    }
+  }
+  c->base = part_base[0];
+  lp_status st;
+  if ((st = dalloc(c, &c->dPartProb, size_t(c->m) * 4)) || (st = dalloc(c, &c->dPartBase, size_t(c->m) * 4)) ||
+      (st = dalloc(c, &c->dProbBegin, (size_t(nprob) + 1) * 4)))
+    return st;
+  LP_CUDA(cudaMemcpyAsync(c->dPartProb, part_prob.data(), size_t(c->m) * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dPartBase, part_base.data(), size_t(c->m) * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dProbBegin, part_begin, (size_t(nprob) + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dW, w.data(), size_t(c->m) * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  c->solved = false;
   return LP_OK;
 }
 
@@ -818,20 +943,32 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
   const int d = static_cast<int>(c->d);
   const int m = c->m;
   const int K = kcap_of(k);
+  // Several problems (a batch group): one start block, aggregate, orth and result
+  // per problem; each partition multiplies its own problem's basis at the start
+  // of a round and aligns with its own problem's base partition.
+  const int NP = c->nprob;
+  const bool multi = NP > 1;
   lp_status st;
   LP_CUDA(cudaMemsetAsync(c->dStatus, 0, 4, c->stream));
-  if ((st = check_launch(c, lp::launch_pack(dy0, c->dY, 1, d, k, K, c->stream), "pack"))) return st;
-  if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream, kxk64), "orth"))) return st;
+  if ((st = check_launch(c, lp::launch_pack(dy0, c->dY, NP, d, k, K, c->stream), "pack"))) return st;
+  if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, NP, d, k, K, c->dStatus, c->stream, kxk64), "orth")))
+    return st;
 
   const int rounds = T + refine_rounds;
   const int64_t zs = int64_t(d) * K;
+  // the first step of a round: the shared basis, or each partition's copy of its problem's
+  auto first_step = [&]() -> lp_status {
+    if (!multi) return launch_step(c, K, c->dZ, 0, timing);
+    lp_status s2 = check_launch(c, lp::launch_broadcast(c->dZ, c->dPartProb, m, d, K, c->dZl, c->stream), "broadcast");
+    return s2 ? s2 : launch_step(c, K, c->dZl, zs, timing);
+  };
   for (int t = 0; t < rounds; ++t) {
     const int p = t < T ? p_schedule[t] : 1;
     for (int j = 0; j < p; ++j) {
       if (j > 0 && (st = check_launch(c, lp::launch_cholqr2(c->dYl, c->dZl, m, d, k, K, c->dStatus, c->stream, kxk64),
                                       "local orth")))
         return st;
-      if ((st = launch_step(c, K, j == 0 ? c->dZ : c->dZl, j == 0 ? 0 : zs, timing))) return st;
+      if ((st = j == 0 ? first_step() : launch_step(c, K, c->dZl, zs, timing))) return st;
       if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream,
                                                   c->max_slots[c->path]),
                              "reduce")))
@@ -842,15 +979,15 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
     if (align) {
       // The last basis each partition multiplied this round is Z_i (orth of its previous Y_i).
       if ((st = check_launch(c, lp::launch_align(c->dZl, zs, c->dZl + zs * c->base, m, d, k, K, c->base, agg, c->dG,
-                                                 c->dStatus, c->stream, kxk64),
+                                                 c->dStatus, c->stream, kxk64, multi ? c->dPartBase : nullptr),
                              "align")))
         return st;
     }
     if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, align ? c->dG : nullptr, agg == LP_AGG_SIGN ? 1 : 0,
-                                                   m, d, K, c->dY, c->stream),
+                                                   m, d, K, c->dY, c->stream, multi ? c->dProbBegin : nullptr, NP),
                            "aggregate")))
       return st;
-    if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, 1, d, k, K, c->dStatus, c->stream, kxk64), "orth")))
+    if ((st = check_launch(c, lp::launch_cholqr2(c->dY, c->dZ, NP, d, k, K, c->dStatus, c->stream, kxk64), "orth")))
       return st;
     if (trace) {
       LP_CUDA(cudaMemcpyAsync(c->dTraceZ + size_t(t) * d * K, c->dZ, size_t(d) * K * 4, cudaMemcpyDeviceToDevice,
@@ -868,21 +1005,25 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
     c->stats.rounds++;
   }
   if (c->ritz) {
-    if ((st = launch_step(c, K, c->dZ, 0, timing))) return st;
+    if ((st = first_step())) return st;
     if ((st = check_launch(c, lp::launch_reduce(c->dP, slot_begin_of(c), c->dInvS, m, d, K, c->dYl, c->stream, c->max_slots[c->path]), "reduce")))
       return st;
-    if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, nullptr, 0, m, d, K, c->dMZ, c->stream),
+    if ((st = check_launch(c, lp::launch_aggregate(c->dYl, c->dW, nullptr, 0, m, d, K, c->dMZ, c->stream,
+                                                   multi ? c->dProbBegin : nullptr, NP),
                            "aggregate")))
       return st;
     // the partials buffer is free again after the reduction: it holds the Ritz scratch
     if (lp::ritz_scratch_bytes(d, K) > state_sizes(c, K).P) return fail(c, LP_ERR_INVALID, "Ritz scratch too small");
-    if ((st = check_launch(c, lp::launch_ritz(c->dZ, c->dMZ, d, k, K, double(c->n), c->dZout, c->dSigma,
-                                              reinterpret_cast<double*>(c->dP), c->dStatus, c->stream, kxk64),
-                           "ritz")))
-      return st;
-    c->stats.kernel_launches += 2;  // launch_ritz runs three kernels
+    for (int q = 0; q < NP; ++q) {
+      if ((st = check_launch(c, lp::launch_ritz(c->dZ + q * zs, c->dMZ + q * zs, d, k, K, double(c->prob_n[q]),
+                                                c->dZout + size_t(q) * d * k, c->dSigma + size_t(q) * LP_MAX_K,
+                                                reinterpret_cast<double*>(c->dP), c->dStatus, c->stream, kxk64),
+                             "ritz")))
+        return st;
+      c->stats.kernel_launches += 2;  // launch_ritz runs three kernels
+    }
   } else {
-    if ((st = check_launch(c, lp::launch_unpack(c->dZ, c->dZout, 1, d, k, K, c->stream), "unpack"))) return st;
+    if ((st = check_launch(c, lp::launch_unpack(c->dZ, c->dZout, NP, d, k, K, c->stream), "unpack"))) return st;
   }
   return LP_OK;
 }
@@ -1033,6 +1174,8 @@ static lp_status solve_prepare(lp_ctx* c, int k, const int* p_schedule, int T, l
   if ((st = select_path(c, k, flags))) return st;
   if ((st = ensure_state(c, K))) return st;
   c->traced_rounds = 0;
+  if ((flags & LP_FLAG_TRACE) && c->nprob > 1)
+    return fail(c, LP_ERR_INVALID, "LP_FLAG_TRACE records one problem per context");
   if (flags & LP_FLAG_TRACE) {
     const int rounds = T + refine_rounds;
     const size_t zb = size_t(rounds) * c->d * K * 4, rb = size_t(rounds) * c->m * 8;
@@ -1050,7 +1193,7 @@ static lp_status solve_prepare(lp_ctx* c, int k, const int* p_schedule, int T, l
   c->k = k;
   c->ritz = (flags & LP_FLAG_RITZ) != 0;
   if (record_start) LP_CUDA(cudaEventRecord(c->ev0, c->stream));
-  return stage_in(c, y0, size_t(c->d) * k, LP_HOST, dy0);
+  return stage_in(c, y0, size_t(c->nprob) * c->d * k, LP_HOST, dy0);  // one start block per problem
 }
 
 static void solve_mark(lp_ctx* c, int k, int rounds, unsigned flags) {
@@ -1421,11 +1564,11 @@ lp_status lp_align_aggregate(lp_ctx* c, int m, int64_t d, int k, lp_aggregator a
   const bool align = agg != LP_AGG_IDENTITY;
   if (align && (st = check_launch(c, lp::launch_align(Zl, int64_t(d) * K, Zl + int64_t(d) * K * base, m, di, k, K, base,
                                                       agg, G, c->dStatus, c->stream,
-                                                      (flags & LP_FLAG_KXK_FP64) != 0),
+                                                      (flags & LP_FLAG_KXK_FP64) != 0, nullptr),
                                   "align")))
     return st;
   if ((st = check_launch(c, lp::launch_aggregate(Yl, W, align ? G : nullptr, agg == LP_AGG_SIGN ? 1 : 0, m, di, K, Y,
-                                                 c->stream),
+                                                 c->stream, nullptr, 1),
                          "aggregate")))
     return st;
   if ((st = check_launch(c, lp::launch_unpack(Y, dy, 1, di, k, K, c->stream), "unpack"))) return st;
@@ -1478,3 +1621,34 @@ void lp::batch_mark(lp_ctx* c, int k, const lp_stats& captured, int rounds, unsi
 }
 
 cudaStream_t lp::ctx_stream(lp_ctx* c) { return c->stream; }
+
+lp_status lp::problem_result(lp_ctx* c, int q, double* z_out, double* sigma_out, lp_stats* stats) {
+  if (!c) return LP_ERR_INVALID;
+  c->err.clear();
+  if (q < 0 || q >= c->nprob) return fail(c, LP_ERR_INVALID, "problem index out of range");
+  if (!c->solved) return fail(c, LP_ERR_STATE, "no solve to report");
+  LP_CUDA(cudaSetDevice(c->device));
+  LP_CUDA(cudaStreamSynchronize(c->stream));
+  int status = 0;
+  LP_CUDA(cudaMemcpy(&status, c->dStatus, 4, cudaMemcpyDeviceToHost));
+  const size_t blk = size_t(c->d) * c->k;
+  if (z_out) LP_CUDA(cudaMemcpy(z_out, c->dZout + q * blk, blk * 8, cudaMemcpyDeviceToHost));
+  if (sigma_out) {
+    if (c->ritz)
+      LP_CUDA(cudaMemcpy(sigma_out, c->dSigma + size_t(q) * LP_MAX_K, size_t(c->k) * 8, cudaMemcpyDeviceToHost));
+    else std::memset(sigma_out, 0, size_t(c->k) * 8);
+  }
+  if (stats) {
+    // the group's counters, with the shape and the A bytes of this problem
+    *stats = c->stats;
+    stats->n = c->prob_n[q];
+    stats->m = c->prob_begin[q + 1] - c->prob_begin[q];
+    stats->a_bytes = c->stats.a_bytes * double(c->prob_n[q]) / double(c->n);
+  }
+  // the status word is shared by the group's problems
+  if (status & lp::ST_TIMEOUT) return fail(c, LP_ERR_TIMEOUT, "device wait timed out");
+  if (status & lp::ST_CHOL) return fail(c, LP_ERR_NUMERIC, "Cholesky breakdown (non-positive or non-finite pivot)");
+  if (status & lp::ST_NONFINITE) return fail(c, LP_ERR_NUMERIC, "non-finite iterate");
+  if (status & lp::ST_JACOBI) return fail(c, LP_ERR_NUMERIC, "Jacobi iteration did not converge or singular block");
+  return LP_OK;
+}

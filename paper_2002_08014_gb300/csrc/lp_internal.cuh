@@ -143,6 +143,16 @@ lp_status batch_enqueue(lp_ctx* c, int k, const int* p_schedule, int T, lp_aggre
                         unsigned flags, lp_stats* captured);
 void batch_mark(lp_ctx* c, int k, const lp_stats& captured, int rounds, unsigned flags);
 cudaStream_t ctx_stream(lp_ctx* c);
+// Several independent problems in one context (the batch runner's groups): load the
+// partitions of nsrc loaded single-problem contexts of one width and type back to
+// back (device copies of the stored rows) and make each source one problem.
+lp_status load_merged(lp_ctx* c, lp_ctx* const* src, int nsrc);
+// Problem q owns partitions [part_begin[q], part_begin[q + 1]); weights s_i / n_q, the
+// base is each problem's first largest partition.  lp_solve then takes nprob
+// consecutive d x k start blocks.
+lp_status set_problems(lp_ctx* c, int nprob, const int* part_begin);
+// lp_result of problem q (the stats are the context's, with problem q's n, m and A bytes).
+lp_status problem_result(lp_ctx* c, int q, double* z_out, double* sigma_out, lp_stats* stats);
 
 // Message returned by lp_last_error(NULL) (failures of calls without a context).
 void set_no_context_error(const char* msg);
@@ -159,11 +169,18 @@ cudaError_t launch_cholqr2(const float* Y, float* Z, int batch, int d, int k, in
                            bool kxk_fp64);
 // G_i = aligning matrices (K x K, FP32) for agg in {SIGN, OPT}; base gets I.  kxk_fp64:
 // the k x k Procrustes SVD in FP64, else FP32.
+// part_base (device, may be nullptr): per-partition base partition (several problems in
+// one context); then Zb and base are ignored and Z_b = Zl + z_stride * part_base[i].
 cudaError_t launch_align(const float* Zl, int64_t z_stride, const float* Zb, int m, int d, int k, int K, int base,
-                         lp_aggregator agg, float* G, int* status, cudaStream_t s, bool kxk_fp64);
-// Y = sum_i w_i Y_i G_i  (G == nullptr: identity; diag_only: G_i diagonal)
+                         lp_aggregator agg, float* G, int* status, cudaStream_t s, bool kxk_fp64,
+                         const int* part_base);
+// Y = sum_i w_i Y_i G_i  (G == nullptr: identity; diag_only: G_i diagonal).  With
+// prob_begin (device, nprob + 1 offsets): Y_q = the sum over problem q's partitions,
+// nprob consecutive d x K blocks.
 cudaError_t launch_aggregate(const float* Yl, const float* w, const float* G, int diag_only, int m, int d, int K,
-                             float* Y, cudaStream_t s);
+                             float* Y, cudaStream_t s, const int* prob_begin, int nprob);
+// Zl[i] = Z[part_prob[i]] for the m partitions' d x K blocks.
+cudaError_t launch_broadcast(const float* Z, const int* part_prob, int m, int d, int K, float* Zl, cudaStream_t s);
 // Ritz: H = Z^T MZ (FP64 sums), eig by Jacobi (FP64 when kxk_fp64, else FP32), Zout = Z W
 // (FP64), sigma = sqrt(n lambda).  Three launches; `scratch` holds ritz_scratch_bytes(d, K) bytes.
 cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, double n, double* Zout, double* sigma,

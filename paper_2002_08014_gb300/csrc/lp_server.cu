@@ -270,21 +270,43 @@ void lp_server_destroy(lp_server* s) {
 // =============================================================================
 // Batch runner: many independent instances solved by one CUDA graph launch.
 //
-// Each instance owns a context (its partitions loaded once, its own stream and
-// state).  lp_batch_solve uploads every instance's start block, then - the
-// first time, or after instances or tuning changed - captures every instance's
-// whole launch sequence into one graph: a fork event on the batch stream, each
-// instance's sequence on its own stream, a join back.  The branches are
-// independent, so the GPU runs the instances' kernels side by side; later
-// solves replay the graph with one launch.
+// Each added instance is loaded into a context of its own (validation, packing,
+// its copy of the data).  Before the first solve, instances that share the
+// shape of the work - width d, storage type, k, schedule, aggregator and flags -
+// are merged into one group context: their partitions are copied back to back
+// into the group's buffers and each instance becomes one problem of the group
+// (its own start block, bases, weights, aggregate and result).  A group's solve
+// is then the ordinary launch sequence with every step kind covering all of the
+// group's instances at once: one persistent step-kernel launch walks the row
+// pieces of every partition of every instance (its work list, dealt to the
+// CTAs by rows), one reduction, one batched CholQR2 over all partitions, one
+// alignment, one aggregation and one batched CholQR2 over the problems.  The
+// groups' sequences are captured into one graph as independent branches (a
+// fork event on the batch stream, each group on its own stream, a join back),
+// so the GPU runs different groups' kernels side by side; later solves replay
+// the graph with one launch.  Each group's step kernel and tuning come from the
+// autotuner, timed on the group's own data.
 namespace {
 
 struct Inst {
-  Request q;     // parameters (ctx, results unused here)
+  Request q;            // parameters (q.ctx holds this instance's loaded data)
+  int group = -1;       // group index
+  int problem = -1;     // problem index inside the group
+};
+
+struct Group {
   lp_ctx* ctx = nullptr;
+  std::vector<int> members;  // instance indices, in problem order
+  std::vector<double> y0;    // members' start blocks back to back
   lp_stats captured{};
   cudaEvent_t join = nullptr, ready = nullptr;
 };
+
+// Instances of one group share every parameter of the launch sequence.
+bool same_group(const Request& a, const Request& b) {
+  return a.d == b.d && a.dtype == b.dtype && a.k == b.k && a.T == b.T && a.refine == b.refine && a.agg == b.agg &&
+         a.flags == b.flags && a.sched == b.sched;
+}
 
 }  // namespace
 
@@ -295,6 +317,9 @@ struct lp_batch {
   cudaStream_t root = nullptr;
   cudaEvent_t fork = nullptr;
   std::vector<std::unique_ptr<Inst>> inst;
+  std::vector<std::unique_ptr<Group>> groups;
+  bool grouped = false;   // groups reflect the current instances
+  bool tuned = false;     // lp_batch_autotune asked for tuned groups
   cudaGraphExec_t exec = nullptr;
   bool solved = false;
   std::string err;
@@ -311,6 +336,65 @@ void drop_batch_graph(lp_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   b->exec = nullptr;
   b->solved = false;
+}
+
+void drop_groups(lp_batch* b) {
+  drop_batch_graph(b);
+  for (auto& g : b->groups) {
+    if (g->join) cudaEventDestroy(g->join);
+    if (g->ready) cudaEventDestroy(g->ready);
+    lp_destroy(g->ctx);
+  }
+  b->groups.clear();
+  b->grouped = false;
+}
+
+// Merge the instances into groups (in order of first appearance) and tune them
+// if the batch was asked to.
+lp_status build_groups(lp_batch* b) {
+  if (b->grouped) return LP_OK;
+  drop_groups(b);
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    Inst& in = *b->inst[i];
+    int g = -1;
+    for (size_t j = 0; j < b->groups.size() && g < 0; ++j)
+      if (same_group(b->inst[b->groups[j]->members[0]]->q, in.q)) g = static_cast<int>(j);
+    if (g < 0) {
+      b->groups.push_back(std::make_unique<Group>());
+      g = static_cast<int>(b->groups.size()) - 1;
+    }
+    in.group = g;
+    in.problem = static_cast<int>(b->groups[g]->members.size());
+    b->groups[g]->members.push_back(static_cast<int>(i));
+  }
+  for (auto& gp : b->groups) {
+    Group& g = *gp;
+    std::vector<lp_ctx*> src;
+    for (int i : g.members) {
+      src.push_back(b->inst[i]->q.ctx);
+      const std::vector<double>& y = b->inst[i]->q.y0;
+      g.y0.insert(g.y0.end(), y.begin(), y.end());
+    }
+    lp_status st = lp_create(&g.ctx, b->device, 0, nullptr);
+    if (st) {
+      drop_groups(b);
+      return bfail(b, st, lp_last_error(nullptr));
+    }
+    if (cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.ready, cudaEventDisableTiming) != cudaSuccess) {
+      (void)cudaGetLastError();
+      drop_groups(b);
+      return bfail(b, LP_ERR_CUDA, "creating the group's events");
+    }
+    if ((st = lp::load_merged(g.ctx, src.data(), static_cast<int>(src.size()))) ||
+        (b->tuned && (st = lp_autotune(g.ctx, b->inst[g.members[0]]->q.k, nullptr, nullptr, nullptr)))) {
+      const std::string msg = lp_last_error(g.ctx);
+      drop_groups(b);
+      return bfail(b, st, msg);
+    }
+  }
+  b->grouped = true;
+  return LP_OK;
 }
 
 }  // namespace
@@ -350,6 +434,9 @@ lp_status lp_batch_add(lp_batch* b, const lp_request* q, int* index) {
       q->T < 0 || q->refine_rounds < 0 || q->T + q->refine_rounds < 1 || (q->T > 0 && !q->p_schedule) ||
       (q->row_pitch != 0 && q->row_pitch < q->d) || (q->dtype == LP_FP8_E4M3 && !q->row_scales))
     return bfail(b, LP_ERR_INVALID, "malformed request");
+  if (q->flags & LP_FLAG_TRACE) return bfail(b, LP_ERR_INVALID, "LP_FLAG_TRACE is not available in a batch");
+  for (int t = 0; t < q->T; ++t)
+    if (q->p_schedule[t] < 1) return bfail(b, LP_ERR_INVALID, "p_schedule entries must be >= 1");
   auto in = std::make_unique<Inst>();
   Request& r = in->q;
   r.m = q->m;
@@ -368,26 +455,26 @@ lp_status lp_batch_add(lp_batch* b, const lp_request* q, int* index) {
   if (q->T > 0) r.sched.assign(q->p_schedule, q->p_schedule + q->T);
   r.y0.assign(q->y0, q->y0 + size_t(q->d) * q->k);
   r.est = lp::estimate_bytes(b->sms, r.m, r.rows.data(), r.d, r.pitch, r.dtype, r.k, r.space);
-  if (b->budget && b->in_use + r.est > b->budget)
+  // the instance's own copy and its share of its group's context
+  if (b->budget && b->in_use + 2 * r.est > b->budget)
     return bfail(b, LP_ERR_OOM, "instance does not fit the batch's HBM budget");
-  lp_status st = lp_create(&in->ctx, b->device, r.est, nullptr);
+  lp_status st = lp_create(&r.ctx, b->device, r.est, nullptr);
   if (st) return bfail(b, st, lp_last_error(nullptr));
-  st = lp::load_pitched(in->ctx, r.m, r.rows.data(), r.d, r.pitch, r.dtype, r.parts.data(),
+  st = lp::load_pitched(r.ctx, r.m, r.rows.data(), r.d, r.pitch, r.dtype, r.parts.data(),
                         r.dtype == LP_FP8_E4M3 ? r.scales.data() : nullptr, r.space);
-  if (!st && (cudaEventCreateWithFlags(&in->join, cudaEventDisableTiming) != cudaSuccess ||
-              cudaEventCreateWithFlags(&in->ready, cudaEventDisableTiming) != cudaSuccess)) {
-    (void)cudaGetLastError();
-    st = LP_ERR_CUDA;
+  if (!st) {
+    // the checks a solve would make, now (a group would report them for all its instances)
+    const int64_t smin = *std::min_element(r.rows.begin(), r.rows.end());
+    if (r.k > smin) st = LP_ERR_INVALID;
   }
   if (st) {
-    const std::string msg = lp_last_error(in->ctx);
-    if (in->join) cudaEventDestroy(in->join);
-    if (in->ready) cudaEventDestroy(in->ready);
-    lp_destroy(in->ctx);
+    const std::string msg = st == LP_ERR_INVALID && r.ctx ? std::string("k exceeds the smallest partition") :
+                                                            std::string(lp_last_error(r.ctx));
+    lp_destroy(r.ctx);
     return bfail(b, st, msg);
   }
-  b->in_use += r.est;
-  drop_batch_graph(b);
+  b->in_use += 2 * r.est;
+  drop_groups(b);
   *index = static_cast<int>(b->inst.size());
   b->inst.push_back(std::move(in));
   return LP_OK;
@@ -396,12 +483,10 @@ lp_status lp_batch_add(lp_batch* b, const lp_request* q, int* index) {
 lp_status lp_batch_autotune(lp_batch* b) {
   if (!b) return LP_ERR_INVALID;
   b->err.clear();
-  for (auto& in : b->inst) {
-    const lp_status st = lp_autotune(in->ctx, in->q.k, nullptr, nullptr, nullptr);
-    if (st) return bfail(b, st, lp_last_error(in->ctx));
-  }
-  drop_batch_graph(b);
-  return LP_OK;
+  if (b->inst.empty()) return bfail(b, LP_ERR_STATE, "empty batch");
+  b->tuned = true;
+  drop_groups(b);
+  return build_groups(b);
 }
 
 lp_status lp_batch_solve(lp_batch* b) {
@@ -418,14 +503,17 @@ lp_status lp_batch_solve(lp_batch* b) {
     return bfail(b, LP_ERR_CUDA, "waiting for the previous batch solve");
   }
   b->solved = false;
+  lp_status st = build_groups(b);
+  if (st) return st;
   // start blocks in; the graph waits for every upload
-  for (auto& in : b->inst) {
-    const Request& r = in->q;
-    lp_status st = lp::batch_prepare(in->ctx, r.k, r.sched.empty() ? nullptr : r.sched.data(), r.T, r.agg,
-                                     r.y0.data(), r.refine, r.flags);
-    if (st) return bfail(b, st, lp_last_error(in->ctx));
-    if (cudaEventRecord(in->ready, lp::ctx_stream(in->ctx)) != cudaSuccess ||
-        cudaStreamWaitEvent(b->root, in->ready, 0) != cudaSuccess) {
+  for (auto& gp : b->groups) {
+    Group& g = *gp;
+    const Request& r = b->inst[g.members[0]]->q;
+    st = lp::batch_prepare(g.ctx, r.k, r.sched.empty() ? nullptr : r.sched.data(), r.T, r.agg, g.y0.data(), r.refine,
+                           r.flags);
+    if (st) return bfail(b, st, lp_last_error(g.ctx));
+    if (cudaEventRecord(g.ready, lp::ctx_stream(g.ctx)) != cudaSuccess ||
+        cudaStreamWaitEvent(b->root, g.ready, 0) != cudaSuccess) {
       (void)cudaGetLastError();
       return bfail(b, LP_ERR_CUDA, "ordering the uploads");
     }
@@ -433,33 +521,33 @@ lp_status lp_batch_solve(lp_batch* b) {
   if (!b->exec) {
     cudaError_t e = cudaStreamBeginCapture(b->root, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->root);
-    lp_status st = LP_OK;
-    for (size_t i = 0; e == cudaSuccess && !st && i < b->inst.size(); ++i) {
-      Inst& in = *b->inst[i];
-      const Request& r = in.q;
-      cudaStream_t s = lp::ctx_stream(in.ctx);
+    st = LP_OK;
+    for (size_t i = 0; e == cudaSuccess && !st && i < b->groups.size(); ++i) {
+      Group& g = *b->groups[i];
+      const Request& r = b->inst[g.members[0]]->q;
+      cudaStream_t s = lp::ctx_stream(g.ctx);
       e = cudaStreamWaitEvent(s, b->fork, 0);
       if (e != cudaSuccess) break;
-      st = lp::batch_enqueue(in.ctx, r.k, r.sched.empty() ? nullptr : r.sched.data(), r.T, r.agg, r.refine, r.flags,
-                             &in.captured);
+      st = lp::batch_enqueue(g.ctx, r.k, r.sched.empty() ? nullptr : r.sched.data(), r.T, r.agg, r.refine, r.flags,
+                             &g.captured);
       if (st) {
-        b->err = lp_last_error(in.ctx);
+        b->err = lp_last_error(g.ctx);
         break;
       }
-      e = cudaEventRecord(in.join, s);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->root, in.join, 0);
+      e = cudaEventRecord(g.join, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->root, g.join, 0);
     }
-    cudaGraph_t g = nullptr;
-    const cudaError_t ee = cudaStreamEndCapture(b->root, &g);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->root, &gr);
     if (st || e != cudaSuccess || ee != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
+      if (gr) cudaGraphDestroy(gr);
       (void)cudaGetLastError();
       if (st) return st;
       return bfail(b, LP_ERR_CUDA, std::string("capturing the batch: ") +
                                        cudaGetErrorString(e != cudaSuccess ? e : ee));
     }
-    e = cudaGraphInstantiate(&b->exec, g, 0);
-    cudaGraphDestroy(g);
+    e = cudaGraphInstantiate(&b->exec, gr, 0);
+    cudaGraphDestroy(gr);
     if (e != cudaSuccess) {
       b->exec = nullptr;
       (void)cudaGetLastError();
@@ -470,7 +558,10 @@ lp_status lp_batch_solve(lp_batch* b) {
     (void)cudaGetLastError();
     return bfail(b, LP_ERR_CUDA, "launching the batch graph");
   }
-  for (auto& in : b->inst) lp::batch_mark(in->ctx, in->q.k, in->captured, in->q.T + in->q.refine, in->q.flags);
+  for (auto& gp : b->groups) {
+    const Request& r = b->inst[gp->members[0]]->q;
+    lp::batch_mark(gp->ctx, r.k, gp->captured, r.T + r.refine, r.flags);
+  }
   b->solved = true;
   return LP_OK;
 }
@@ -484,13 +575,16 @@ lp_status lp_batch_result(lp_batch* b, int index, double* z_out, double* sigma_o
     (void)cudaGetLastError();
     return bfail(b, LP_ERR_CUDA, "waiting for the batch");
   }
-  lp_ctx* c = b->inst[index]->ctx;
-  const lp_status st = lp_result(c, z_out, sigma_out, stats);
+  const Inst& in = *b->inst[index];
+  lp_ctx* c = b->groups[in.group]->ctx;
+  const lp_status st = lp::problem_result(c, in.problem, z_out, sigma_out, stats);
   if (st) b->err = lp_last_error(c);
   return st;
 }
 
 int lp_batch_size(const lp_batch* b) { return b ? static_cast<int>(b->inst.size()) : 0; }
+
+int lp_batch_groups(const lp_batch* b) { return b && b->grouped ? static_cast<int>(b->groups.size()) : 0; }
 
 const char* lp_batch_error(const lp_batch* b) { return b ? b->err.c_str() : ""; }
 
@@ -498,12 +592,8 @@ void lp_batch_destroy(lp_batch* b) {
   if (!b) return;
   cudaSetDevice(b->device);
   if (b->root) cudaStreamSynchronize(b->root);
-  drop_batch_graph(b);
-  for (auto& in : b->inst) {
-    if (in->join) cudaEventDestroy(in->join);
-    if (in->ready) cudaEventDestroy(in->ready);
-    lp_destroy(in->ctx);
-  }
+  drop_groups(b);
+  for (auto& in : b->inst) lp_destroy(in->q.ctx);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->root) cudaStreamDestroy(b->root);
   delete b;

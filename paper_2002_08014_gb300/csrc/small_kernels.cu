@@ -494,14 +494,18 @@ __global__ void __launch_bounds__(kT) cholqr2_kernel(const float* __restrict__ Y
 // ---------------------------------------------------------------- align
 // One CTA per partition.  G_i (K x K float, row-major) = D_i (sign) or O_i (OPT).
 __global__ void __launch_bounds__(kT) align_kernel(const float* __restrict__ Zl, int64_t z_stride,
-                                                   const float* __restrict__ Zb, int d, int k, int K, int base,
-                                                   int opt, int f64, float* __restrict__ Gout, int* status) {
+                                                   const float* __restrict__ Zb_one, int d, int k, int K,
+                                                   int base_one, const int* __restrict__ part_base, int opt, int f64,
+                                                   float* __restrict__ Gout, int* status) {
   extern __shared__ __align__(16) unsigned char sm[];
   double* C = reinterpret_cast<double*>(sm);   // K*K
   double* V = C + K * K;                        // K*K
   double* part = V + K * K;                     // kT doubles
   const int i = blockIdx.x;
   const int t = threadIdx.x;
+  // the base of partition i's problem: one for the context, or per partition (batch groups)
+  const int base = part_base ? part_base[i] : base_one;
+  const float* Zb = part_base ? Zl + z_stride * base : Zb_one;
   float* Gi = Gout + int64_t(i) * K * K;
   if (i == base) {
     for (int e = t; e < K * K; e += kT) Gi[e] = ((e / K) == (e % K) && (e / K) < k) ? 1.f : 0.f;
@@ -680,13 +684,17 @@ __global__ void __launch_bounds__(kT) rho_kernel(const float* __restrict__ Zl, i
 // ---------------------------------------------------------------- aggregate
 __global__ void aggregate_kernel(const float* __restrict__ Yl, const float* __restrict__ w,
                                  const float* __restrict__ G, int diag_only, int m, int d, int K,
-                                 float* __restrict__ Y) {
+                                 const int* __restrict__ prob_begin, float* __restrict__ Y) {
   const int t = threadIdx.x;
   const int j = t % K;
   const int r = blockIdx.x * (kT / K) + t / K;
   if (r >= d) return;
+  // problem q = blockIdx.y sums its own partitions [i0, i1) into its own block of Y
+  const int q = blockIdx.y;
+  const int i0 = prob_begin ? prob_begin[q] : 0, i1 = prob_begin ? prob_begin[q + 1] : m;
+  Y += int64_t(q) * d * K;
   float acc = 0.f;
-  for (int i = 0; i < m; ++i) {
+  for (int i = i0; i < i1; ++i) {
     const float* yi = Yl + (int64_t(i) * d + r) * K;
     float v;
     if (G == nullptr) {
@@ -701,6 +709,17 @@ __global__ void aggregate_kernel(const float* __restrict__ Yl, const float* __re
     acc = fmaf(w[i], v, acc);
   }
   Y[int64_t(r) * K + j] = acc;
+}
+
+// Zl[i] = Z[part_prob[i]]: each partition's copy of its problem's d x K block
+// (batch groups, where the first step of a round multiplies per-problem bases).
+__global__ void broadcast_kernel(const float4* __restrict__ Z, const int* __restrict__ part_prob, int m,
+                                 int64_t blk4, float4* __restrict__ Zl) {
+  const int64_t total = int64_t(m) * blk4;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / blk4, off = e - i * blk4;
+    Zl[e] = Z[int64_t(part_prob[i]) * blk4 + off];
+  }
 }
 
 // ---------------------------------------------------------------- Ritz
@@ -877,16 +896,26 @@ cudaError_t launch_cholqr2(const float* Y, float* Z, int batch, int d, int k, in
 }
 
 cudaError_t launch_align(const float* Zl, int64_t z_stride, const float* Zb, int m, int d, int k, int K, int base,
-                         lp_aggregator agg, float* G, int* status, cudaStream_t s, bool kxk_fp64) {
-  align_kernel<<<m, kT, align_smem(K), s>>>(Zl, z_stride, Zb, d, k, K, base, agg == LP_AGG_OPT ? 1 : 0,
+                         lp_aggregator agg, float* G, int* status, cudaStream_t s, bool kxk_fp64,
+                         const int* part_base) {
+  align_kernel<<<m, kT, align_smem(K), s>>>(Zl, z_stride, Zb, d, k, K, base, part_base, agg == LP_AGG_OPT ? 1 : 0,
                                             kxk_fp64 ? 1 : 0, G, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_aggregate(const float* Yl, const float* w, const float* G, int diag_only, int m, int d, int K,
-                             float* Y, cudaStream_t s) {
+                             float* Y, cudaStream_t s, const int* prob_begin, int nprob) {
   const int rpb = kT / K;
-  aggregate_kernel<<<(d + rpb - 1) / rpb, kT, 0, s>>>(Yl, w, G, diag_only, m, d, K, Y);
+  aggregate_kernel<<<dim3((d + rpb - 1) / rpb, nprob), kT, 0, s>>>(Yl, w, G, diag_only, m, d, K, prob_begin, Y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_broadcast(const float* Z, const int* part_prob, int m, int d, int K, float* Zl, cudaStream_t s) {
+  const int64_t blk4 = int64_t(d) * K / 4;
+  const int64_t total = int64_t(m) * blk4;
+  const int blocks = static_cast<int>(std::min<int64_t>((total + kT - 1) / kT, 4096));
+  broadcast_kernel<<<blocks > 0 ? blocks : 1, kT, 0, s>>>(reinterpret_cast<const float4*>(Z), part_prob, m, blk4,
+                                                          reinterpret_cast<float4*>(Zl));
   return cudaGetLastError();
 }
 
