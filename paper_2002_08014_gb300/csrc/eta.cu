@@ -253,8 +253,7 @@ cudaError_t launch_deviations(float* Mall, const float* w, int m, int d, cudaStr
 
 cudaError_t launch_lanczos_norms(const float* Mall, int nmat, int d, float* V, double* out, cudaStream_t s) {
   const size_t smem = lanczos_smem(d);
-  cudaError_t e = cudaFuncSetAttribute(lanczos_norms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem));
+  cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(lanczos_norms_kernel));
   if (e != cudaSuccess) return e;
   lanczos_norms_kernel<<<nmat, kLzThreads, smem, s>>>(Mall, d, lanczos_steps(d), V, out);
   return cudaGetLastError();

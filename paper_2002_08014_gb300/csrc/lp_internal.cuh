@@ -25,6 +25,14 @@ struct Segment {
   int slot;            // output slot of the CTA's partial A_i^T A_i Z_i
 };
 
+// Lets every launch of `kern` request up to the device's opt-in shared memory per
+// block, less the kernel's static shared memory (once per kernel).  The limit is
+// a property of the function, not of a launch: set to each plan's own size, a
+// smaller plan of another context (same kernel, another shape) would lower it
+// under a larger launch already captured in a graph, and that launch would be
+// rejected when the graph replays.
+cudaError_t allow_max_dynamic_smem(const void* kern);
+
 // ---- fused local power step (SIMT) ---------------------------------------
 struct StepArgs {
   const void* A;          // packed partitions, row pitch `ld` elements

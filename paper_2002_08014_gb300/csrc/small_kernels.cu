@@ -15,6 +15,8 @@
 // FP64) and its Cholesky, the Procrustes SVD and the Ritz eigen-solve.
 #include <algorithm>
 #include <cfloat>
+#include <mutex>
+#include <unordered_set>
 
 #include <cuda_bf16.h>
 
@@ -838,6 +840,23 @@ __global__ void ritz_rotate_kernel(const float* __restrict__ Z, const double* __
 }
 
 }  // namespace
+
+cudaError_t allow_max_dynamic_smem(const void* kern) {
+  static std::mutex mu;
+  static std::unordered_set<const void*> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(kern)) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - static_cast<int>(fa.sharedSizeBytes));
+  if (e == cudaSuccess) done.insert(kern);
+  return e;
+}
 
 cudaError_t launch_split_planes(const float* src, int64_t src_ld, int64_t rows, int d, uint16_t* hi, uint16_t* lo,
                                 int64_t ld, cudaStream_t s) {

@@ -523,8 +523,7 @@ cudaLaunchConfig_t pair_config(unsigned grid, size_t smem, cudaStream_t s, cudaL
 
 template <int K, int PL>
 int pair_active_clusters(size_t smem) {
-  if (cudaFuncSetAttribute(step_pair_kernel<K, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem)) != cudaSuccess) {
+  if (allow_max_dynamic_smem(reinterpret_cast<const void*>(step_pair_kernel<K, PL>)) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
   }
@@ -548,8 +547,7 @@ int pair_active_for(int K, int planes, size_t smem) {
 
 template <int K, int PL>
 cudaError_t launch_pair_t(const TcsPlan& p, const PairArgs& a, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(step_pair_kernel<K, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(p.smem));
+  cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(step_pair_kernel<K, PL>));
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = pair_config<K, PL>(static_cast<unsigned>(2 * p.nclusters), p.smem, s, attr);

@@ -515,7 +515,7 @@ constexpr size_t kSmemLimit2 = 227 * 1024;
 template <int K, int CPT, int R>
 cudaError_t launch_two(const StepArgs& a, const Geo2& g, size_t bytes, cudaStream_t s) {
   auto kern = step_simt2_kernel<K, CPT, R>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
   if (e != cudaSuccess) return e;
   kern<<<a.grid, kThreads2, bytes, s>>>(a, g);
   return cudaGetLastError();
@@ -577,7 +577,7 @@ cudaError_t launch_one(const StepArgs& a, cudaStream_t s) {
   const Geo g = make_geo(a.d, a.ld, R, K, sizeof(Tin));
   const size_t bytes = Smem<Tin, K, CPT, R>::bytes(g);
   auto kern = step_simt_kernel<Tin, K, CPT, R>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
   if (e != cudaSuccess) return e;
   kern<<<a.grid, kThreads, bytes, s>>>(a, g);
   return cudaGetLastError();

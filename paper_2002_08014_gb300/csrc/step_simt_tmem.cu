@@ -518,14 +518,13 @@ cudaError_t launch_step_simt_tmem(const StepArgs& a, cudaStream_t s) {
   if (!geo_tmem(a.d, a.ld, &g, &bytes)) return cudaErrorInvalidConfiguration;
   if (a.d == kD && a.ld == kD) {
     const size_t b3 = size_t(4) * (3 * kTile + 2 * kR * kK);
-    cudaError_t e = cudaFuncSetAttribute(step_simt_tmem_d1024_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(b3));
+    cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(step_simt_tmem_d1024_kernel));
     if (e != cudaSuccess) return e;
     step_simt_tmem_d1024_kernel<<<a.grid, kThr, b3, s>>>(a);
     return cudaGetLastError();
   }
   auto kern = a.d > kThr ? step_simt_tmem_kernel<2> : step_simt_tmem_kernel<1>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
+  cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
   if (e != cudaSuccess) return e;
   kern<<<a.grid, kThr, bytes, s>>>(a, g);
   return cudaGetLastError();

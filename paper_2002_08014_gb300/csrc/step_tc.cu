@@ -442,7 +442,7 @@ template <int K, int NCH>
 cudaError_t launch_tc_t(const TcPlan& p, const TcArgs& a, cudaStream_t s) {
   using L = TcLayout<K, NCH>;
   auto kern = step_tc_kernel<K, NCH>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::alloc_bytes);
+  cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(kern));
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(p.nclusters * p.cluster), 1, 1);
@@ -469,7 +469,7 @@ template <int K, int NCH>
 int active_clusters(int cl) {
   using L = TcLayout<K, NCH>;
   auto kern = step_tc_kernel<K, NCH>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::alloc_bytes) != cudaSuccess) {
+  if (allow_max_dynamic_smem(reinterpret_cast<const void*>(kern)) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
   }

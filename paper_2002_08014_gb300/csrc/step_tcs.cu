@@ -439,9 +439,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int K, int PL>
-cudaError_t set_smem_attr(size_t bytes) {
-  return cudaFuncSetAttribute(step_tcs_kernel<K, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(bytes));
+cudaError_t set_smem_attr(size_t) {
+  return allow_max_dynamic_smem(reinterpret_cast<const void*>(step_tcs_kernel<K, PL>));
 }
 
 template <int K, int PL>

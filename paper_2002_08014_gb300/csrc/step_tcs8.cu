@@ -463,8 +463,7 @@ cudaLaunchConfig_t tcs8_config(unsigned grid, int cl, size_t smem, cudaStream_t 
 
 template <int K>
 int tcs8_active_clusters(int cl, size_t smem) {
-  if (cudaFuncSetAttribute(step_tcs8_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
-      cudaSuccess) {
+  if (allow_max_dynamic_smem(reinterpret_cast<const void*>(step_tcs8_kernel<K>)) != cudaSuccess) {
     (void)cudaGetLastError();
     return 0;
   }
@@ -480,8 +479,7 @@ int tcs8_active_clusters(int cl, size_t smem) {
 
 template <int K>
 cudaError_t launch_tcs8_t(const TcsPlan& p, const Tcs8Args& a, cudaStream_t s) {
-  cudaError_t e =
-      cudaFuncSetAttribute(step_tcs8_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(p.smem));
+  cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(step_tcs8_kernel<K>));
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = tcs8_config<K>(static_cast<unsigned>(p.nclusters * p.cluster), p.cluster, p.smem, s, attr);
