@@ -209,6 +209,8 @@ KERNELS = {0: "step_simt2_kernel (SIMT FP32 fused A_i^T (A_i Z_i))",
 
 def _kernel(path, dtype="f32", d=1024, k=16):
     """Name of the step kernel a solve ran (lp_stats.path plus the shape for the SIMT path)."""
+    if path == 2 and dtype == "e4m3":
+        return "step_tcs8_kernel (tcgen05 streaming, E4M3 codes widened to FP16 in shared memory, row scales factored out)"
     if path != 0:
         return KERNELS[path]
     if dtype != "f32":
@@ -703,8 +705,9 @@ def run_kernels(args):
     """Each step kernel on one shape: one-step solves (a single fused-step launch
     each) per kernel, in a fixed order, for profiler captures and quick scans:
     SIMT FP32, streaming tcgen05 BF16, resident tcgen05 BF16, streaming tcgen05
-    on hi/lo planes of the FP32 data, then the pass-split pair kernel on BF16 and
-    on the hi/lo planes."""
+    on hi/lo planes of the FP32 data, the pass-split pair kernel on BF16 and on
+    the hi/lo planes, then the FP8-E4M3 tensor-core kernel on the codes and row
+    scales of the same rows."""
     import synth
     from paper_2002_08014_gb300 import binding as B
 
@@ -716,14 +719,18 @@ def run_kernels(args):
     parts = synth.split_rows(A, synth.partition_sizes(n, m))
     Y0 = synth.gaussian_start(d, k, 1)
     runs = [("f32", parts, 0, None), ("bf16", None, 0, "stream"), ("bf16", None, B.LP_FLAG_TC_RESIDENT, None),
-            ("f32_bf16x2", parts, 0, "stream"), ("bf16", None, 0, "pair"), ("f32_bf16x2", parts, 0, "pair")]
+            ("f32_bf16x2", parts, 0, "stream"), ("bf16", None, 0, "pair"), ("f32_bf16x2", parts, 0, "pair"),
+            ("e4m3", None, 0, None)]
     bits = [synth.f32_to_bf16_bits(p) for p in parts]
+    codes, scales = map(list, zip(*[synth.f32_to_e4m3_rowscaled(p) for p in parts]))
     out = {}
     for dtype, data, flags, kern in runs:
-        eb = 2 if dtype == "bf16" else 4
+        eb = {"bf16": 2, "e4m3": 1 + 4.0 / d}.get(dtype, 4)
         name = f"{dtype}{'_resident' if flags else ''}{'_' + kern if kern else ''}"
+        if data is None:
+            data = codes if dtype == "e4m3" else bits
         try:
-            with B.LocalPower(data if data is not None else bits, dtype=dtype) as lp:
+            with B.LocalPower(data, dtype=dtype, row_scales=scales if dtype == "e4m3" else None) as lp:
                 if kern:
                     B.lp_set_tuning(lp.ctx, kernel=kern)
                 tuned = (B.lp_autotune(lp.ctx, k) if args.autotune and dtype != "f32" and not flags and kern != "pair"
@@ -735,7 +742,7 @@ def run_kernels(args):
                     ms.append(st["ms_step_kernels"])
             best = min(ms[1:])
             out[name] = {
-                "kernel": _kernel(st["path"], dtype if dtype == "f32" else "bf16", d, k), "tuning": tuned,
+                "kernel": _kernel(st["path"], dtype if dtype in ("f32", "e4m3") else "bf16", d, k), "tuning": tuned,
                 "launch_ms": best, "gbs": n * d * eb / (best / 1e3) / 1e9}
         except Exception as e:
             out[name] = {"error": str(e)[:200]}
