@@ -328,86 +328,104 @@ __device__ void gram_fp64(const float* Y, int d, double* red, double* G) {
   __syncthreads();
 }
 
-// Right-looking Cholesky of G (k x k, stride K, FP64, overwritten) by one warp.
-// Writes L in FP32 (lower, stride K) and 1 / L[j][j] in FP32; returns false on breakdown.
+// One-warp right-looking Cholesky with the matrix in registers: lane l holds
+// column l (rows 0..K-1) of the symmetric Gram; at pivot j lane j scales its
+// column into L[:, j], the other lanes receive L[i][j] from lane j by shuffles,
+// lane l keeps L[l][j] when i reaches l and updates its rows i >= l:
+// G[i][l] -= L[i][j] L[l][j].  Every entry of the lower triangle sees the same
+// operations in the same order as the textbook shared-memory form; the upper
+// rows of a column (i < l) are never read.  No index arithmetic by k in the
+// inner loops (the shared-memory form divided by the trailing size for every
+// entry, which dominated CholQR2 at K = 32).
+
+// FP64 factor of the FP64 Gram G (k x k, stride K; not modified).  Writes L in FP32
+// (lower, stride K) and 1 / L[j][j] in FP32; returns false on breakdown (a pivot
+// that is not positive and finite is then taken as 1 so the kernel can finish).
 template <int K>
-__device__ bool warp_cholesky_rl(double* G, float* Lf, float* invd, int k) {
+__device__ bool warp_cholesky_rl(const double* G, float* Lf, float* invd, int k) {
   const int lane = threadIdx.x & 31;
+  double col[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) col[i] = (i < k && lane < k) ? G[i * K + lane] : 0.0;
   bool ok = true;
-  for (int j = 0; j < k; ++j) {
-    double piv = G[j * K + j];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    if (j >= k) continue;  // (not break: the loop stays unrolled, col[] in registers)
+    double piv = __shfl_sync(0xffffffffu, col[j], j);
     if (!(piv > 0.0) || !isfinite(piv)) {
       ok = false;
       piv = 1.0;
     }
     const double inv = rsqrt_nr(piv);
     const double ljj = piv * inv;
-    // column j below the diagonal
-    for (int i = j + 1 + lane; i < k; i += 32) G[i * K + j] *= inv;
-    if (lane == 0) {
-      G[j * K + j] = ljj;
+    if (lane == j) {
+      col[j] = ljj;
+#pragma unroll
+      for (int i = j + 1; i < K; ++i) col[i] *= inv;
       invd[j] = static_cast<float>(inv);
     }
-    __syncwarp();
-    // trailing update G[i][l] -= L[i][j] L[l][j] for j < l <= i < k
-    const int m = k - j - 1;
-    for (int e = lane; e < m * m; e += 32) {
-      const int i = j + 1 + e / m, l = j + 1 + e % m;
-      if (l <= i) G[i * K + l] -= G[i * K + j] * G[l * K + j];
+    double my = 0.0;  // L[lane][j], known once i reaches lane
+#pragma unroll
+    for (int i = j + 1; i < K; ++i) {
+      const double lij = __shfl_sync(0xffffffffu, col[i], j);
+      if (i == lane) my = lij;
+      if (lane > j && i >= lane) col[i] -= lij * my;
     }
-    __syncwarp();
   }
-  for (int e = lane; e < K * K; e += 32) {
-    const int i = e / K, l = e % K;
-    Lf[e] = (i < k && l <= i) ? static_cast<float>(G[e]) : 0.f;
+  if (lane < K) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) Lf[i * K + lane] = (i < k && lane <= i) ? static_cast<float>(col[i]) : 0.f;
   }
   __syncwarp();
   return ok;
 }
 
-// Right-looking Cholesky of the FP64 Gram in FP32 on one warp, written to Lf
-// (lower, stride K) and invd.  Returns false (and leaves the FP64 Gram intact for
-// warp_cholesky_rl) when a pivot is not above 1e-6 of the largest diagonal entry
-// or not finite: GB300's FP64 pipe is a small fraction of its FP32 pipe, and the
-// FP32 factor serves both CholQR passes whenever the Gram allows it (the column
-// space is that of Y for any invertible factor; the second pass restores
-// orthonormality).
+// FP32 factor of the FP64 Gram (read in FP32) on one warp, written to Lf (lower,
+// stride K) and invd.  Returns false (G untouched, for warp_cholesky_rl) when a
+// pivot is not above 1e-6 of the largest diagonal entry or not finite: GB300's
+// FP64 pipe is a small fraction of its FP32 pipe, and the FP32 factor serves both
+// CholQR passes whenever the Gram allows it (the column space is that of Y for
+// any invertible factor; the second pass restores orthonormality).
 template <int K>
 __device__ bool warp_cholesky_f32(const double* G, float* Lf, float* invd, int k) {
   const int lane = threadIdx.x & 31;
-  float dmax = 0.f;
-  for (int e = lane; e < K * K; e += 32) {
-    const int i = e / K, l = e % K;
-    const float v = (i < k && l < k) ? static_cast<float>(G[e]) : 0.f;
-    Lf[e] = v;
-    if (i == l && i < k) dmax = fmaxf(dmax, v);
-  }
+  float col[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) col[i] = (i < k && lane < k) ? static_cast<float>(G[i * K + lane]) : 0.f;
+  float dmax = lane < k ? static_cast<float>(G[lane * K + lane]) : 0.f;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-  __syncwarp();
   if (!(dmax > 0.f) || !isfinite(dmax)) return false;
   const float floor = 1e-6f * dmax;
-  for (int j = 0; j < k; ++j) {
-    const float piv = Lf[j * K + j];  // the same value in every lane
-    if (!(piv > floor) || !isfinite(piv)) return false;
+  bool good = true;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    if (j >= k || !good) continue;  // (not break / return: the loop stays unrolled, col[] in registers)
+    const float piv = __shfl_sync(0xffffffffu, col[j], j);
+    if (!(piv > floor) || !isfinite(piv)) {
+      good = false;
+      continue;
+    }
     const float ljj = sqrtf(piv);
     const float inv = 1.0f / ljj;
-    for (int i = j + 1 + lane; i < k; i += 32) Lf[i * K + j] *= inv;
-    __syncwarp();
-    if (lane == 0) {
-      Lf[j * K + j] = ljj;
+    if (lane == j) {
+      col[j] = ljj;
+#pragma unroll
+      for (int i = j + 1; i < K; ++i) col[i] *= inv;
       invd[j] = inv;
     }
-    const int m = k - j - 1;
-    for (int e = lane; e < m * m; e += 32) {
-      const int i = j + 1 + e / m, l = j + 1 + e % m;
-      if (l <= i) Lf[i * K + l] -= Lf[i * K + j] * Lf[l * K + j];
+    float my = 0.f;  // L[lane][j], known once i reaches lane
+#pragma unroll
+    for (int i = j + 1; i < K; ++i) {
+      const float lij = __shfl_sync(0xffffffffu, col[i], j);
+      if (i == lane) my = lij;
+      if (lane > j && i >= lane) col[i] -= lij * my;
     }
-    __syncwarp();
   }
-  for (int e = lane; e < K * K; e += 32) {
-    const int i = e / K, l = e % K;
-    if (l > i || i >= k) Lf[e] = 0.f;
+  if (!good) return false;
+  if (lane < K) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) Lf[i * K + lane] = (i < k && lane <= i) ? col[i] : 0.f;
   }
   __syncwarp();
   return true;
