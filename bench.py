@@ -64,6 +64,9 @@ def _args():
                          "kernels: every step kernel on one shape (--shape, --rows), one-step solves, for profiling; "
                          "batching: independent BF16 instances of mixed shapes solved by one graph launch; "
                          "rounds: rounds-to-accuracy and the residual error rho_t for constant p in {1, 2, 4, 8}")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="batching: after the timed solves, one more batch solve between cudaProfilerStart and "
+                         "cudaProfilerStop (for ncu --profile-from-start off); not timed")
     ap.add_argument("--rows", type=int, default=None,
                     help="override n (same spectrum and partition count): a smaller case for profiler captures")
     return ap.parse_args()
@@ -473,6 +476,13 @@ def run_batching(args):
             bt.result(0)               # waits for the whole batch
             ms.append((time.perf_counter() - t0) * 1e3)
         clk = clocks.stop()
+        if args.profile_solve:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            bt.solve()
+            bt.result(0)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
         outs = [bt.result(i) for i in range(len(inst))]
         n_groups = bt.groups()
         a_bytes = sum(o[2]["a_bytes"] for o in outs)
