@@ -191,9 +191,10 @@ def run_reference(args):
 # captures of the current kernels, keyed by (path, planes, cache hints, slice
 # columns, lag); other configurations report traffic as unknown.
 DRAM_RATIO = {(0, 0, 0, 0, 0): 1081.1 / 1073.7,    # SIMT FP32, Z_i in TMEM (n = 262,144)
-              (2, 1, 1, 0, 1): 2094.9 / 2048.0,    # streaming tcgen05, BF16, as autotuned (n = 1,000,000)
-              (2, 2, 1, 512, 1): 4496.9 / 4096.0,  # streaming tcgen05, hi/lo planes, as autotuned (n = 1,000,000)
               (3, 2, 0, 0, 0): 2120.4 / 2048.0}    # pass-split pair tcgen05, hi/lo planes (n = 500,000)
+# the precision workload's shape (d = 2,048, k = 32), from captures at n = 131,072 scaled by rows
+DRAM_RATIO_PRECISION = {"bf16": 552.866 / 536.871,   # streaming tcgen05 (profiles/step_tcs_bf16_d2048_k32.md)
+                        "e4m3": 275.163 / 268.960}   # FP8 tcgen05, codes + scales (profiles/step_tcs8_e4m3_d2048_k32.md)
 
 
 def _traffic(path, planes, tuning, launch_bytes, d=1024, k=16):
@@ -290,7 +291,9 @@ def run_lowprec(args):
             "gpu_launches": s["launches"], "e2e": None, "autotune": choice,
             "roofline": {"kernel": _kernel(s["path"], "bf16", c["d"], c["k"]), "bound": "hbm",
                          "achieved": gbs_k, "peak": hbm_peak, "unit": "GB/s", "frac": gbs_k / hbm_peak,
-                         "traffic": None, "launch_ms": s["step_ms"], "peak_source": f"{peak_src} HBM copy bandwidth"}}
+                         "traffic": (DRAM_RATIO_PRECISION["bf16"] * s["launch_bytes"] if s["path"] == 2 else None),
+                         "traffic_unit": "bytes per launch", "launch_ms": s["step_ms"],
+                         "peak_source": f"{peak_src} HBM copy bandwidth"}}
     line["orthonormality"] = float(np.abs(Z.T @ Z - np.eye(k)).max())
     line["sigma_top3"] = [float(x) for x in sig[:3]]
     line["kxk"] = {"precision": "fp64 (Gram/Cholesky of CholQR2, Procrustes SVD, Ritz eigen-solve)",
@@ -317,6 +320,9 @@ def run_lowprec(args):
                "speedup_solves_vs_bf16": s8["solves_per_s"] / s["solves_per_s"],
                "roofline": {"bound": "hbm", "achieved": gbs8, "peak": hbm_peak, "unit": "GB/s",
                             "frac": gbs8 / hbm_peak, "launch_ms": s8["step_ms"],
+                            "traffic": (DRAM_RATIO_PRECISION["e4m3"] * (s8["launch_bytes"] + 4.0 * c["n"])
+                                        if s8["path"] == 2 else None),
+                            "traffic_unit": "bytes per launch",
                             "algorithmic_bytes_per_launch": s8["launch_bytes"] + 4.0 * c["n"],
                             "peak_source": f"{peak_src} HBM copy bandwidth"},
                "autotune": choice8,
