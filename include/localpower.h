@@ -393,7 +393,9 @@ lp_status lp_batch_autotune(lp_batch* b);
 /* lp_batch_solve: every instance's solve, asynchronously, as one graph launch. */
 lp_status lp_batch_solve(lp_batch* b);
 
-/* lp_batch_result: waits for the batch, then lp_result of instance `index`. */
+/* lp_batch_result: waits for the batch, then lp_result of instance `index`:
+ * its basis and sigma; stats are its group's counters (rounds, launches, path,
+ * timings) with this instance's n, m and A bytes. */
 lp_status lp_batch_result(lp_batch* b, int index, double* z_out, double* sigma_out, lp_stats* stats);
 
 /* lp_batch_size: number of instances (0 for NULL). */

@@ -458,18 +458,16 @@ lp_status lp_batch_add(lp_batch* b, const lp_request* q, int* index) {
   // the instance's own copy and its share of its group's context
   if (b->budget && b->in_use + 2 * r.est > b->budget)
     return bfail(b, LP_ERR_OOM, "instance does not fit the batch's HBM budget");
+  // the check a solve would make, now (a group would report it for all its instances)
+  const int64_t smin = *std::min_element(r.rows.begin(), r.rows.end());
+  if (smin < 1) return bfail(b, LP_ERR_INVALID, "a partition has no rows");
+  if (r.k > smin) return bfail(b, LP_ERR_INVALID, "k exceeds the smallest partition");
   lp_status st = lp_create(&r.ctx, b->device, r.est, nullptr);
   if (st) return bfail(b, st, lp_last_error(nullptr));
   st = lp::load_pitched(r.ctx, r.m, r.rows.data(), r.d, r.pitch, r.dtype, r.parts.data(),
                         r.dtype == LP_FP8_E4M3 ? r.scales.data() : nullptr, r.space);
-  if (!st) {
-    // the checks a solve would make, now (a group would report them for all its instances)
-    const int64_t smin = *std::min_element(r.rows.begin(), r.rows.end());
-    if (r.k > smin) st = LP_ERR_INVALID;
-  }
   if (st) {
-    const std::string msg = st == LP_ERR_INVALID && r.ctx ? std::string("k exceeds the smallest partition") :
-                                                            std::string(lp_last_error(r.ctx));
+    const std::string msg = lp_last_error(r.ctx);
     lp_destroy(r.ctx);
     return bfail(b, st, msg);
   }

@@ -76,6 +76,12 @@ def test_batch_rejects_bad_input(gpu_lib):
         with pytest.raises(B.LPError) as e:
             bt.add(stored, 0, SCHED, "sign", y0)
         assert e.value.status == B.LP_ERR_INVALID
+        # k above the smallest partition's row count: rejected at add, with its reason
+        small = [stored[0][:5]] + list(stored[1:])
+        with pytest.raises(B.LPError) as e:
+            bt.add(small, 8, SCHED, "sign", y0)
+        assert e.value.status == B.LP_ERR_INVALID and "k exceeds" in str(e.value)
+        assert len(bt) == 0
 
 
 def _uneven_sizes(n, m, seed):
