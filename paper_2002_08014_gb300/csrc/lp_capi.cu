@@ -860,7 +860,7 @@ static lp_status ensure_tcs(lp_ctx* c, int k) {
         return fail(c, LP_ERR_UNSUPPORTED, "no streaming tensor-core plan for d=" + std::to_string(c->d));
       const uint16_t* hi = static_cast<const uint16_t*>(c->dA);
       const uint16_t* lo = c->planes == 2 ? hi + size_t(c->n) * c->ld : nullptr;
-      LP_CUDA(lp::tcs_encode_maps(hi, lo, c->n, static_cast<int>(c->d), c->ld, &p));
+      LP_CUDA(lp::tcs_encode_maps(hi, lo, c->n, static_cast<int>(c->d), c->ld, &p, p.pair != 0));
     }
     c->tcs_state[idx] = 1;
   }

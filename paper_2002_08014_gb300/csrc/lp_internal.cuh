@@ -98,6 +98,7 @@ struct TcsPlan {
   // FP8-E4M3 streaming kernel (step_tcs8.cu): codes staged by TMA, widened to FP16
   int fp8 = 0;         // 1: this plan is for step_tcs8_kernel
   int issuers = 1;     // streaming kernels: MMA-issuing threads (own partial D1 and ring slots each)
+  int map3d = 0;       // pair kernel: the maps are (64 columns, row, chunk), one box per unit
   int stage = 0;       // staging ring units (16 KB of codes each)
   uint32_t off_stage = 0;
   alignas(64) unsigned char tmap[2][128];  // CUtensorMaps of the planes
@@ -111,7 +112,10 @@ struct TcsTuning {
 // Fills the geometry for (d, k, planes).  False when the shape has no streaming kernel.
 bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan* p);
 // Encodes the tensor maps of the planes (plane1 may be NULL for one plane).
-cudaError_t tcs_encode_maps(const void* plane0, const void* plane1, int64_t n, int d, int64_t ld, TcsPlan* p);
+// unit_boxes: where d is a multiple of 64 and rows are unpadded, encode three-dimensional
+// maps whose one box covers a whole 128-column unit (p->map3d = 1; the pair kernel's loads).
+cudaError_t tcs_encode_maps(const void* plane0, const void* plane1, int64_t n, int d, int64_t ld, TcsPlan* p,
+                            bool unit_boxes = false);
 cudaError_t launch_step_tcs(const TcsPlan& p, const Segment* segs, const int* seg_ptr, const float* Z,
                             int64_t z_stride, float* P, int d, int* status, cudaStream_t s);
 // Pass-split pair kernel: the same product with the HBM pass and the L2 pass on

@@ -90,6 +90,7 @@ struct PairArgs {
   int nd2;    // rank 1 Y-slice buffers in TMEM (1 or 2)
   int hints;  // 1: rank 0 loads evict_last, rank 1 loads evict_first
   int prefetch;  // rank 0: units brought into L2 this far ahead of their load (0: none)
+  int map3d;     // 1: the maps are (64 columns, row, chunk) and one box brings a whole unit
   long long stall;  // test hook: > 0 makes rank 0's producer wait this many cycles on B_NEVER
   uint32_t off_Z, off_stage, off_bar, tmem0, tmem1;
 };
@@ -214,6 +215,10 @@ __global__ void __launch_bounds__(kPairThreads, 1)
       const int nt = tiles_of(s);
       auto prefetch_unit = [&](int q) {
         const int t2 = q / U, u2 = q % U, b2 = u2 / PL, pl2 = u2 % PL;
+        if (a.map3d) {
+          tma_prefetch_3d(pl2 ? &map1 : &map0, 0, static_cast<int>(sg.row0) + t2 * kBM, 2 * b2);
+          return;
+        }
         for (int j = 0; j < 2; ++j)
           tma_prefetch_2d(pl2 ? &map1 : &map0, 64 * (2 * b2 + j), static_cast<int>(sg.row0) + t2 * kBM);
       };
@@ -232,10 +237,17 @@ __global__ void __launch_bounds__(kPairThreads, 1)
           const int b = u / PL, pl = u % PL;
           const int row = static_cast<int>(sg.row0) + t * kBM;
           const CUtensorMap* map = pl ? &map1 : &map0;
-          for (int j = 0; j < 2; ++j) {
-            const uint32_t dst = su32(sRing + slot * kUnitBytes + j * kChunkBytes);
-            if (a.hints) tma_load_2d_hint(dst, map, 64 * (2 * b + j), row, &bar[B_RING0 + slot], policy);
-            else tma_load_2d(dst, map, 64 * (2 * b + j), row, &bar[B_RING0 + slot]);
+          if (a.map3d) {
+            // chunks 2b and 2b + 1 as one box (a chunk past d is out of range: zeros)
+            const uint32_t dst = su32(sRing + slot * kUnitBytes);
+            if (a.hints) tma_load_3d_hint(dst, map, 0, row, 2 * b, &bar[B_RING0 + slot], policy);
+            else tma_load_3d(dst, map, 0, row, 2 * b, &bar[B_RING0 + slot]);
+          } else {
+            for (int j = 0; j < 2; ++j) {
+              const uint32_t dst = su32(sRing + slot * kUnitBytes + j * kChunkBytes);
+              if (a.hints) tma_load_2d_hint(dst, map, 64 * (2 * b + j), row, &bar[B_RING0 + slot], policy);
+              else tma_load_2d(dst, map, 64 * (2 * b + j), row, &bar[B_RING0 + slot]);
+            }
           }
           // Test hook: after rank 0's first ring fill (copies in flight, MMAs started),
           // a wait that nothing can complete runs out its short limit and aborts.
@@ -628,6 +640,7 @@ cudaError_t launch_step_pair(const TcsPlan& p, const Segment* segs, const int* s
   a.nd2 = p.nd2;
   a.hints = p.hints;
   a.prefetch = p.prefetch;
+  a.map3d = p.map3d;
   a.stall = p.stall;
   a.off_Z = p.off_B1;
   a.off_stage = p.off_B2;

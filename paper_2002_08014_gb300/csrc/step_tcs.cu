@@ -557,7 +557,8 @@ bool tcs_plan(int d, int k, int planes, int sms, const TcsTuning& tune, TcsPlan*
   return p->nclusters >= 1;
 }
 
-cudaError_t tcs_encode_maps(const void* plane0, const void* plane1, int64_t n, int d, int64_t ld, TcsPlan* p) {
+cudaError_t tcs_encode_maps(const void* plane0, const void* plane1, int64_t n, int d, int64_t ld, TcsPlan* p,
+                            bool unit_boxes) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -568,6 +569,28 @@ cudaError_t tcs_encode_maps(const void* plane0, const void* plane1, int64_t n, i
   }
   static_assert(sizeof(CUtensorMap) <= sizeof(p->tmap[0]), "tensor map storage");
   const void* planes[2] = {plane0, plane1};
+  p->map3d = 0;
+  // One box per 128-column unit (both 64-column chunks): the matrix viewed as
+  // (column within a chunk, row, chunk), which stays inside every row only when
+  // d is a whole number of chunks and rows are not padded (ld == d).
+  if (unit_boxes && d % 64 == 0 && ld == d) {
+    bool ok = true;
+    for (int i = 0; i < 2 && ok; ++i) {
+      if (!planes[i]) continue;
+      cuuint64_t dims[3] = {64, static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(d / 64)};
+      cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld) * 2, 128};
+      cuuint32_t box[3] = {64, static_cast<cuuint32_t>(kBM), 2};
+      cuuint32_t estr[3] = {1, 1, 1};
+      ok = encode(reinterpret_cast<CUtensorMap*>(p->tmap[i]), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                  const_cast<void*>(planes[i]), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    if (ok) {
+      p->map3d = 1;
+      return cudaSuccess;
+    }
+  }
   for (int i = 0; i < 2; ++i) {
     if (!planes[i]) continue;
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(d), static_cast<cuuint64_t>(n)};
