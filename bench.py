@@ -191,7 +191,7 @@ def run_reference(args):
 # captures of the current kernels, keyed by (path, planes, cache hints, slice
 # columns, lag); other configurations report traffic as unknown.
 DRAM_RATIO = {(0, 0, 0, 0, 0): 1081.1 / 1073.7,    # SIMT FP32, Z_i in TMEM (n = 262,144)
-              (3, 2, 0, 0, 0): 2120.4 / 2048.0}    # pass-split pair tcgen05, hi/lo planes (n = 500,000)
+              (3, 2, 0, 0, 0): 2118.4 / 2048.0}    # pass-split pair tcgen05, hi/lo planes (n = 500,000)
 # the precision workload's shape (d = 2,048, k = 32), from captures at n = 131,072 scaled by rows
 DRAM_RATIO_PRECISION = {"bf16": 552.866 / 536.871,   # streaming tcgen05 (profiles/step_tcs_bf16_d2048_k32.md)
                         "e4m3": 275.163 / 268.960}   # FP8 tcgen05, codes + scales (profiles/step_tcs8_e4m3_d2048_k32.md)
