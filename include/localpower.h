@@ -360,8 +360,8 @@ void lp_server_destroy(lp_server* s);
  * the width d, the storage dtype, k, the schedule, the aggregator and the flags
  * form a group: their partitions are copied back to back into one group
  * context, and each step kind of the solve (the fused power step, the
- * reduction, the local and global CholQR2, the alignment, the aggregation) is
- * one launch over all of the group's instances; the step kernel is persistent
+ * reduction, the local and global CholQR2, the alignment, the aggregation, the
+ * Rayleigh-Ritz pass) is one launch over all of the group's instances; the step kernel is persistent
  * (one CTA or CTA pair per SM walking the row pieces of every partition of
  * every instance).  The graph holds each group's whole solve as an independent
  * branch; it is captured on the first lp_batch_solve and replayed by later ones

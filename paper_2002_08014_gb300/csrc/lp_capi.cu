@@ -86,6 +86,7 @@ struct lp_ctx {
   int* dPartProb = nullptr;   // partition -> problem
   int* dPartBase = nullptr;   // partition -> its problem's base partition
   int* dProbBegin = nullptr;  // nprob + 1 partition offsets
+  double* dProbN = nullptr;   // rows per problem (the Ritz values' scale)
 
   // per-round records (LP_FLAG_TRACE): Z_t blocks and per-partition residuals
   float* dTraceZ = nullptr;
@@ -276,6 +277,7 @@ void free_partitions(lp_ctx* c) {
   dfree(c, c->dPartProb, size_t(c->m) * 4);
   dfree(c, c->dPartBase, size_t(c->m) * 4);
   dfree(c, c->dProbBegin, (size_t(c->nprob) + 1) * 4);
+  dfree(c, c->dProbN, size_t(c->nprob) * 8);
   c->nprob = 1;
   c->prob_begin.clear();
   c->prob_n.clear();
@@ -743,6 +745,7 @@ lp_status lp::set_problems(lp_ctx* c, int nprob, const int* part_begin) {
   dfree(c, c->dPartProb, size_t(c->m) * 4);
   dfree(c, c->dPartBase, size_t(c->m) * 4);
   dfree(c, c->dProbBegin, (size_t(c->nprob) + 1) * 4);
+  dfree(c, c->dProbN, size_t(c->nprob) * 8);
   c->nprob = nprob;
   c->prob_begin.assign(part_begin, part_begin + nprob + 1);
   c->prob_n.assign(nprob, 0);
@@ -763,11 +766,13 @@ lp_status lp::set_problems(lp_ctx* c, int nprob, const int* part_begin) {
   c->base = part_base[0];
   lp_status st;
   if ((st = dalloc(c, &c->dPartProb, size_t(c->m) * 4)) || (st = dalloc(c, &c->dPartBase, size_t(c->m) * 4)) ||
-      (st = dalloc(c, &c->dProbBegin, (size_t(nprob) + 1) * 4)))
+      (st = dalloc(c, &c->dProbBegin, (size_t(nprob) + 1) * 4)) || (st = dalloc(c, &c->dProbN, size_t(nprob) * 8)))
     return st;
+  std::vector<double> prob_nd(c->prob_n.begin(), c->prob_n.end());
   LP_CUDA(cudaMemcpyAsync(c->dPartProb, part_prob.data(), size_t(c->m) * 4, cudaMemcpyHostToDevice, c->stream));
   LP_CUDA(cudaMemcpyAsync(c->dPartBase, part_base.data(), size_t(c->m) * 4, cudaMemcpyHostToDevice, c->stream));
   LP_CUDA(cudaMemcpyAsync(c->dProbBegin, part_begin, (size_t(nprob) + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+  LP_CUDA(cudaMemcpyAsync(c->dProbN, prob_nd.data(), size_t(nprob) * 8, cudaMemcpyHostToDevice, c->stream));
   LP_CUDA(cudaMemcpyAsync(c->dW, w.data(), size_t(c->m) * 4, cudaMemcpyHostToDevice, c->stream));
   LP_CUDA(cudaStreamSynchronize(c->stream));
   c->solved = false;
@@ -1012,15 +1017,26 @@ static lp_status solve_body(lp_ctx* c, int k, const int* p_schedule, int T, lp_a
                                                    multi ? c->dProbBegin : nullptr, NP),
                            "aggregate")))
       return st;
-    // the partials buffer is free again after the reduction: it holds the Ritz scratch
-    if (lp::ritz_scratch_bytes(d, K) > state_sizes(c, K).P) return fail(c, LP_ERR_INVALID, "Ritz scratch too small");
-    for (int q = 0; q < NP; ++q) {
-      if ((st = check_launch(c, lp::launch_ritz(c->dZ + q * zs, c->dMZ + q * zs, d, k, K, double(c->prob_n[q]),
-                                                c->dZout + size_t(q) * d * k, c->dSigma + size_t(q) * LP_MAX_K,
-                                                reinterpret_cast<double*>(c->dP), c->dStatus, c->stream, kxk64),
+    // the partials buffer is free again after the reduction: it holds the Ritz scratch,
+    // for all problems at once when it is large enough, else for one after another
+    const size_t P_bytes = state_sizes(c, K).P;
+    if (lp::ritz_scratch_bytes(d, K) > P_bytes) return fail(c, LP_ERR_INVALID, "Ritz scratch too small");
+    if (lp::ritz_scratch_bytes(d, K, NP) <= P_bytes) {
+      if ((st = check_launch(c, lp::launch_ritz(c->dZ, c->dMZ, d, k, K, double(c->prob_n[0]), c->dZout, c->dSigma,
+                                                reinterpret_cast<double*>(c->dP), c->dStatus, c->stream, kxk64, NP,
+                                                multi ? c->dProbN : nullptr),
                              "ritz")))
         return st;
       c->stats.kernel_launches += 2;  // launch_ritz runs three kernels
+    } else {
+      for (int q = 0; q < NP; ++q) {
+        if ((st = check_launch(c, lp::launch_ritz(c->dZ + q * zs, c->dMZ + q * zs, d, k, K, double(c->prob_n[q]),
+                                                  c->dZout + size_t(q) * d * k, c->dSigma + size_t(q) * LP_MAX_K,
+                                                  reinterpret_cast<double*>(c->dP), c->dStatus, c->stream, kxk64),
+                               "ritz")))
+          return st;
+        c->stats.kernel_launches += 2;
+      }
     }
   } else {
     if ((st = check_launch(c, lp::launch_unpack(c->dZ, c->dZout, NP, d, k, K, c->stream), "unpack"))) return st;

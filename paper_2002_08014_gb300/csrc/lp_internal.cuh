@@ -194,10 +194,14 @@ cudaError_t launch_aggregate(const float* Yl, const float* w, const float* G, in
 // Zl[i] = Z[part_prob[i]] for the m partitions' d x K blocks.
 cudaError_t launch_broadcast(const float* Z, const int* part_prob, int m, int d, int K, float* Zl, cudaStream_t s);
 // Ritz: H = Z^T MZ (FP64 sums), eig by Jacobi (FP64 when kxk_fp64, else FP32), Zout = Z W
-// (FP64), sigma = sqrt(n lambda).  Three launches; `scratch` holds ritz_scratch_bytes(d, K) bytes.
+// (FP64), sigma = sqrt(n lambda).  Three launches; `scratch` holds ritz_scratch_bytes(d, K,
+// nprob) bytes.  nprob problems at once: Z, MZ consecutive d x K blocks, Zout consecutive
+// d x k blocks, sigma LP_MAX_K apart, n_of (device, may be nullptr for one problem) their
+// row counts.
 cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, double n, double* Zout, double* sigma,
-                        double* scratch, int* status, cudaStream_t s, bool kxk_fp64);
-size_t ritz_scratch_bytes(int d, int K);
+                        double* scratch, int* status, cudaStream_t s, bool kxk_fp64, int nprob = 1,
+                        const double* n_of = nullptr);
+size_t ritz_scratch_bytes(int d, int K, int nprob = 1);
 // out[i] = ||Z_i G_i - Z_b||_2 (Def. 3), G_i the aligner (nullptr: none; diag_only: sign-fixing); out[base] = 0.
 cudaError_t launch_rho(const float* Zl, int64_t z_stride, const float* Zb, const float* G, int diag_only, int base,
                        int m, int d, int k, int K, double* out, int* status, cudaStream_t s);

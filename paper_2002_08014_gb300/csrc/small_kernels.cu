@@ -756,6 +756,10 @@ __global__ void __launch_bounds__(kT) ritz_partial_kernel(const float* __restric
   __shared__ float zs[kRitzRows * LP_MAX_K], ms[kRitzRows * LP_MAX_K];
   const int t = threadIdx.x;
   const int r0 = blockIdx.x * kRitzRows;
+  // problem blockIdx.y: its d x K blocks and its slices of the scratch
+  Z += int64_t(blockIdx.y) * d * K;
+  MZ += int64_t(blockIdx.y) * d * K;
+  Hpart += int64_t(blockIdx.y) * gridDim.x * K * K;
   const int nr = min(kRitzRows, d - r0);
   for (int e = t; e < nr * K; e += kT) {
     zs[e] = Z[int64_t(r0) * K + e];
@@ -773,9 +777,16 @@ __global__ void __launch_bounds__(kT) ritz_partial_kernel(const float* __restric
 }
 
 __global__ void __launch_bounds__(kT) ritz_solve_kernel(const double* __restrict__ Hpart, int slices, int k, int K,
-                                                        double n, int f64, double* __restrict__ Vo,
-                                                        double* __restrict__ sigma, int* status) {
+                                                        double n_one, const double* __restrict__ n_of, int f64,
+                                                        double* __restrict__ Vo, double* __restrict__ sigma,
+                                                        int* status) {
   extern __shared__ __align__(16) unsigned char sm[];
+  // problem blockIdx.x: its slices, its V and sigma, its row count
+  const int qp = blockIdx.x;
+  Hpart += int64_t(qp) * slices * K * K;
+  Vo += int64_t(qp) * K * K;
+  sigma += int64_t(qp) * LP_MAX_K;
+  const double n = n_of ? n_of[qp] : n_one;
   double* H = reinterpret_cast<double*>(sm);  // K*K
   double* V = H + K * K;                       // K*K
   double* lam = V + K * K;                     // K
@@ -848,10 +859,15 @@ __global__ void __launch_bounds__(kT) ritz_solve_kernel(const double* __restrict
 }
 
 __global__ void ritz_rotate_kernel(const float* __restrict__ Z, const double* __restrict__ Vo, int d, int k, int K,
-                                   double* __restrict__ Zout) {
+                                   int nprob, double* __restrict__ Zout) {
   const int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  if (e >= int64_t(d) * k) return;
-  const int r = static_cast<int>(e / k), j = static_cast<int>(e % k);
+  if (e >= int64_t(nprob) * d * k) return;
+  // problem q's d x k output block follows problem q - 1's
+  const int q = static_cast<int>(e / (int64_t(d) * k));
+  const int64_t el = e - int64_t(q) * d * k;
+  Z += int64_t(q) * d * K;
+  Vo += int64_t(q) * K * K;
+  const int r = static_cast<int>(el / k), j = static_cast<int>(el % k);
   double sum = 0.0;
   for (int l = 0; l < k; ++l) sum += static_cast<double>(Z[int64_t(r) * K + l]) * Vo[l * K + j];
   Zout[e] = sum;
@@ -957,18 +973,18 @@ cudaError_t launch_broadcast(const float* Z, const int* part_prob, int m, int d,
 }
 
 cudaError_t launch_ritz(const float* Z, const float* MZ, int d, int k, int K, double n, double* Zout, double* sigma,
-                        double* scratch, int* status, cudaStream_t s, bool kxk_fp64) {
+                        double* scratch, int* status, cudaStream_t s, bool kxk_fp64, int nprob, const double* n_of) {
   const int slices = (d + kRitzRows - 1) / kRitzRows;
   double* Hpart = scratch;
-  double* Vo = scratch + size_t(slices) * K * K;
-  ritz_partial_kernel<<<slices, kT, 0, s>>>(Z, MZ, d, k, K, Hpart);
+  double* Vo = scratch + size_t(nprob) * slices * K * K;
+  ritz_partial_kernel<<<dim3(slices, nprob), kT, 0, s>>>(Z, MZ, d, k, K, Hpart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t sm = size_t(2) * K * K * 8 + size_t(K) * 8 + size_t(K) * 4 + 16;
-  ritz_solve_kernel<<<1, kT, sm, s>>>(Hpart, slices, k, K, n, kxk_fp64 ? 1 : 0, Vo, sigma, status);
+  ritz_solve_kernel<<<nprob, kT, sm, s>>>(Hpart, slices, k, K, n, n_of, kxk_fp64 ? 1 : 0, Vo, sigma, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int64_t total = int64_t(d) * k;
-  ritz_rotate_kernel<<<static_cast<unsigned>((total + kT - 1) / kT), kT, 0, s>>>(Z, Vo, d, k, K, Zout);
+  const int64_t total = int64_t(nprob) * d * k;
+  ritz_rotate_kernel<<<static_cast<unsigned>((total + kT - 1) / kT), kT, 0, s>>>(Z, Vo, d, k, K, nprob, Zout);
   return cudaGetLastError();
 }
 
@@ -979,9 +995,9 @@ cudaError_t launch_rho(const float* Zl, int64_t z_stride, const float* Zb, const
   return cudaGetLastError();
 }
 
-size_t ritz_scratch_bytes(int d, int K) {
+size_t ritz_scratch_bytes(int d, int K, int nprob) {
   const int slices = (d + kRitzRows - 1) / kRitzRows;
-  return (size_t(slices) + 1) * K * K * 8;
+  return size_t(nprob) * (size_t(slices) + 1) * K * K * 8;
 }
 
 }  // namespace lp
