@@ -414,19 +414,22 @@ def _serving_requests(n_req: int, rate: float, seed: int):
                  seed=seed * 100_000 + i) for i in range(n_req)]
 
 
-def _width_pools(torch, local, seed, pool_rows):
+def _width_pools(torch, local, seed, pool_rows, fp32=False):
     """Device pools of spiked BF16 rows, one per width in SERVING_WIDTHS, each with
-    its own Haar rotation and lambda_j = 0.85^j (j <= width); host copies too."""
+    its own Haar rotation and lambda_j = 0.85^j (j <= width); host copies too.
+    fp32: also device pools of the FP32 rows the BF16 ones are rounded from."""
     import synth
-    bits, dev = {}, {}
+    bits, dev, dev32 = {}, {}, {}
     for wi, w in enumerate(SERVING_WIDTHS):
         lam = 0.85 ** np.arange(1, w + 1)
         rows = synth.spiked_rows(pool_rows, w, lam, 0.0, seed + 10 + wi, out_dtype=np.float32,
                                  threads=os.cpu_count())
         bits[w] = synth.f32_to_bf16_bits(rows)
         dev[w] = torch.from_numpy(bits[w].view(np.int16)).cuda(local)
+        if fp32:
+            dev32[w] = torch.from_numpy(rows).cuda(local)
         del rows
-    return bits, dev
+    return (bits, dev, dev32) if fp32 else (bits, dev)
 
 
 def run_batching(args):
@@ -614,7 +617,9 @@ def run_serving(args):
     the constant-p error floor that small, heterogeneous partitions leave.  Rows
     come from device-resident pools of spiked BF16 rows, one per width d, each
     with its own Haar rotation and lambda_j = 0.85^j (j <= d); a request names a
-    row range of the pool of its width."""
+    row range of the pool of its width.  Beside it: the same stream on the plain
+    FP32 path (the FP32 rows the BF16 pools are rounded from), and both paths with
+    every request submitted at once (the largest throughput each sustains)."""
     import torch
 
     import oracle
@@ -628,56 +633,64 @@ def run_serving(args):
     seed = synth.configs.SEED_BASE + 5
     reqs = _serving_requests(args.requests, args.rate, seed)
     pool_rows = 400_000
-    pool_bits, dev_pool = _width_pools(torch, local, seed, pool_rows)
+    pool_bits, dev_pool, dev_pool32 = _width_pools(torch, local, seed, pool_rows, fp32=True)
     orng = np.random.default_rng(seed + 1)
     for r in reqs:
         r["off"] = int(orng.integers(0, pool_rows - r["n"]))
     sched = SERVING_SCHEDULE
     budget = 120 << 30
-    lat, done_t, a_bytes = {}, {}, 0.0
-    clocks = Clocks(local)
-    with B.Server(device=local, hbm_budget_bytes=budget, max_active=64) as srv:
-        # warm-up: a few requests of the same kind, not timed
-        for r in reqs[:4]:
-            sizes = synth.partition_sizes(r["n"], r["m"])
-            offs = r["off"] + np.cumsum([0] + sizes[:-1])
-            parts = [dev_pool[r["d"]][o:o + s_] for o, s_ in zip(offs, sizes)]
-            rid = srv.submit(parts, r["k"], sched, "sign", synth.gaussian_start(r["d"], r["k"], r["seed"]),
-                             dtype="bf16", refine_rounds=3)
-            while rid not in srv.progress():
-                time.sleep(0.0005)
-            srv.result(rid)
-        torch.cuda.synchronize()
-        clocks.start()
-        t0 = time.perf_counter()
-        nxt, ids = 0, {}
-        peak = {"active": 0, "queued": 0}
-        while len(done_t) < len(reqs):
-            now = time.perf_counter() - t0
-            while nxt < len(reqs) and reqs[nxt]["t"] <= now:
-                r = reqs[nxt]
+
+    def serve(dtype, pools, saturated=False, clocks=None):
+        """The request stream through a server: arrivals at their Poisson times, or
+        all at once (saturated).  Returns per-request completion times (from the
+        arrival, or from the start when saturated), the A bytes, the wall time, the
+        peaks and the results."""
+        done_t, a_bytes, Zs = {}, 0.0, {}
+        with B.Server(device=local, hbm_budget_bytes=budget, max_active=64) as srv:
+            def submit(r):
                 sizes = synth.partition_sizes(r["n"], r["m"])
                 offs = r["off"] + np.cumsum([0] + sizes[:-1])
-                parts = [dev_pool[r["d"]][o:o + s_] for o, s_ in zip(offs, sizes)]
-                y0 = synth.gaussian_start(r["d"], r["k"], r["seed"])
-                ids[srv.submit(parts, r["k"], sched, "sign", y0, dtype="bf16", refine_rounds=3)] = nxt
-                nxt += 1
-            fin = srv.progress()
-            tnow = time.perf_counter() - t0
-            for rid in fin:
-                i = ids[rid]
-                done_t[i] = tnow
-                Z, sig, st = srv.result(rid)
-                a_bytes += st["a_bytes"]
-                reqs[i]["Z"] = Z
-            info = srv.query()
-            peak["active"] = max(peak["active"], info["active"])
-            peak["queued"] = max(peak["queued"], info["queued"])
-            if not fin:
-                time.sleep(0.0002)
-        wall = time.perf_counter() - t0
-        hbm_peak = srv.query()["hbm_peak"]
-    clk = clocks.stop()
+                parts = [pools[r["d"]][o:o + s_] for o, s_ in zip(offs, sizes)]
+                return srv.submit(parts, r["k"], sched, "sign", synth.gaussian_start(r["d"], r["k"], r["seed"]),
+                                  dtype=dtype, refine_rounds=3)
+            for r in reqs[:4]:  # warm-up: a few requests of the same kind, not timed
+                rid = submit(r)
+                while rid not in srv.progress():
+                    time.sleep(0.0005)
+                srv.result(rid)
+            torch.cuda.synchronize()
+            if clocks:
+                clocks.start()
+            t0 = time.perf_counter()
+            nxt, ids = 0, {}
+            peak = {"active": 0, "queued": 0}
+            while len(done_t) < len(reqs):
+                now = time.perf_counter() - t0
+                while nxt < len(reqs) and (saturated or reqs[nxt]["t"] <= now):
+                    ids[submit(reqs[nxt])] = nxt
+                    nxt += 1
+                fin = srv.progress()
+                tnow = time.perf_counter() - t0
+                for rid in fin:
+                    i = ids[rid]
+                    done_t[i] = tnow
+                    Z, sig, st = srv.result(rid)
+                    a_bytes += st["a_bytes"]
+                    Zs[i] = Z
+                info = srv.query()
+                peak["active"] = max(peak["active"], info["active"])
+                peak["queued"] = max(peak["queued"], info["queued"])
+                if not fin:
+                    time.sleep(0.0002)
+            wall = time.perf_counter() - t0
+            hbm_peak = srv.query()["hbm_peak"]
+        clk = clocks.stop() if clocks else None
+        return done_t, a_bytes, wall, peak, hbm_peak, Zs, clk
+
+    clocks = Clocks(local)
+    done_t, a_bytes, wall, peak, hbm_peak, Zs, clk = serve("bf16", dev_pool, clocks=clocks)
+    for i, Z in Zs.items():
+        reqs[i]["Z"] = Z
     lats = np.array([(done_t[i] - reqs[i]["t"]) * 1e3 for i in range(len(reqs))])
     span = max(done_t.values()) - reqs[0]["t"]
     # a sample of requests against the FP64 oracle run on the same decoded data and schedule
@@ -693,6 +706,26 @@ def run_serving(args):
         ref = oracle.localpower(synth.split_rows(rows, synth.partition_sizes(r["n"], r["m"])), r["k"],
                                 sched + [1, 1, 1], "sign", synth.gaussian_start(r["d"], r["k"], r["seed"]))
         acc_o.append(oracle.subspace_dist(oracle.orth(r["Z"]), ref["Z"]))
+    # the plain FP32 path on the same request stream (the FP32 rows the BF16 pools
+    # are rounded from), then both with every request submitted at once: the
+    # largest throughput each path sustains
+    d32, b32, wall32, peak32, _, Zs32, clk32 = serve("f32", dev_pool32, clocks=Clocks(local))
+    lats32 = np.array([(d32[i] - reqs[i]["t"]) * 1e3 for i in range(len(reqs))])
+    span32 = max(d32.values()) - reqs[0]["t"]
+    acc32 = []
+    for i in [cheap[j] for j in np.linspace(0, len(cheap) - 1, min(4, len(cheap))).astype(int)]:
+        r = reqs[i]
+        rows = dev_pool32[r["d"]][r["off"]:r["off"] + r["n"]].cpu().numpy().astype(np.float64)
+        w, V = np.linalg.eigh(rows.T @ rows / r["n"])
+        acc32.append(oracle.subspace_dist(oracle.orth(Zs32[i]), V[:, ::-1][:, :r["k"]]))
+    sat = {}
+    for dtype, pools in (("bf16", dev_pool), ("f32", dev_pool32)):
+        dsat, bsat, wsat, psat, _, _, _ = serve(dtype, pools, saturated=True)
+        lsat = np.array(list(dsat.values())) * 1e3
+        sat[dtype] = {"solves_per_s": len(reqs) / max(dsat.values()), "gbs": bsat / max(dsat.values()) / 1e9,
+                      "completion_ms": {"p50": float(np.percentile(lsat, 50)), "p99": float(np.percentile(lsat, 99))},
+                      "peak_active": psat["active"]}
+    sat["speedup_solves_bf16_vs_plain_fp32"] = sat["bf16"]["solves_per_s"] / sat["f32"]["solves_per_s"]
     line = {"metric": METRIC, "value": a_bytes / span / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": len(reqs),
             "warmup": 4, "ms_per_step": span * 1e3 / len(reqs), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
@@ -713,7 +746,18 @@ def run_serving(args):
                                 "dist_to_eigh_topk": [float(x) for x in acc],
                                 "max_dist_to_eigh_topk": float(max(acc)), "target": 1e-4,
                                 "met": bool(max(acc) <= 1e-4),
-                                "truth": "FP64 eigendecomposition of each sampled request's decoded BF16 matrix"}}
+                                "truth": "FP64 eigendecomposition of each sampled request's decoded BF16 matrix"},
+            "plain_fp32_serving": {"dtype": "f32 (SIMT FP32 step kernels)", "solves_per_s": len(reqs) / span32,
+                                   "gbs": b32 / span32 / 1e9,
+                                   "latency_ms": {"p50": float(np.percentile(lats32, 50)),
+                                                  "p99": float(np.percentile(lats32, 99)),
+                                                  "max": float(lats32.max()), "samples": len(lats32)},
+                                   "peak_active": peak32["active"], "clocks": clk32,
+                                   "accuracy_sample": {"dist_to_eigh_topk": [float(x) for x in acc32],
+                                                       "max_dist_to_eigh_topk": float(max(acc32)),
+                                                       "met": bool(max(acc32) <= 1e-4),
+                                                       "truth": "FP64 eigendecomposition of the FP32 rows"}},
+            "saturated": sat}
     print(json.dumps(line))
 
 
