@@ -376,6 +376,18 @@ def run_plain(args):
         lp.result(k)
     ms, stats, Z, sig, clk = _timed(torch, dist, world, dev, stream, lp, k, sched, "sign", solves, Clocks(local))
     s = _summary(world, solves, ms, stats, 4, c)
+    # the other two aligners of eq. (3) on the same solves (latency and launches)
+    others = {}
+    for agg in ("opt", "identity"):
+        for _ in range(max(args.warmup, 3)):
+            lp.submit(k, sched, agg, Y0, ritz=True, timing=True)
+            lp.result(k)
+        ms_a, st_a, Za, _, clk_a = _timed(torch, dist, world, dev, stream, lp, k, sched, agg, solves, Clocks(local))
+        sa = _summary(world, solves, ms_a, st_a, 4, c)
+        ref_a = oracle.localpower(parts, k, sched, agg, Y0)
+        others[agg] = {"solves_per_s": sa["solves_per_s"], "latency_ms": sa["latency_ms"],
+                       "launches_per_solve": sa["launches"] / solves, "clocks": clk_a,
+                       "dist_to_oracle": oracle.subspace_dist(oracle.orth(Za), ref_a["Z"])}
     lp.close()
     ref = oracle.localpower(parts, k, sched, "sign", Y0)
     line = {"metric": METRIC, "value": s["gbs"], "unit": "GB/s", "n_gpus": world, "steps": solves,
@@ -384,7 +396,19 @@ def run_plain(args):
             "config": _config(c, sched, "plain"), "solves_per_s": s["solves_per_s"], "latency_ms": s["latency_ms"],
             "clocks": clk, "gpu_launches": s["launches"], "e2e": None,
             "launches_per_solve": s["launches"] / solves, "step_kernel": _kernel(s["path"], "f32", c["d"], c["k"]),
-            "dist_to_oracle": oracle.subspace_dist(oracle.orth(Z), ref["Z"])}
+            "dist_to_oracle": oracle.subspace_dist(oracle.orth(Z), ref["Z"]), "other_aggregators": others}
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, runs = _oracle_solves(parts, k, sched, "sign", Y0, 10.0)
+        rate1, runs1 = _oracle_solves(parts, k, sched, "sign", Y0, 10.0, one_thread=True)
+        solve_bytes = s["bytes_solve"] / 1e9     # algorithmic GB per solve (all step passes)
+        line["cpu_baseline"] = {"value": rate * solve_bytes, "unit": "GB/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "solves_per_s": rate,
+                                "sample": f"{runs} whole FP64 oracle solves (Alg. 1, sign-fixing, Ritz output) "
+                                          f"in about 10 s, NumPy's BLAS on all cores",
+                                "one_thread_solves_per_s": rate1,
+                                "one_thread_gbs": None if rate1 is None else rate1 * solve_bytes,
+                                "one_thread_sample": f"{runs1} whole oracle solves in about 10 s, BLAS limited "
+                                                     f"to one thread", **_cpu_info()}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -920,6 +944,41 @@ def _oracle_one_thread_gbps(parts, Y0) -> float | None:
         os.unlink(path)
 
 
+def _oracle_solves(parts, k, sched, agg, Y0, seconds: float, one_thread: bool = False):
+    """Whole oracle solves (Alg. 1 with Ritz output) repeated for about `seconds`;
+    returns (solves/s, solves run).  With one_thread, in a child process whose BLAS
+    is limited to one thread."""
+    if not one_thread:
+        import oracle
+        t = time.perf_counter()
+        runs = 0
+        while True:
+            r = oracle.localpower(parts, k, sched, agg, Y0)
+            oracle.ritz(parts, r["Z"])
+            runs += 1
+            if time.perf_counter() - t >= seconds:
+                return runs / (time.perf_counter() - t), runs
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    try:
+        np.savez(path, Y0=Y0, sched=np.asarray(sched), **{f"p{i}": p for i, p in enumerate(parts)})
+        code = ("import sys, time, numpy as np; sys.path.insert(0, %r); import oracle; f = np.load(%r); "
+                "P = [f['p%%d' %% i] for i in range(%d)]; s = [int(x) for x in f['sched']]; "
+                "t = time.perf_counter(); n = 0\n"
+                "while True:\n"
+                "    r = oracle.localpower(P, %d, s, %r, f['Y0']); oracle.ritz(P, r['Z']); n += 1\n"
+                "    if time.perf_counter() - t >= %r: break\n"
+                "print(n / (time.perf_counter() - t), n)") % (ROOT, path, len(parts), k, agg, seconds)
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+        rate, runs = out.stdout.strip().splitlines()[-1].split()
+        return float(rate), int(runs)
+    except Exception:
+        return None, 0
+    finally:
+        os.unlink(path)
+
+
 def run_ours(args):
     """The FP32 workload (the default).  Three runs of the same matrix, one after
     another on the device, each timed over K solves after W warm-up solves:
@@ -927,7 +986,8 @@ def run_ours(args):
                 2^-17 of the FP32 values), pass-split tcgen05 step: FP32-level results;
       plain     the FP32 data on the SIMT FP32 step (the plain FP32 path the metric
                 compares with);
-      bf16      the data rounded to BF16 (reduced precision), same tcgen05 step.
+      bf16      the data rounded to BF16 (reduced precision), same tcgen05 step;
+    and the headline again with the other aligner (sign-fixing and OPT both run).
     Each run's result is compared with the FP64 eigendecomposition of A^T A / n
     (the metric's accuracy bar is 1e-4), and a traced solve gives rounds to 1e-4."""
     import torch
@@ -952,17 +1012,18 @@ def run_ours(args):
     alu_peak = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12      # FP32 FMA lanes x 2 flop x max SM clock
     want_acc = rank == 0 and not args.no_accuracy
 
-    def run_path(data, dtype, elem_bytes):
+    def run_path(data, dtype, elem_bytes, agg=None):
+        agg = agg or args.agg
         lpx = B.LocalPower(data, dtype=dtype, device=local, stream=stream)
         for _ in range(args.warmup):
-            lpx.submit(k, sched, args.agg, Y0, ritz=True, timing=True)
+            lpx.submit(k, sched, agg, Y0, ritz=True, timing=True)
             lpx.result(k)
-        ms, stats, Z, sig, clk = _timed(torch, dist, world, dev, stream, lpx, k, sched, args.agg, args.steps,
+        ms, stats, Z, sig, clk = _timed(torch, dist, world, dev, stream, lpx, k, sched, agg, args.steps,
                                         Clocks(local))
         summ = _summary(world, args.steps, ms, stats, elem_bytes, c)
         ztrace = None
         if want_acc:  # one traced solve outside the timed region: Z_t after every round
-            B.lp_solve(lpx.ctx, k, sched, args.agg, Y0, 0, B.LP_FLAG_TRACE)
+            B.lp_solve(lpx.ctx, k, sched, agg, Y0, 0, B.LP_FLAG_TRACE)
             lpx.result(k)
             ztrace, _ = B.lp_trace(lpx.ctx, len(sched), d, k)
         lpx.close()
@@ -1013,6 +1074,10 @@ def run_ours(args):
                "pipelining": "two contexts: step i+1's host-to-device copy (FP32, split into planes on the "
                              "device) overlaps step i's solve; solves in sequence"}
 
+    # ---------------- the headline path with the other aligner (the workload runs both)
+    other = "opt" if args.agg == "sign" else "sign"
+    ho, Zo, sigo, clko, tr_o = run_path(parts, "f32_bf16x2", 4, agg=other)
+
     # ---------------- the plain FP32 path (SIMT FP32 step) and the BF16 copy
     f32, Zf, sigf, clkf, tr_f = run_path(parts, "f32", 4)
     Zb = None
@@ -1036,6 +1101,9 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": hl["launch_bytes"],
                          "peak_source": f"{peak_src} HBM copy bandwidth", "frac_of_nominal_8000": gbs_hl / 8000.0},
             "speedup_solves_vs_plain_fp32": hl["solves_per_s"] / f32["solves_per_s"],
+            "other_aggregator": {"aggregator": other, "solves_per_s": ho["solves_per_s"],
+                                 "ms_per_solve": ho["ms_per_solve"], "latency_ms": ho["latency_ms"],
+                                 "step_launch_ms": ho["step_ms"], "clocks": clko, "gpu_launches": ho["launches"]},
             "plain_fp32_path": {
                 "dtype": "f32", "step_kernel": _kernel(f32["path"], "f32", c["d"], c["k"]), "gbs": f32["gbs"],
                 "solves_per_s": f32["solves_per_s"], "ms_per_solve": f32["ms_per_solve"],
@@ -1072,6 +1140,7 @@ def run_ours(args):
         line["accuracy"] = acc_of(Z, sig, tr_hl)
         line["accuracy"]["dist_to_plain_fp32_output"] = oracle.subspace_dist(oracle.orth(Z), oracle.orth(Zf))
         line["plain_fp32_path"]["accuracy"] = acc_of(Zf, sigf, tr_f)
+        line["other_aggregator"]["accuracy"] = acc_of(Zo, sigo, tr_o)
         if Zb is not None:
             line["precision_path"]["accuracy"] = acc_of(Zb, sigb, tr_b)
             line["precision_path"]["accuracy"]["dist_to_plain_fp32_output"] = oracle.subspace_dist(

@@ -122,15 +122,8 @@ __global__ void reduce_kernel(const float* __restrict__ P, const int* __restrict
   reinterpret_cast<float4*>(Y + int64_t(i) * d * K)[e] = acc;
 }
 
-// ---------------------------------------------------------------- k x k helpers (warp 0)
+// ---------------------------------------------------------------- k x k helpers
 __device__ __forceinline__ float warp_sumf(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -156,51 +149,105 @@ template <> struct JacobiLimits<double> {
 // default because GB300's FP64 pipe is a small fraction of its FP32 pipe and
 // these k x k problems sit on serial critical paths (the aligners and Ritz
 // values stay within 1e-7 of FP64 factorisations on the FP32 workload's
-// spectrum); FP64 under LP_FLAG_KXK_FP64.  Returns false if the sweep limit was hit.
+// spectrum); FP64 under LP_FLAG_KXK_FP64.
+//
+// All kT threads of the CTA call it.  A sweep visits every column pair once in
+// the round-robin (circle) order: with np = k rounded up to even (the extra
+// column a dummy whose pairs are skipped), step s pairs column np - 1 with s and
+// (s + j) mod (np - 1) with (s - j) mod (np - 1) for j = 1 .. np/2 - 1, which
+// makes each step a set of disjoint pairs and each sweep np - 1 steps.  Pair
+// slot j of a step belongs to half-warp j; its 16 lanes hold rows h and h + 16
+// of the two columns, sum the three inner products over the half-warp and
+// rotate their rows.  One barrier per step; the sweeps stop when a whole sweep
+// rotated nothing.  Returns false if the sweep limit was hit.
 template <typename T>
-__device__ bool warp_jacobi(T* C, T* V, int k, int K) {
+__device__ bool cta_jacobi(T* C, T* V, int k, int K) {
   using L = JacobiLimits<T>;
-  const int lane = threadIdx.x & 31;
-  for (int r = lane; r < k; r += 32)
-    for (int j = 0; j < k; ++j) V[r * K + j] = (r == j) ? T(1) : T(0);
-  __syncwarp();
+  const int t = threadIdx.x;
+  const int slot = t >> 4, h = t & 15;
+  const int np = k + (k & 1);
+  for (int e = t; e < K * K; e += kT) V[e] = (e / K == e % K) ? T(1) : T(0);
+  __syncthreads();
   for (int sweep = 0; sweep < 40; ++sweep) {
     int rotated = 0;
-    for (int p = 0; p < k - 1; ++p) {
-      for (int q = p + 1; q < k; ++q) {
-        T a = 0, b = 0, g = 0;
-        if (lane < k) {
-          const T cp = C[lane * K + p], cq = C[lane * K + q];
-          a = cp * cp;
-          b = cq * cq;
-          g = cp * cq;
+    for (int s = 0; s < np - 1; ++s) {
+      int p = 0, q = 0;
+      bool live = slot < np / 2;
+      if (live) {
+        if (slot == 0) {
+          p = s;
+          q = np - 1;
+        } else {
+          p = (s + slot) % (np - 1);
+          q = (s - slot + np - 1) % (np - 1);
         }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
-        if (fabs(g) > L::tol * sqrt(a * b) && fabs(g) > L::tiny) {
-          rotated = 1;
-          // zeta = (b - a) / 2g, t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2)
-          const T zeta = (b - a) / (T(2) * g);
-          const T az = fabs(zeta);
-          const T t = (zeta >= T(0) ? T(1) : T(-1)) / (az > L::huge ? T(2) * az : az + sqrt(T(1) + zeta * zeta));
-          const T c = T(1) / sqrt(T(1) + t * t);
-          const T sn = c * t;
-          if (lane < k) {
-            const T cp = C[lane * K + p], cq = C[lane * K + q];
-            C[lane * K + p] = c * cp - sn * cq;
-            C[lane * K + q] = sn * cp + c * cq;
-            const T vp = V[lane * K + p], vq = V[lane * K + q];
-            V[lane * K + p] = c * vp - sn * vq;
-            V[lane * K + q] = sn * vp + c * vq;
-          }
-          __syncwarp();
+        live = p < k && q < k;
+      }
+      T a = 0, b = 0, g = 0;
+      if (live)
+        for (int r = h; r < k; r += 16) {
+          const T cp = C[r * K + p], cq = C[r * K + q];
+          a += cp * cp;
+          b += cq * cq;
+          g += cp * cq;
+        }
+      // every lane takes part in the shuffles; offsets below 16 stay in the half-warp
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        g += __shfl_xor_sync(0xffffffffu, g, o);
+      }
+      if (live && fabs(g) > L::tol * sqrt(a * b) && fabs(g) > L::tiny) {
+        rotated = 1;
+        // zeta = (b - a) / 2g, t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2)
+        const T zeta = (b - a) / (T(2) * g);
+        const T az = fabs(zeta);
+        const T tn = (zeta >= T(0) ? T(1) : T(-1)) / (az > L::huge ? T(2) * az : az + sqrt(T(1) + zeta * zeta));
+        const T c = T(1) / sqrt(T(1) + tn * tn);
+        const T sn = c * tn;
+        for (int r = h; r < k; r += 16) {
+          const T cp = C[r * K + p], cq = C[r * K + q];
+          C[r * K + p] = c * cp - sn * cq;
+          C[r * K + q] = sn * cp + c * cq;
+          const T vp = V[r * K + p], vq = V[r * K + q];
+          V[r * K + p] = c * vp - sn * vq;
+          V[r * K + q] = sn * vp + c * vq;
         }
       }
+      __syncthreads();
     }
-    if (!rotated) return true;
+    if (!__syncthreads_or(rotated)) return true;
   }
   return false;
+}
+
+// The orthogonal Procrustes factor O = U V^T of eq. (3) from a finished one-sided
+// Jacobi (C holds U Sigma, V the rotations): U's columns are normalised in
+// place, then O is formed entry by entry into Gi (K x K, zero beyond k).  A
+// column with no norm leaves O short of orthogonal and sets ST_JACOBI.  All
+// threads call it; `inv` holds K values of scratch.
+template <typename T>
+__device__ void procrustes_factor(T* C, const T* V, T* inv, int k, int K, float* Gi, int* status) {
+  const int t = threadIdx.x;
+  const T small = sizeof(T) == 8 ? T(1e-300) : T(1e-37);
+  if (t < k) {
+    T nrm = 0;
+    for (int r = 0; r < k; ++r) nrm += C[r * K + t] * C[r * K + t];
+    inv[t] = nrm > small ? T(1) / sqrt(nrm) : T(0);
+    if (!(nrm > small)) atomicOr(status, ST_JACOBI);
+  }
+  __syncthreads();
+  for (int e = t; e < k * K; e += kT)
+    if (e % K < k) C[e] *= inv[e % K];
+  __syncthreads();
+  for (int e = t; e < K * K; e += kT) {
+    const int a = e / K, b = e % K;
+    T sum = 0;
+    if (a < k && b < k)
+      for (int j = 0; j < k; ++j) sum = fma(C[a * K + j], V[b * K + j], sum);
+    Gi[e] = static_cast<float>(sum);
+  }
 }
 
 // ---------------------------------------------------------------- CholQR2
@@ -520,7 +567,7 @@ __global__ void __launch_bounds__(kT) align_kernel(const float* __restrict__ Zl,
   extern __shared__ __align__(16) unsigned char sm[];
   double* C = reinterpret_cast<double*>(sm);   // K*K
   double* V = C + K * K;                        // K*K
-  double* part = V + K * K;                     // kT doubles
+  double* part = V + K * K;                     // kT x 16 floats
   const int i = blockIdx.x;
   const int t = threadIdx.x;
   // the base of partition i's problem: one for the context, or per partition (batch groups)
@@ -553,78 +600,72 @@ __global__ void __launch_bounds__(kT) align_kernel(const float* __restrict__ Zl,
     }
     return;
   }
-  // OPT: C = Z_i^T Z_b (FP32 products, FP32 partial sums, FP64 combine), SVD by Jacobi.
-  const int NP = K * K;
-  const int RS = NP >= kT ? 1 : kT / NP;
-  const int PP = NP >= kT ? NP / kT : 1;
-  for (int pp = 0; pp < PP; ++pp) {
-    const int idx = t + kT * pp;
-    const int pair = idx % NP, sl = idx / NP;
-    const int a = pair / K, b = pair % K;
-    float s = 0.f;
-    if (sl < RS)
-      for (int r = sl; r < d; r += RS) s = fmaf(Zi[int64_t(r) * K + a], Zb[int64_t(r) * K + b], s);
-    if (RS > 1) part[t] = s;
-    else C[idx] = s;
-  }
-  __syncthreads();
-  if (RS > 1) {
-    if (t < NP) {
-      double s = 0.0;
-      for (int sl = 0; sl < RS; ++sl) s += part[sl * NP + t];
-      C[t] = s;
+  // OPT: C = Z_i^T Z_b.  Thread (4 x 4 block (bi, bj) of C, row slice sl) sums
+  // FP32 products of rows sl, sl + S, ... in FP32; the slices are added in FP64
+  // in slice order.  Then the Procrustes SVD by the CTA's Jacobi.
+  float* red = reinterpret_cast<float*>(part);  // kT x 16 partial blocks
+  {
+    const int NB = K / 4, NBB = NB * NB, S = kT / NBB;
+    const int blk = t % NBB, sl = t / NBB;
+    const int bi = blk / NB, bj = blk % NB;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    constexpr int U = 4;  // rows per trip, loads issued before the FMAs
+    for (int r0 = sl; r0 < d; r0 += S * U) {
+      float4 u[U], v[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int r = r0 + q * S;
+        u[q] = r < d ? *reinterpret_cast<const float4*>(Zi + int64_t(r) * K + 4 * bi) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[q] = r < d ? *reinterpret_cast<const float4*>(Zb + int64_t(r) * K + 4 * bj) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const float uu[4] = {u[q].x, u[q].y, u[q].z, u[q].w}, vv[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(uu[a], vv[b], acc[a][b]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) red[t * 16 + 4 * a + b] = acc[a][b];
+    __syncthreads();
+    for (int e = t; e < K * K; e += kT) {
+      const int a = e / K, b = e % K;
+      const int bb = (a / 4) * NB + b / 4, el = 4 * (a % 4) + b % 4;
+      double sum = 0.0;
+      for (int q = 0; q < S; ++q) sum += red[(q * NBB + bb) * 16 + el];
+      C[e] = sum;
     }
     __syncthreads();
   }
-  if (t < 32 && f64) {
+  if (f64) {
     // k x k Procrustes SVD in FP64 (LP_FLAG_KXK_FP64): C = U Sigma V^T, O = U V^T
-    const bool ok = warp_jacobi<double>(C, V, k, K);
+    const bool ok = cta_jacobi<double>(C, V, k, K);
     if (!ok && t == 0) atomicOr(status, ST_JACOBI);
-    for (int j = 0; j < k; ++j) {
-      double nrm = 0.0;
-      if (t < k) nrm = C[t * K + j] * C[t * K + j];
-      nrm = warp_sum(nrm);
-      const double inv = nrm > 1e-300 ? 1.0 / sqrt(nrm) : 0.0;
-      if (t < k) C[t * K + j] *= inv;
-      if (!(nrm > 1e-300) && t == 0) atomicOr(status, ST_JACOBI);
-    }
-    __syncwarp();
-    for (int e = t; e < K * K; e += 32) {
-      const int a = e / K, b = e % K;
-      double sum = 0.0;
-      if (a < k && b < k)
-        for (int j = 0; j < k; ++j) sum = fma(C[a * K + j], V[b * K + j], sum);
-      Gi[e] = static_cast<float>(sum);
-    }
-  } else if (t < 32) {
+    procrustes_factor<double>(C, V, part, k, K, Gi, status);
+  } else {
     // FP32 copies in the V area (2 K*K floats fit in K*K doubles)
     float* Cf = reinterpret_cast<float*>(V);
     float* Vf = Cf + K * K;
-    for (int e = t; e < K * K; e += 32) Cf[e] = static_cast<float>(C[e]);
-    __syncwarp();
-    const bool ok = warp_jacobi<float>(Cf, Vf, k, K);
+    for (int e = t; e < K * K; e += kT) Cf[e] = static_cast<float>(C[e]);
+    __syncthreads();
+    const bool ok = cta_jacobi<float>(Cf, Vf, k, K);
     if (!ok && t == 0) atomicOr(status, ST_JACOBI);
-    // U[:, j] = C[:, j] / sigma_j ; O = U V^T
-    for (int j = 0; j < k; ++j) {
-      float nrm = 0.f;
-      if (t < k) nrm = Cf[t * K + j] * Cf[t * K + j];
-      nrm = warp_sumf(nrm);  // squared norm
-      const float inv = nrm > 1e-37f ? 1.f / sqrtf(nrm) : 0.f;
-      if (t < k) Cf[t * K + j] *= inv;
-      if (!(nrm > 1e-37f) && t == 0) atomicOr(status, ST_JACOBI);
-    }
-    __syncwarp();
-    for (int e = t; e < K * K; e += 32) {
-      const int a = e / K, b = e % K;
-      float sum = 0.f;
-      if (a < k && b < k)
-        for (int j = 0; j < k; ++j) sum = fmaf(Cf[a * K + j], Vf[b * K + j], sum);
-      Gi[e] = sum;
-    }
+    procrustes_factor<float>(Cf, Vf, reinterpret_cast<float*>(part), k, K, Gi, status);
   }
 }
 
-size_t align_smem(int K) { return size_t(2) * K * K * 8 + size_t(kT) * 8 + 16; }
+// C and V (K x K doubles each), then the partial-block area (kT x 16 floats; it
+// also holds the column scales of the Procrustes factor, and the sign path's
+// kT doubles)
+size_t align_smem(int K) { return size_t(2) * K * K * 8 + size_t(kT) * 16 * 4 + 16; }
 
 // ---------------------------------------------------------------- residual error
 // rho_i = ||Z_i G_i - Z_b||_2 (Def. 3) for one partition per CTA: E = Z_i G_i - Z_b
@@ -682,14 +723,14 @@ __global__ void __launch_bounds__(kT) rho_kernel(const float* __restrict__ Zl, i
     if (e < K * K) C[e] = acc[q];
   }
   __syncthreads();
+  // E^T E is symmetric positive semidefinite: the one-sided Jacobi's column norms are its eigenvalues
+  float* Cf = reinterpret_cast<float*>(V);
+  float* Vf = Cf + K * K;
+  for (int e = t; e < K * K; e += kT) Cf[e] = static_cast<float>(C[e]);
+  __syncthreads();
+  const bool ok = cta_jacobi<float>(Cf, Vf, k, K);
+  if (!ok && t == 0) atomicOr(status, ST_JACOBI);
   if (t < 32) {
-    // E^T E is symmetric positive semidefinite: the one-sided Jacobi's column norms are its eigenvalues
-    float* Cf = reinterpret_cast<float*>(V);
-    float* Vf = Cf + K * K;
-    for (int e = t; e < K * K; e += 32) Cf[e] = static_cast<float>(C[e]);
-    __syncwarp();
-    const bool ok = warp_jacobi<float>(Cf, Vf, k, K);
-    if (!ok && t == 0) atomicOr(status, ST_JACOBI);
     float top = 0.f;
     for (int j = 0; j < k; ++j) {
       float v = 0.f;
@@ -702,33 +743,79 @@ __global__ void __launch_bounds__(kT) rho_kernel(const float* __restrict__ Zl, i
 }
 
 // ---------------------------------------------------------------- aggregate
-__global__ void aggregate_kernel(const float* __restrict__ Yl, const float* __restrict__ w,
-                                 const float* __restrict__ G, int diag_only, int m, int d, int K,
-                                 const int* __restrict__ prob_begin, float* __restrict__ Y) {
+// Y = sum_i w_i Y_i G_i over each problem's partitions (Alg. 1 aggregation; G_i
+// the aligner: K x K, diagonal for sign-fixing, or none).  Thread (slice sl,
+// row, group jg of four columns) sums the partitions i0 + sl, i0 + sl + S, ... in
+// order into four FP32 accumulators, then the S slices are added in slice order
+// through shared memory: a fixed summation order for a given S.  RPB = kT /
+// (S K/4) rows per CTA; problem q = blockIdx.y sums its own partitions
+// [i0, i1) into its own d x K block of Y.
+template <int K>
+__global__ void __launch_bounds__(kT) aggregate_kernel(const float* __restrict__ Yl, const float* __restrict__ w,
+                                                       const float* __restrict__ G, int diag_only, int m, int d, int S,
+                                                       const int* __restrict__ prob_begin, float* __restrict__ Y) {
+  constexpr int JG = K / 4;
+  __shared__ float4 red[kT];
   const int t = threadIdx.x;
-  const int j = t % K;
-  const int r = blockIdx.x * (kT / K) + t / K;
-  if (r >= d) return;
-  // problem q = blockIdx.y sums its own partitions [i0, i1) into its own block of Y
+  const int RPB = kT / (JG * S);
+  const int jg = t % JG, row = (t / JG) % RPB, sl = t / (JG * RPB);
+  const int r = blockIdx.x * RPB + row;
   const int q = blockIdx.y;
   const int i0 = prob_begin ? prob_begin[q] : 0, i1 = prob_begin ? prob_begin[q + 1] : m;
-  Y += int64_t(q) * d * K;
-  float acc = 0.f;
-  for (int i = i0; i < i1; ++i) {
-    const float* yi = Yl + (int64_t(i) * d + r) * K;
-    float v;
-    if (G == nullptr) {
-      v = yi[j];
-    } else if (diag_only) {
-      v = yi[j] * G[int64_t(i) * K * K + j * K + j];
-    } else {
-      const float* gi = G + int64_t(i) * K * K;
-      v = 0.f;
-      for (int l = 0; l < K; ++l) v = fmaf(yi[l], gi[l * K + j], v);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (r < d) {
+    for (int i = i0 + sl; i < i1; i += S) {
+      const float* yi = Yl + (int64_t(i) * d + r) * K;
+      float4 v;
+      if (G == nullptr) {
+        v = *reinterpret_cast<const float4*>(yi + 4 * jg);
+      } else if (diag_only) {
+        const float* gi = G + int64_t(i) * K * K + (4 * jg) * (K + 1);
+        const float4 y = *reinterpret_cast<const float4*>(yi + 4 * jg);
+        v = make_float4(y.x * gi[0], y.y * gi[K + 1], y.z * gi[2 * (K + 1)], y.w * gi[3 * (K + 1)]);
+      } else {
+        const float* gi = G + int64_t(i) * K * K + 4 * jg;
+        float yr[K];
+#pragma unroll
+        for (int l = 0; l < K; l += 4) {
+          const float4 y = *reinterpret_cast<const float4*>(yi + l);
+          yr[l] = y.x;
+          yr[l + 1] = y.y;
+          yr[l + 2] = y.z;
+          yr[l + 3] = y.w;
+        }
+        v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < K; ++l) {
+          const float4 g = *reinterpret_cast<const float4*>(gi + l * K);
+          v.x = fmaf(yr[l], g.x, v.x);
+          v.y = fmaf(yr[l], g.y, v.y);
+          v.z = fmaf(yr[l], g.z, v.z);
+          v.w = fmaf(yr[l], g.w, v.w);
+        }
+      }
+      const float wi = w[i];
+      acc.x = fmaf(wi, v.x, acc.x);
+      acc.y = fmaf(wi, v.y, acc.y);
+      acc.z = fmaf(wi, v.z, acc.z);
+      acc.w = fmaf(wi, v.w, acc.w);
     }
-    acc = fmaf(w[i], v, acc);
   }
-  Y[int64_t(r) * K + j] = acc;
+  red[t] = acc;
+  __syncthreads();
+  if (t < RPB * JG) {
+    const int row2 = t / JG, jg2 = t % JG;
+    const int r2 = blockIdx.x * RPB + row2;
+    float4 sum = red[t];
+    for (int s2 = 1; s2 < S; ++s2) {
+      const float4 o = red[(s2 * RPB + row2) * JG + jg2];
+      sum.x += o.x;
+      sum.y += o.y;
+      sum.z += o.z;
+      sum.w += o.w;
+    }
+    if (r2 < d) reinterpret_cast<float4*>(Y + int64_t(q) * d * K + int64_t(r2) * K)[jg2] = sum;
+  }
 }
 
 // Zl[i] = Z[part_prob[i]]: each partition's copy of its problem's d x K block
@@ -798,56 +885,51 @@ __global__ void __launch_bounds__(kT) ritz_solve_kernel(const double* __restrict
     H[e] = sum;
   }
   __syncthreads();
-  if (t < 32) {
-    // symmetrise
-    for (int e = t; e < K * K; e += 32) {
-      const int a = e / K, b = e % K;
-      if (a < b) {
-        const double v = 0.5 * (H[a * K + b] + H[b * K + a]);
-        H[a * K + b] = v;
-        H[b * K + a] = v;
-      }
+  // symmetrise: the thread of entry (a, b), a < b, writes both halves
+  for (int e = t; e < K * K; e += kT) {
+    const int a = e / K, b = e % K;
+    if (a < b) {
+      const double v = 0.5 * (H[a * K + b] + H[b * K + a]);
+      H[a * K + b] = v;
+      H[b * K + a] = v;
     }
-    __syncwarp();
-    // H is symmetric positive semidefinite: its one-sided Jacobi SVD is its
-    // eigendecomposition, in FP64 under LP_FLAG_KXK_FP64, else on FP32 copies in
-    // the V area.
-    if (f64) {
-      const bool ok = warp_jacobi<double>(H, V, k, K);
-      if (!ok && t == 0) atomicOr(status, ST_JACOBI);
-      for (int j = 0; j < k; ++j) {
-        double v = 0.0;
-        if (t < k) v = H[t * K + j] * H[t * K + j];
-        v = warp_sum(v);
-        if (t == 0) lam[j] = v > 0.0 ? sqrt(v) : 0.0;
-      }
-    } else {
-      float* Hf = reinterpret_cast<float*>(V);
-      float* Vf = Hf + K * K;
-      for (int e = t; e < K * K; e += 32) Hf[e] = static_cast<float>(H[e]);
-      __syncwarp();
-      const bool ok = warp_jacobi<float>(Hf, Vf, k, K);
-      if (!ok && t == 0) atomicOr(status, ST_JACOBI);
-      for (int j = 0; j < k; ++j) {
-        float v = 0.f;
-        if (t < k) v = Hf[t * K + j] * Hf[t * K + j];
-        v = warp_sumf(v);
-        if (t == 0) lam[j] = v > 0.f ? sqrt(static_cast<double>(v)) : 0.0;
-      }
+  }
+  __syncthreads();
+  // H is symmetric positive semidefinite: its one-sided Jacobi SVD is its
+  // eigendecomposition, in FP64 under LP_FLAG_KXK_FP64, else on FP32 copies in
+  // the V area.
+  if (f64) {
+    const bool ok = cta_jacobi<double>(H, V, k, K);
+    if (!ok && t == 0) atomicOr(status, ST_JACOBI);
+    if (t < k) {
+      double v = 0.0;
+      for (int r = 0; r < k; ++r) v += H[r * K + t] * H[r * K + t];
+      lam[t] = v > 0.0 ? sqrt(v) : 0.0;
     }
-    __syncwarp();
-    if (t == 0) {
-      for (int j = 0; j < k; ++j) order[j] = j;
-      for (int a = 0; a < k; ++a)
-        for (int b = a + 1; b < k; ++b)
-          if (lam[order[b]] > lam[order[a]]) {
-            const int tmp = order[a];
-            order[a] = order[b];
-            order[b] = tmp;
-          }
-      for (int j = 0; j < k; ++j) sigma[j] = sqrt(n * lam[order[j]]);
+  } else {
+    float* Hf = reinterpret_cast<float*>(V);
+    float* Vf = Hf + K * K;
+    for (int e = t; e < K * K; e += kT) Hf[e] = static_cast<float>(H[e]);
+    __syncthreads();
+    const bool ok = cta_jacobi<float>(Hf, Vf, k, K);
+    if (!ok && t == 0) atomicOr(status, ST_JACOBI);
+    if (t < k) {
+      float v = 0.f;
+      for (int r = 0; r < k; ++r) v += Hf[r * K + t] * Hf[r * K + t];
+      lam[t] = v > 0.f ? sqrt(static_cast<double>(v)) : 0.0;
     }
-    __syncwarp();
+  }
+  __syncthreads();
+  if (t == 0) {
+    for (int j = 0; j < k; ++j) order[j] = j;
+    for (int a = 0; a < k; ++a)
+      for (int b = a + 1; b < k; ++b)
+        if (lam[order[b]] > lam[order[a]]) {
+          const int tmp = order[a];
+          order[a] = order[b];
+          order[b] = tmp;
+        }
+    for (int j = 0; j < k; ++j) sigma[j] = sqrt(n * lam[order[j]]);
   }
   __syncthreads();
   for (int e = t; e < K * K; e += kT) {
@@ -958,8 +1040,19 @@ cudaError_t launch_align(const float* Zl, int64_t z_stride, const float* Zb, int
 
 cudaError_t launch_aggregate(const float* Yl, const float* w, const float* G, int diag_only, int m, int d, int K,
                              float* Y, cudaStream_t s, const int* prob_begin, int nprob) {
-  const int rpb = kT / K;
-  aggregate_kernel<<<dim3((d + rpb - 1) / rpb, nprob), kT, 0, s>>>(Yl, w, G, diag_only, m, d, K, prob_begin, Y);
+  // slices: a power of two up to the partitions per problem, at most 16
+  const int per = nprob > 0 ? m / nprob : m;
+  int S = 1;
+  while (S * 2 <= per && S * 2 <= 16) S *= 2;
+  const int rpb = kT / (K / 4 * S);
+  const dim3 grid((d + rpb - 1) / rpb, nprob);
+  switch (K) {
+    case 4: aggregate_kernel<4><<<grid, kT, 0, s>>>(Yl, w, G, diag_only, m, d, S, prob_begin, Y); break;
+    case 8: aggregate_kernel<8><<<grid, kT, 0, s>>>(Yl, w, G, diag_only, m, d, S, prob_begin, Y); break;
+    case 16: aggregate_kernel<16><<<grid, kT, 0, s>>>(Yl, w, G, diag_only, m, d, S, prob_begin, Y); break;
+    case 32: aggregate_kernel<32><<<grid, kT, 0, s>>>(Yl, w, G, diag_only, m, d, S, prob_begin, Y); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
