@@ -519,19 +519,20 @@ __device__ void forward_rows(const float* Yin, float* Zout, const float* Lf, con
   }
 }
 
-// Z = orth(Y) of one d x K block by the CTA.  Y and Z may be written earlier in
-// the same kernel (the fused reduction writes Y; the second pass reads Z).
-// F64: Gram and Cholesky in FP64 (LP_FLAG_KXK_FP64); else the FP32 Gram and
-// FP32 Cholesky with the FP64 factorisation as fallback.  The d x k forward
+// Z = orth(Y) of one d x K block by the CTA: the first pass writes Zmid from Y,
+// the second Zout from Zmid (Zmid may be Y itself: each thread solves its own
+// rows in place; or Zout).  Any of them may have been written earlier in the same
+// kernel.  F64: Gram and Cholesky in FP64 (LP_FLAG_KXK_FP64); else the FP32 Gram
+// and FP32 Cholesky with the FP64 factorisation as fallback.  The d x k forward
 // substitution is FP32 either way.
 template <int K, bool F64>
-__device__ void cholqr2_block(const float* Y, float* Z, int d, int k, int* status) {
+__device__ void cholqr2_block(const float* Y, float* Zmid, float* Zout, int d, int k, int* status) {
   __shared__ __align__(16) double G[K * K];
   __shared__ __align__(16) float Lf[K * K];
   __shared__ float invd[K];
   __shared__ __align__(16) unsigned char red[(F64 ? 8 : 4) * kT * 16];
   for (int pass = 0; pass < 2; ++pass) {
-    const float* src = pass == 0 ? Y : Z;
+    const float* src = pass == 0 ? Y : Zmid;
     if (F64) {
       gram_fp64<K>(src, d, reinterpret_cast<double*>(red), G);
       if (threadIdx.x < 32) {
@@ -546,15 +547,60 @@ __device__ void cholqr2_block(const float* Y, float* Z, int d, int k, int* statu
       }
     }
     __syncthreads();
-    forward_rows<K>(src, Z, Lf, invd, d, k);
+    forward_rows<K>(src, pass == 0 ? Zmid : Zout, Lf, invd, d, k);
     __syncthreads();
   }
 }
 
-template <int K, bool F64>
+// One CTA per block.  STAGED: the d x K block is copied into shared memory once
+// (eight 16-byte loads in flight per thread), both Grams and the first solve
+// work there (the first pass's Z overwrites Y in place) and only the second
+// pass writes global memory; otherwise each pass reads global memory (blocks
+// larger than kCholStageBytes).
+constexpr size_t kCholStageBytes = size_t(128) << 10;
+
+template <int K, bool F64, bool STAGED>
 __global__ void __launch_bounds__(kT) cholqr2_kernel(const float* __restrict__ Yall, float* __restrict__ Zall, int d,
                                                      int k, int* status) {
-  cholqr2_block<K, F64>(Yall + int64_t(blockIdx.x) * d * K, Zall + int64_t(blockIdx.x) * d * K, d, k, status);
+  const float* Y = Yall + int64_t(blockIdx.x) * d * K;
+  float* Z = Zall + int64_t(blockIdx.x) * d * K;
+  if constexpr (STAGED) {
+    extern __shared__ __align__(16) float4 stage4[];
+    const float4* Y4 = reinterpret_cast<const float4*>(Y);
+    const int n4 = d * (K / 4);
+    constexpr int UL = 8;
+    for (int e0 = threadIdx.x; e0 < n4; e0 += kT * UL) {
+      float4 v[UL];
+#pragma unroll
+      for (int q = 0; q < UL; ++q) {
+        const int e = e0 + q * kT;
+        v[q] = e < n4 ? Y4[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < UL; ++q) {
+        const int e = e0 + q * kT;
+        if (e < n4) stage4[e] = v[q];
+      }
+    }
+    __syncthreads();
+    float* stage = reinterpret_cast<float*>(stage4);
+    cholqr2_block<K, F64>(stage, stage, Z, d, k, status);
+  } else {
+    cholqr2_block<K, F64>(Y, Z, Z, d, k, status);
+  }
+}
+
+template <int K, bool F64>
+cudaError_t launch_cholqr2_t(const float* Y, float* Z, int batch, int d, int k, int* status, cudaStream_t s) {
+  const size_t bytes = size_t(d) * K * 4;
+  if (bytes <= kCholStageBytes) {
+    const cudaError_t e = allow_max_dynamic_smem(reinterpret_cast<const void*>(cholqr2_kernel<K, F64, true>));
+    if (e != cudaSuccess) return e;
+    cholqr2_kernel<K, F64, true><<<batch, kT, bytes, s>>>(Y, Z, d, k, status);
+  } else {
+    cholqr2_kernel<K, F64, false><<<batch, kT, 0, s>>>(Y, Z, d, k, status);
+  }
+  return cudaGetLastError();
 }
 
 
@@ -1019,15 +1065,14 @@ cudaError_t launch_reduce(const float* P, const int* slot_begin, const float* sc
 cudaError_t launch_cholqr2(const float* Y, float* Z, int batch, int d, int k, int K, int* status, cudaStream_t s,
                            bool kxk_fp64) {
   switch (K * 2 + (kxk_fp64 ? 1 : 0)) {
-    case 16: cholqr2_kernel<8, false><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
-    case 17: cholqr2_kernel<8, true><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
-    case 32: cholqr2_kernel<16, false><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
-    case 33: cholqr2_kernel<16, true><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
-    case 64: cholqr2_kernel<32, false><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
-    case 65: cholqr2_kernel<32, true><<<batch, kT, 0, s>>>(Y, Z, d, k, status); break;
+    case 16: return launch_cholqr2_t<8, false>(Y, Z, batch, d, k, status, s);
+    case 17: return launch_cholqr2_t<8, true>(Y, Z, batch, d, k, status, s);
+    case 32: return launch_cholqr2_t<16, false>(Y, Z, batch, d, k, status, s);
+    case 33: return launch_cholqr2_t<16, true>(Y, Z, batch, d, k, status, s);
+    case 64: return launch_cholqr2_t<32, false>(Y, Z, batch, d, k, status, s);
+    case 65: return launch_cholqr2_t<32, true>(Y, Z, batch, d, k, status, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_align(const float* Zl, int64_t z_stride, const float* Zb, int m, int d, int k, int K, int base,
