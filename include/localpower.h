@@ -473,7 +473,7 @@ lp_status lp_align_aggregate(lp_ctx* ctx, int m, int64_t d, int k, lp_aggregator
  * A problem whose scratch would exceed the array fails with LP_ERR_INVALID
  * and launches nothing; lp_last_error(NULL) describes any failure.  The first
  * call on a device (made with that device current) looks up the array's
- * device address; make that first call before any stream capture.  Every call
+ * device address and keeps it for later calls.  Every call
  * shares the one array, which keeps the last call's contents: each call
  * writes everything it reads, but calls whose work overlaps on the GPU race.
  * A bounded wait that gives up inside the step kernel (a stall of seconds)

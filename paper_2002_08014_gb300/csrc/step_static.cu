@@ -12,8 +12,7 @@
 //   * The array is part of the library image: every GPU that loads the library
 //     holds it (32 MiB) until the process exits.
 //   * The first call on a device, with that device current, looks up the
-//     array's device address (cudaGetSymbolAddress) and caches it; make that
-//     first call before any stream capture.
+//     array's device address (cudaGetSymbolAddress) and caches it.
 //   * All calls share the one array and it keeps the last call's contents.
 //     Every byte a call reads is written earlier in the same call (the kernels
 //     overwrite the tables, partials and padded blocks in full, and the status
