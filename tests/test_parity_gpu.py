@@ -119,7 +119,11 @@ def test_orth_reports_rank_deficiency(gpu_lib):
 
 
 @pytest.mark.parametrize("agg", ["identity", "sign", "opt"])
-@pytest.mark.parametrize("d,k,m,base", [(100, 5, 4, 0), (513, 16, 7, 3), (64, 32, 3, 2), (30, 1, 5, 4)])
+@pytest.mark.parametrize("d,k,m,base", [(100, 5, 4, 0), (513, 16, 7, 3), (64, 32, 3, 2), (30, 1, 5, 4),
+                                        # odd k next to the column padding (a dummy column in the
+                                        # Jacobi's round-robin pairing), 16 partition slices with a
+                                        # ragged last pass, a single partition, the FP32 workload's shape
+                                        (257, 13, 20, 19), (40, 31, 17, 0), (16, 3, 1, 0), (1024, 16, 64, 5)])
 def test_align_aggregate_matches_oracle(gpu_lib, agg, d, k, m, base):
     rng = np.random.default_rng(7 * d + k)
     Zb = O.orth(rng.standard_normal((d, k)))
@@ -147,6 +151,7 @@ def test_align_aggregate_matches_oracle(gpu_lib, agg, d, k, m, base):
             assert np.array_equal(D[i], Dref)          # the +-1 decisions are exact
         else:
             assert np.abs(D[i] - Dref).max() < 1e-5
+            assert np.abs(D[i].T @ D[i] - np.eye(k)).max() < 1e-5
 
 
 @pytest.mark.parametrize("agg", ["sign", "opt", "identity"])
