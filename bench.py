@@ -134,12 +134,23 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# host seconds spent generating synthetic inputs (outside every timed region),
+# reported beside the results as data_generation_s
+_DATA_GEN_S = [0.0]
+
+
+def _emit(line: dict) -> None:
+    print(json.dumps(dict(line, data_generation_s=_DATA_GEN_S[0])))
+
+
 def _workload(rank: int, rows: int | None = None, name: str = WORKLOAD):
     import synth
+    t = time.perf_counter()
     c = dict(synth.CONFIGS[name])
     if rows:
         c["n"] = int(rows)
     A, sizes, Y0 = synth.make_config_data(name, n=c["n"])
+    _DATA_GEN_S[0] += time.perf_counter() - t
     return c, A, sizes, Y0, synth.config_schedule(name)
 
 
@@ -180,7 +191,7 @@ def run_reference(args):
             "config": _config(c, sched),
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample_txt},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    _emit(line)
 
 
 # DRAM bytes per launch over algorithmic bytes, from ncu captures (dram__bytes_read.sum +
@@ -344,7 +355,7 @@ def run_lowprec(args):
         if fp8 and "error" not in fp8:
             line["fp8_path"]["dist_to_eigh_topk_fp32_problem"] = oracle.subspace_dist(oracle.orth(Z8), Vf)
     if rank == 0:
-        print(json.dumps(line))
+        _emit(line)
     if world > 1:
         dist.destroy_process_group()
 
@@ -410,7 +421,7 @@ def run_plain(args):
                                 "one_thread_sample": f"{runs1} whole oracle solves in about 10 s, BLAS limited "
                                                      f"to one thread", **_cpu_info()}
     if rank == 0:
-        print(json.dumps(line))
+        _emit(line)
     if world > 1:
         dist.destroy_process_group()
 
@@ -443,6 +454,7 @@ def _width_pools(torch, local, seed, pool_rows, fp32=False):
     its own Haar rotation and lambda_j = 0.85^j (j <= width); host copies too.
     fp32: also device pools of the FP32 rows the BF16 ones are rounded from."""
     import synth
+    t = time.perf_counter()
     bits, dev, dev32 = {}, {}, {}
     for wi, w in enumerate(SERVING_WIDTHS):
         lam = 0.85 ** np.arange(1, w + 1)
@@ -453,6 +465,7 @@ def _width_pools(torch, local, seed, pool_rows, fp32=False):
         if fp32:
             dev32[w] = torch.from_numpy(rows).cuda(local)
         del rows
+    _DATA_GEN_S[0] += time.perf_counter() - t
     return (bits, dev, dev32) if fp32 else (bits, dev)
 
 
@@ -571,7 +584,7 @@ def run_batching(args):
             "clocks": clk, "e2e": None,
             "accuracy_sample": {"dist_to_oracle": [float(x) for x in acc_o], "max_dist_to_oracle": float(max(acc_o)),
                                 "dist_to_eigh_topk": [float(x) for x in acc]}}
-    print(json.dumps(line))
+    _emit(line)
 
 
 def run_rounds(args):
@@ -782,7 +795,7 @@ def run_serving(args):
                                                        "met": bool(max(acc32) <= 1e-4),
                                                        "truth": "FP64 eigendecomposition of the FP32 rows"}},
             "saturated": sat}
-    print(json.dumps(line))
+    _emit(line)
 
 
 def run_kernels(args):
@@ -1156,7 +1169,7 @@ def run_ours(args):
                                                      "BLAS limited to one thread",
                                 **_cpu_info()}
     if rank == 0:
-        print(json.dumps(line))
+        _emit(line)
     if world > 1:
         dist.destroy_process_group()
 
