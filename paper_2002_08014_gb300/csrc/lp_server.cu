@@ -338,7 +338,11 @@ void drop_batch_graph(lp_batch* b) {
   b->solved = false;
 }
 
+// The group contexts go only after a batch solve still running on the root
+// stream (a later add or autotune may follow a solve without a result call).
 void drop_groups(lp_batch* b) {
+  if (b->root && (b->exec || !b->groups.empty()) && cudaStreamSynchronize(b->root) != cudaSuccess)
+    (void)cudaGetLastError();
   drop_batch_graph(b);
   for (auto& g : b->groups) {
     if (g->join) cudaEventDestroy(g->join);
